@@ -1,0 +1,206 @@
+"""Pins of the oracle's full explicit step (Sec. 3.1-3.2): Sod's shock tube against the
+exact Riemann solution, free-stream preservation of the axisymmetric discretisation,
+conservation in a closed box and against the boundary fluxes in an open one, and the
+isentropic nozzle."""
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import riemann
+from conftest import read_golden, ROOT
+from synth import cases
+
+RA = 287.05
+
+
+def _field(prims_rows, nr, nx):
+    U = O.prim_to_cons_batch(prims_rows)
+    return np.ascontiguousarray(U.T.reshape(14, nr, nx))
+
+
+@pytest.mark.parametrize("row", read_golden("toro_star_states.txt"))
+def test_exact_riemann_solver_against_toro(row):
+    v = [float(x) for x in row]
+    p, u = riemann.star_state(tuple(v[0:3]), tuple(v[3:6]))
+    assert p == pytest.approx(v[6], rel=2e-4, abs=1e-5)
+    assert u == pytest.approx(v[7], rel=2e-4, abs=1e-5)
+
+
+def _sod(nx, t_end=6.3e-4):
+    c = cases.shock_tube_case(nx)
+    o = O.Oracle(c)
+    x = (np.arange(nx) + 0.5) / nx
+    P = np.zeros((nx, 14))
+    left = x < 0.5
+    P[:, 0] = np.where(left, 1.0e5, 1.0e4)
+    rho = np.where(left, 1.0, 0.125)
+    P[:, 1] = P[:, 0] / (rho * RA)
+    U = _field(P, 1, nx)
+    t = 0.0
+    while t < t_end - 1e-15:
+        dt = o.dt(U, 0.5)
+        if t + dt > t_end:
+            break
+        d = o.step(U, 1, 0.5)
+        t += d[0, 0]
+    ex = riemann.sample((1.0, 0.0, 1.0e5), (0.125, 0.0, 1.0e4), (x - 0.5) / t)
+    return np.abs(U[0, 0] - ex[0]).mean(), U, ex
+
+
+def test_sod_converges_to_exact_solution():
+    errs = [_sod(n)[0] for n in (100, 200, 400)]
+    assert errs[2] < errs[1] < errs[0]
+    rate = math.log(errs[0] / errs[2], 4.0)
+    assert 0.5 < rate < 1.5          # discontinuities limit the order to about one
+    assert errs[2] < 6e-3
+
+
+def test_sod_star_region_values():
+    _, U, ex = _sod(400)
+    P = O.cons_to_prim_batch(np.ascontiguousarray(U[:, 0, :].T))
+    x = (np.arange(400) + 0.5) / 400
+    ps, us = riemann.star_state((1.0, 0.0, 1.0e5), (0.125, 0.0, 1.0e4))
+    mid = (x > 0.56) & (x < 0.64)        # between contact and shock at this time
+    assert np.allclose(P[mid, 3], ps, rtol=5e-3)
+    assert np.allclose(P[mid, 1], us, rtol=1e-2)
+
+
+def test_free_stream_preservation_axisymmetric_at_rest():
+    """A uniform gas at rest in a closed axisymmetric box stays uniform: the geometric
+    source p/r balances the radial flux difference (a dropped or mis-scaled term fails)."""
+    c, _ = cases.closed_box_case(nx=20, nr=16)
+    c.update(phase_change=0)
+    o = O.Oracle(c)
+    P = np.zeros((20 * 16, 14))
+    P[:, 0], P[:, 1], P[:, 4] = 2.4e4, 250.0, 0.01
+    U = _field(P, 16, 20)
+    U0 = U.copy()
+    o.step(U, 20, 0.5)
+    P = O.cons_to_prim_batch(np.ascontiguousarray(U0[:, 0, :1].T))[0]
+    mom = U0[0].max() * math.sqrt(P[8])            # momentum scale rho c
+    scale = np.abs(U0).reshape(14, -1).max(axis=1)
+    scale[1:3] = mom
+    err = np.abs(U - U0).reshape(14, -1).max(axis=1)
+    assert np.all(err <= 1e-12 * scale)
+
+
+def test_free_stream_preservation_uniform_flow():
+    """Uniform ambient coflow through inflow, outflow and far-field boundaries."""
+    c, _ = cases.mixing_layer_case(nx=24, nr=12, seeded=False)
+    c.update(d_core=0.0, d_fan=0.0, mix_width=0.0, phase_change=0)
+    o = O.Oracle(c)
+    U = o.init_state()
+    U0 = U.copy()
+    o.step(U, 20, 0.5)
+    assert np.max(np.abs(U - U0)) <= 1e-12 * np.max(np.abs(U0))
+
+
+def _q1d_box_state(c):
+    """Moist gas at rest, cold in the middle (supersaturated over liquid, nucleating)
+    and warm at the ends, with a seeded droplet population."""
+    nx = c["nx"]
+    x = (np.arange(nx) + 0.5) / nx
+    P = np.zeros((nx, 14))
+    P[:, 0] = 3.0e4
+    P[:, 1] = 300.0 - 80.0 * np.exp(-((x - 0.5) / 0.15) ** 2)
+    P[:, 4] = 0.01
+    n, r = 1e10, 2e-7
+    for k in range(4):
+        P[:, 5 + k] = n * (r / 1e-6) ** k
+    return _field(P, 1, nx)
+
+
+@pytest.mark.parametrize("geom", [1, 0])
+def test_closed_box_conserves_mass_water_energy(geom):
+    c, uf = cases.closed_box_case(geom=geom)
+    o = O.Oracle(c, uf)
+    U = o.init_state() if geom == 1 else _q1d_box_state(c)
+    d0 = o.step(U.copy(), 1, 0.5)
+    d = o.step(U, 100, 0.5)
+    M0, W0, E0 = d0[0, 1], d0[0, 2], d0[0, 3]
+    assert np.all(d[:, 8] == 0)
+    assert d[:, 7].max() > 0   # sources were active
+    for k, ref in ((1, M0), (2, W0), (3, E0)):
+        assert np.max(np.abs(d[:, k] - ref)) <= 1e-12 * abs(ref)
+    assert np.all(np.abs(d[:, 4:7]) <= 1e-12 * np.array([M0, W0, abs(E0)]))
+
+
+def test_open_box_balance_against_boundary_fluxes():
+    """Per step: change of total mass, water and energy = inflow through the boundary
+    integrated by the RK2 rule (sources exchange water between phases only)."""
+    c, uf = cases.mixing_layer_case()
+    o = O.Oracle(c, uf)
+    U = o.init_state()
+    d = o.step(U, 60, 0.5)
+    assert d[:, 7].max() > 100 and np.isfinite(d[:, 23]).any()
+    for k in range(3):
+        tot = d[:, 1 + k]
+        bal = np.diff(tot) - d[1:, 4 + k]
+        assert np.max(np.abs(bal)) <= 1e-12 * np.max(np.abs(tot)), k
+
+
+def test_isentropic_dry_nozzle():
+    """Dry nozzle (sources off) marched to steady state: choked mass flow and the exit
+    Mach number of the area-Mach relation for A/A* = 3.5."""
+    c = cases.nozzle_case(nx=100, phase_change=False)
+    o = O.Oracle(c)
+    U = o.init_state()
+    o.step(U, 6000, 0.5)
+    P = O.cons_to_prim_batch(np.ascontiguousarray(U[:, 0, :].T))
+    x = (np.arange(100) + 0.5) * 0.002
+    A = 1.0 + 2.5 * (x / 0.1 - 1.0) ** 2
+    mdot = P[:, 0] * P[:, 1] * A
+    Yv = 0.02
+    cp = (1 - Yv) * (RA / 0.4 + RA) + Yv * 1859.0
+    cv = (1 - Yv) * RA / 0.4 + Yv * O.const("cv_v")
+    g, R = cp / cv, cp - cv
+    mdot_choked = 40e3 / math.sqrt(c["T0"]) * math.sqrt(g / R) * (2 / (g + 1)) ** ((g + 1) / (2 * (g - 1)))
+    assert np.std(mdot) / np.mean(mdot) < 2e-3
+    assert np.mean(mdot) == pytest.approx(mdot_choked, rel=1.5e-2)
+    M_exit = P[-1, 1] / math.sqrt(P[-1, 8])
+    # area-Mach relation at the last cell centre, supersonic branch
+    ar = A[-1]
+    lo, hi = 1.0, 6.0
+    for _ in range(100):
+        m = 0.5 * (lo + hi)
+        f = 1 / m * (2 / (g + 1) * (1 + 0.5 * (g - 1) * m * m)) ** ((g + 1) / (2 * (g - 1))) - ar
+        lo, hi = (lo, m) if f > 0 else (m, hi)
+    assert M_exit == pytest.approx(0.5 * (lo + hi), rel=2e-2)
+
+
+def test_condensing_nozzle_nucleates_after_the_throat():
+    """Moist nozzle: homogeneous nucleation switches on downstream of the throat (the
+    Wilson point) and leaves liquid at the exit; the state stays finite."""
+    c = cases.nozzle_case(nx=200)
+    o = O.Oracle(c)
+    U = o.init_state()
+    d = o.step(U, 3000, 0.5)
+    assert np.all(d[:, 8] == 0)
+    lj = o.derived(U, 4)[0]
+    x = (np.arange(200) + 0.5) * 0.001
+    on = x[np.isfinite(lj) & (lj > 0)]
+    assert on.size > 0 and on.min() > 0.09                  # onset near the throat
+    ipk = int(np.argmax(np.where(np.isfinite(lj), lj, -1e300)))
+    assert x[ipk] > 0.1                                      # peak downstream of the throat
+    after = np.where(np.isfinite(lj[ipk:]), lj[ipk:], -1e300)
+    assert after.min() < lj[ipk] - 20.0                      # quenched by the latent heat
+    Yl = 4.0 / 3.0 * math.pi * 1000.0 * U[8, 0, -1] / U[0, 0, -1] * 1e-18
+    assert Yl > 1e-4
+
+
+def test_results_do_not_depend_on_thread_count():
+    code = ("import sys; sys.path.insert(0, %r); import numpy as np, oracle as O; "
+            "from synth import cases; c, uf = cases.mixing_layer_case(nx=40, nr=20); "
+            "o = O.Oracle(c, uf); U = o.init_state(); o.step(U, 20, 0.5); "
+            "sys.stdout.buffer.write(U.tobytes())") % ROOT
+    outs = []
+    for nt in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=nt)
+        outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                                   check=True).stdout)
+    assert outs[0] == outs[1]

@@ -1,0 +1,270 @@
+"""Pins of the oracle's phase-change source (Sec. 2.2, Eqs. (1)-(21); readings D, F-J):
+brute force on the Gibbs energy of Eq. (2), the molecular (Becker-Doering) form of the CNT
+prefactor, special cases of the growth law, and mass conservation of every source."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import cases
+
+NA, KB, MW = 6.02214076e23, 1.380649e-23, 0.018015
+PI = math.pi
+
+
+def _state(p, T, Yv, ml=(0, 0, 0, 0), ms=(0, 0, 0, 0), ns=0.0, u=0.0):
+    return O.prim_to_cons_batch(np.array([[p, T, u, 0.0, Yv, *ml, *ms, ns]]))[0]
+
+
+def _yv_for_S(S, T, p):
+    """Vapour mass fraction giving liquid saturation ratio S at (T, p)."""
+    Ra, Rv = 287.05, O.const("R_v")
+    pv = S * math.exp(O.ln_psat_l(T))
+    return pv * Ra / (Rv * (p - pv) + pv * Ra)
+
+
+def _case(**kw):
+    c, _ = cases.mixing_layer_case(seeded=False)
+    c.update(kw)
+    return c
+
+
+GRID = [(S, T) for S in (1.5, 3.0, 5.0, 10.0, 20.0) for T in (200.0, 220.0, 240.0)]
+
+
+@pytest.mark.parametrize("S,T", GRID)
+def test_kelvin_radius_and_barrier_by_brute_force(S, T):
+    """Eq. (3) is the maximum of Eq. (2): find max_r dG(r) numerically, compare r* with
+    the oracle's r_crit and dG(r*)/kT with the barrier implied by ln J_het - ln J_hom."""
+    p = 24e3
+    Yv = _yv_for_S(S, T, p)
+    U = _state(p, T, Yv, ns=0.0)
+    rho = U[0]
+    c = _case(n_soot=1.0)   # soot at the reference number per volume: gate = 1
+    U[13] = 1.0
+    Q, aux = O.source_batch(c, U, 1e-9)
+    lnS, rc, lnJhom, lnJhet = aux[0, 0], aux[0, 5], aux[0, 2], aux[0, 3]
+    assert lnS == pytest.approx(math.log(S), rel=1e-10)
+    sig = O.sigma_lg(T)
+    Rv = O.const("R_v")
+    dG = lambda r: 4.0 / 3.0 * PI * r**3 * 1000.0 * (-Rv * T * lnS) + 4.0 * PI * r * r * sig
+    # golden-section search for the maximum of dG on (0, 1e-7)
+    a, b = 1e-12, 1e-7
+    gr = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(200):
+        x1, x2 = b - gr * (b - a), a + gr * (b - a)
+        if dG(x1) > dG(x2):
+            b = x2
+        else:
+            a = x1
+    rstar = 0.5 * (a + b)
+    assert rc == pytest.approx(rstar, rel=1e-6)
+    barrier = dG(rstar) / (KB * T)
+    # f(90 deg) = 1/2 (Eq. (9)): ln J_het - ln J_hom = (1 - f) dG*/kT
+    assert (lnJhet - lnJhom) == pytest.approx(0.5 * barrier, rel=1e-9)
+
+
+@pytest.mark.parametrize("S,T", GRID)
+def test_cnt_prefactor_molecular_form(S, T):
+    """The prefactor of Eq. (4), q_c sqrt(2 sigma N_A^3/(pi M^3)) rho_g^2/rho_l, equals the
+    Becker-Doering/Frenkel molecular form n_v^2 v_m sqrt(2 sigma/(pi m)) with m the molecular
+    mass, n_v the vapour number density and v_m the molecular volume of the liquid."""
+    p = 24e3
+    Yv = _yv_for_S(S, T, p)
+    U = _state(p, T, Yv)
+    rho = U[0]
+    c = _case(n_soot=1.0)
+    U[13] = 1.0   # n_soot per volume = 1 = reference -> gate 1
+    _, aux = O.source_batch(c, U, 1e-9)
+    lnA = 2.0 * aux[0, 3] - aux[0, 2]     # ln J_het = lnA - dG/2kT, ln J_hom = lnA - dG/kT
+    m = MW / NA
+    rhov = rho * Yv
+    nv = rhov / m
+    vm = m / 1000.0
+    lnA_mol = math.log(nv * nv * vm * math.sqrt(2.0 * O.sigma_lg(T) / (PI * m)))
+    assert lnA == pytest.approx(lnA_mol, abs=1e-9)
+
+
+@pytest.mark.parametrize("S", [0.2, 0.9, 1.0])
+def test_no_nucleation_at_or_below_saturation(S):
+    T, p = 220.0, 24e3
+    U = _state(p, T, _yv_for_S(S, T, p), ns=1e12)
+    Q, aux = O.source_batch(_case(), U, 1e-5)
+    assert aux[0, 2] == -math.inf and aux[0, 3] == -math.inf
+    assert np.all(Q == 0.0)   # no population: exactly zero source
+    assert aux[0, 4] == 0.0
+
+
+def test_het_nucleation_gated_by_soot():
+    """Without soot only homogeneous nucleation occurs (Sec. 4.3, hydrogen case)."""
+    T, p = 220.0, 24e3
+    U = _state(p, T, _yv_for_S(8.0, T, p), ns=0.0)
+    Q0, aux0 = O.source_batch(_case(), U, 1e-9)
+    assert aux0[0, 3] == -math.inf and aux0[0, 2] > -math.inf
+
+
+def _gas(T, p, Yv):
+    """Gas-phase transport inputs of the growth law (reading G)."""
+    Ra, Rv = 287.05, O.const("R_v")
+    cp = (1 - Yv) * (Ra / 0.4 + Ra) + Yv * 1859.0
+    cv = (1 - Yv) * Ra / 0.4 + Yv * O.const("cv_v")
+    mu = 1.716e-5 * (T / 273.15) ** 1.5 * (273.15 + 110.4) / (T + 110.4)
+    lam = mu * cp / 0.71
+    lbar = 1.5 * mu * math.sqrt(((1 - Yv) * Ra + Yv * Rv) * T) / p
+    return lam, lbar, cp / cv, cp
+
+
+def test_growth_vanishes_at_critical_radius_and_has_the_right_sign():
+    T, p, Yv = 230.0, 24e3, 0.002
+    pv = p * Yv * O.const("R_v") / ((1 - Yv) * 287.05 + Yv * O.const("R_v"))
+    lnS = math.log(pv) - O.ln_psat_l(T)
+    Ts = O.tsat(pv, 0)
+    sig = O.sigma_lg(T)
+    h = O.hfg(T)
+    lam, lbar, gam, cp = _gas(T, p, Yv)
+    rc = 2 * sig / (1000.0 * O.const("R_v") * T * lnS)
+    g = lambda r, lnS_=lnS, Ts_=Ts: O.growth(r, T, Ts_, lnS_, sig, 1000.0, h, lam, lbar, gam, cp)
+    assert abs(g(rc)) < 1e-12 * abs(g(10 * rc))
+    assert g(2 * rc) > 0 and g(1e-6) > 0 and g(0.5 * rc) < 0
+    # sub-saturated: every droplet evaporates
+    assert g(1e-7, -0.2, O.tsat(pv * math.exp(-0.2 - lnS), 0)) < 0
+
+
+def test_growth_continuum_limit_is_heat_conduction():
+    """Kn -> 0: Eq. (16) reduces to conduction-limited growth lam dT (1 - rc/r)/(rho h r)."""
+    T, p, Yv = 230.0, 24e3, 0.002
+    pv = p * Yv * O.const("R_v") / ((1 - Yv) * 287.05 + Yv * O.const("R_v"))
+    lnS = math.log(pv) - O.ln_psat_l(T)
+    Ts = O.tsat(pv, 0)
+    sig, h = O.sigma_lg(T), O.hfg(T)
+    lam, _, gam, cp = _gas(T, p, Yv)
+    r = 5e-6
+    rc = 2 * sig / (1000.0 * O.const("R_v") * T * lnS)
+    gc = O.growth(r, T, Ts, lnS, sig, 1000.0, h, lam, 1e-30, gam, cp)
+    assert gc == pytest.approx(lam * (Ts - T) * (1 - rc / r) / (1000.0 * h * r), rel=1e-12)
+
+
+def test_growth_regular_at_saturation():
+    """The Delta T / ln S form of reading G is continuous through S = 1."""
+    T, p = 230.0, 24e3
+    lam, lbar, gam, cp = _gas(T, p, 0.001)
+    sig, h = O.sigma_lg(T), O.hfg(T)
+    pv0 = math.exp(O.ln_psat_l(T))
+    vals = []
+    for e in (-2e-8, -5e-9, 5e-9, 2e-8):
+        pv = pv0 * math.exp(e)
+        vals.append(O.growth(1e-7, T, O.tsat(pv, 0), math.log(pv) - O.ln_psat_l(T), sig, 1000.0, h,
+                             lam, lbar, gam, cp))
+    assert np.all(np.isfinite(vals))
+    assert abs(vals[1] - vals[2]) < 1e-3 * abs(vals[0] - vals[3]) + 1e-6 * abs(vals[0])
+
+
+def test_growth_moment_source_is_exact_for_a_monodisperse_population():
+    """For mu_k = n r^k the r20 closure (Eq. (21)) is exact: the source of the k-th moment
+    must be k n r^(k-1) G(r), with G from Eq. (16); checks indices, moment scaling and the
+    per-volume factor rho of Eq. (26)."""
+    T, p, Yv = 230.0, 24e3, 0.0015
+    r, n = 3e-7, 1e9
+    ml = tuple(n * (r / 1e-6) ** k for k in range(4))
+    U = _state(p, T, Yv, ml=ml)
+    rho = U[0]
+    c = _case(freezing=0)
+    Q, aux = O.source_batch(c, U, 1e-12)
+    G = aux[0, 7]
+    assert G != 0.0
+    for k in range(1, 4):
+        expect = rho * k * n * r ** (k - 1) * G / 1e-6**k
+        assert Q[0, 5 + k] == pytest.approx(expect, rel=1e-12)
+    assert Q[0, 5] == 0.0 or aux[0, 0] > 0
+    # nucleation at S < 1 is off, so Q_0 = 0 exactly
+    if aux[0, 0] <= 0:
+        assert Q[0, 5] == 0.0
+
+
+def test_nucleation_moment_source_and_eq6_mass():
+    """Newly nucleated droplets sit at r_crit (Eq. (20)): Q_k ~ J r_crit^k, and the liquid
+    mass gain equals Eq. (6): (4/3) pi r_crit^3 rho_l J/(1+phi)."""
+    T, p = 220.0, 24e3
+    U = _state(p, T, _yv_for_S(12.0, T, p))
+    c = _case()
+    Q, aux = O.source_batch(c, U, 1e-12)
+    rc, phi = aux[0, 5], aux[0, 6]
+    Jhom = math.exp(aux[0, 2])
+    for k in range(3):
+        assert Q[0, 6 + k] / Q[0, 5 + k] == pytest.approx(rc / 1e-6, rel=1e-12)
+    dYl = 4.0 / 3.0 * PI * 1000.0 * Q[0, 8] * 1e-18
+    assert dYl == pytest.approx(4.0 / 3.0 * PI * rc**3 * 1000.0 * Jhom / (1.0 + phi), rel=1e-12)
+    assert phi > 0
+
+
+def _random_states(n, seed=7):
+    rng = np.random.default_rng(seed)
+    P = np.zeros((n, 14))
+    P[:, 0] = rng.uniform(8e3, 40e3, n)
+    P[:, 1] = rng.uniform(190.0, 300.0, n)
+    P[:, 2] = rng.uniform(-50, 400, n)
+    P[:, 4] = 10 ** rng.uniform(-5, -1, n)
+    for base, rho_d in ((5, 1000.0), (9, 917.0)):
+        Y = 10 ** rng.uniform(-14, -2.5, n)            # condensed mass fraction
+        r = 10 ** rng.uniform(-9, -5.5, n)
+        sg = np.exp(rng.uniform(0, 0.4, n) ** 2)       # lognormal spread: mu2 mu0 >= mu1^2
+        nn = Y / (4.0 / 3.0 * PI * rho_d * r**3 * sg**4.5)
+        for k in range(4):
+            P[:, base + k] = nn * (r / 1e-6) ** k * sg ** (k * k / 2.0)
+    P[:, 13] = 10 ** rng.uniform(8, 13, n)
+    return O.prim_to_cons_batch(P)
+
+
+@pytest.mark.parametrize("dt", [1e-7, 1e-5, 1e-3])
+def test_every_source_conserves_water_and_never_creates_mass(dt):
+    """Eqs. (18), (25): the vapour sink is the condensed gain negated, cell by cell; rho,
+    momentum, energy and soot have no source (reading E: latent heat is in the formation
+    energies)."""
+    U = _random_states(3000)
+    c = _case()
+    Q, aux = O.source_batch(c, U, dt)
+    assert np.all(np.isfinite(Q))
+    water = Q[:, 4] + 4.0 / 3.0 * PI * (1000.0 * Q[:, 8] + 917.0 * Q[:, 12]) * 1e-18
+    scale = np.abs(Q[:, 4]) + 4.0 / 3.0 * PI * (1000.0 * np.abs(Q[:, 8]) + 917.0 * np.abs(Q[:, 12])) * 1e-18
+    assert np.all(np.abs(water) <= 1e-13 * scale + 1e-300)
+    assert np.all(Q[:, [0, 1, 2, 3, 13]] == 0.0)
+    # positivity limiters (reading J): the source alone never drives a phase negative
+    new = U + dt * Q
+    assert np.all(new[:, 4] >= -1e-14 * U[:, 4])
+    assert np.all(new[:, 8] >= -1e-12 * np.abs(U[:, 8]))
+    assert np.all(new[:, 12] >= -1e-12 * np.abs(U[:, 12]))
+    assert aux[:, 4].sum() > 100
+
+
+def test_freezing_transfers_mass_without_loss():
+    """Immersion + homogeneous freezing moves droplets to ice at equal mass
+    (rho_s r_f^3 = rho_l r_v^3); with growth switched off by S_l = S_i = 1 nothing else acts."""
+    T, p = 225.0, 24e3
+    r, n = 2e-7, 1e9
+    ml = tuple(n * (r / 1e-6) ** k for k in range(4))
+    # vapour exactly at ice saturation; liquid subsaturated -> evaporation + freezing
+    Ra, Rv = 287.05, O.const("R_v")
+    pv = math.exp(O.ln_psat_i(T))
+    Yv = pv * Ra / (Rv * (p - pv) + pv * Ra)
+    U = _state(p, T, Yv, ml=ml, ns=1e12)
+    Q, aux = O.source_batch(_case(), U, 1e-12)
+    omega = aux[0, 10]
+    assert omega > 0
+    Nf = n * omega
+    rf = r * (1000.0 / 917.0) ** (1.0 / 3.0)
+    rho = U[0]
+    for k in range(4):
+        assert Q[0, 9 + k] == pytest.approx(rho * Nf * rf**k / 1e-6**k, rel=1e-12)
+    # Koop: 10^J in cm^-3 s^-1, clamped range of Delta a_w
+    daw = 1 - math.exp(O.ln_psat_i(T) - O.ln_psat_l(T))
+    assert aux[0, 9] == pytest.approx(O.koop_log10J(daw), rel=1e-14)
+    assert O.koop_log10J(0.2) == -math.inf
+    assert O.koop_log10J(0.5) == O.koop_log10J(0.34)
+
+
+def test_koop_threshold_temperature():
+    """The Koop fit with a_w = 1 and Sonntag's a_w^ice gives J = 1e9..1e12 cm^-3 s^-1 near
+    235-237 K, the homogeneous freezing limit of pure water droplets."""
+    daw = 1 - math.exp(O.ln_psat_i(236.0) - O.ln_psat_l(236.0))
+    assert 8.0 < O.koop_log10J(daw) < 13.0
