@@ -1,0 +1,262 @@
+"""Benchmark of the contrail finite-volume step on GB300.
+
+Workloads (synthetic plumes shaped like the paper's turbofan exhaust, Sec. 4.1):
+  fp64  -- axisymmetric coaxial plume, 1024 x 256 cells, plain FP64 method (default)
+  fp32  -- the same plume on 4096 x 1024 cells, FP32 transport with FP64 islands
+
+One benchmark step = one explicit SSP-RK2 step (two fused stage launches) over the whole
+grid.  `value` is cell-steps per second (whole job) with the state resident in HBM; L2 is
+flushed between timed steps (512 MB write).  `e2e` is the same metric through the C ABI's
+host-buffer entry point (state host->device, one step, state device->host each step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload fp64|fp32] [--impl reference]
+
+With --impl reference the CPU oracle (the plain FP64 C implementation the GPU path is
+checked against) is timed on the host cores for the same workload and metric.
+Multi-GPU: one process per GPU (torchrun); each rank advances its own plume replica
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-steps/s: plain FP64 vs FP32+MLP-source at stated error; % HBM peak"
+UNIT = "Gcell-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _workload(name):
+    from synth import cases
+    if name == "fp64":
+        c, uf = cases.plume_case()
+        return c, uf, "axisymmetric coaxial plume 1024x256, FP64 plain method", 0
+    c, uf = cases.plume_case_mixed_precision()
+    return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 transport + FP64 islands", 1
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            sm = [float(r[0]) for r in rows]
+            mx = [float(r[1]) for r in rows]
+            names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+            reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].strip() == "Active"})
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": reasons,
+                    "samples": len(rows)}
+        except Exception as e:  # noqa: BLE001
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
+
+
+def run_cuda(args):
+    import torch
+    import paper_2504_20742_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    c, uf, desc, prec = _workload(args.workload)
+    cells = int(c["nx"]) * int(c["nr"])
+    cfl = 0.5
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        s = P.Solver(c, uf, precision=prec, device=dev, stream=stream)
+        s.init_state(cfl)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            s.step(1, cfl)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with Clocks(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.fill_(float(k))              # L2 flush between timed steps (not timed)
+                starts[k].record(stream)
+                s.step(1, cfl)
+                ends[k].record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        step_ms = float(np.sum(ms)) / args.steps
+        d = s.diagnostics()
+        # end to end through the host-buffer entry point (pinned memory)
+        host_in = s.U.detach().cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        P.ct_step_host(c, prec, host_in, host_out, s.U, s.U1, s.work, 1, cfl, stream)   # warm
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            P.ct_step_host(c, prec, host_in, host_out, s.U, s.U1, s.work, 1, cfl, stream)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ms_t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    step_ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * cells / (step_ms * 1e-3) / 1e9
+    peaks, peak_kind = _peaks()
+    launch_ms = step_ms / 2.0     # two launches of the fused stage kernel per step
+    elem = 8 if prec == 0 else 4
+    alg_bytes = cells * 14 * elem * 2.5          # stage 1: read U, write U1; stage 2: read U1, U, write U
+    bw = alg_bytes / (launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": None,
+            "kernel": "ct::k_stage", "peak_source": peak_kind,
+            "note": "algorithmic bytes 2.5*14*w per cell per launch (mean of the two stages)"}
+    bytes_state = cells * 14 * elem
+    line = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
+        "data": "synthetic", "impl": "cuda",
+        "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
+                "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": round(wall, 3),
+        "diag": {"dt": d[0], "active_cells": d[7], "nonfinite": d[8]},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(c, uf, args.cpu_seconds)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(c, uf, target_s=12.0):
+    """The oracle as it stands (plain C, FP64, OpenMP over rows) on the host cores, on a
+    bounded sample of the workload: whole-grid steps until about target_s of CPU time."""
+    import oracle as O
+    o = O.Oracle(c, uf)
+    U = o.init_state()
+    t0 = time.perf_counter()
+    o.step(U, 1, 0.5)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(U, n, 0.5)
+    dt = time.perf_counter() - t0
+    cells = int(c["nx"]) * (int(c["nr"]) if c["geom"] == 1 else 1)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(cells * n / dt / 1e9, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} whole-grid steps of the same workload after 1 warm-up step ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c, uf, desc, prec = _workload(args.workload)
+    import oracle as O
+    o = O.Oracle(c, uf)
+    U = o.init_state()
+    cells = int(c["nx"]) * int(c["nr"])
+    for _ in range(args.warmup):
+        o.step(U, 1, 0.5)
+    # bounded sample: at most ~60 s of oracle time in total
+    t0 = time.perf_counter()
+    o.step(U, 1, 0.5)
+    per = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(60.0 / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(U, steps, 0.5)
+    dt = time.perf_counter() - t0
+    value = cells * steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": round(value, 7), "unit": UNIT, "n_gpus": 0, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": desc, "cells": cells},
+            "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} whole-grid steps (of {args.steps} requested)"},
+            "e2e": {"value": round(value, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
+    ap.add_argument("--workload", default="fp64", choices=("fp64", "fp32"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

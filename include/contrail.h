@@ -1,0 +1,152 @@
+/*
+ * contrail.h -- C ABI of the GB300 contrail finite-volume library.
+ *
+ * The library advances the explicit finite-volume time step of the paper "Non-Equilibrium
+ * Phase Changes in Aircraft Exhaust" (Tegethoff & Wheeler, arXiv 2504.20742): the
+ * compressible multi-component axisymmetric (or quasi-1D nozzle) flow of Sec. 3.1,
+ * Eqs. (22)-(26), with moment transport of droplets, ice and soot, coupled to the
+ * per-cell non-equilibrium phase-change sources of Sec. 2.2, Eqs. (1)-(21), integrated by
+ * the second-order explicit Runge-Kutta scheme with a global CFL number and sources in
+ * every stage (Sec. 3.2).
+ *
+ * Conventions
+ *   - Every call returns ct_status; none aborts.  On error, ct_last_error() returns a
+ *     thread-local message.  CT_ERR_CUDA also reports asynchronous launch errors seen at
+ *     the call.
+ *   - Device pointers are allocated by the caller (e.g. by PyTorch) and borrowed for
+ *     the duration of the call and of the work it enqueues; the library allocates no
+ *     device memory.  Host pointers are borrowed for the duration of the call only.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device work is
+ *     stream-ordered; calls that return host data synchronise that stream.
+ *   - State layout: structure of arrays, U[f*N + j*nx + i], N = nx*nr (nr = 1 for the
+ *     nozzle), 14 fields f:
+ *        0 rho, 1 rho*u, 2 rho*v, 3 rho*E, 4 rho*Y_v,
+ *        5..8  rho*mu_k(liquid)/(1 um)^k, 9..12 rho*mu_k(ice)/(1 um)^k, 13 rho*n_soot
+ *     in SI units; mu_k are specific moments (per kg of mixture, Eq. (26)).
+ *     Element type: double for CT_FP64, float for CT_FP32 and CT_FP32_MLP.
+ */
+#ifndef CONTRAIL_H
+#define CONTRAIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CT_NFIELDS 14
+#define CT_NDIAG 32
+#define CT_NAUX 11
+
+typedef enum {
+  CT_OK = 0,
+  CT_ERR_ARG = 1,        /* invalid argument or size */
+  CT_ERR_CUDA = 2,       /* a CUDA runtime call or launch failed */
+  CT_ERR_NONFINITE = 3,  /* the last step produced a non-finite value */
+  CT_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+  CT_ERR_STATE = 5,      /* call out of order (e.g. step before setup) */
+  CT_ERR_SIZE = 6        /* workspace or scratch too small */
+} ct_status;
+
+typedef enum { CT_FP64 = 0, CT_FP32 = 1, CT_FP32_MLP = 2 } ct_precision;
+
+/* One plume or nozzle case.  Geometry and boundary conditions follow Sec. 4.1 of the
+ * paper, reduced to a single-velocity mixture: geom 0 is the quasi-1D nozzle with area
+ * law A/A_t = 1 + area_a (x/x_throat - 1)^2; geom 1 the axisymmetric domain [0,lx]x[0,lr]
+ * with a core (r < d_core/2), bypass (r < d_fan/2) and ambient coflow inflow profile at
+ * ambient static pressure, an outflow at x = lx, a far field at r = lr and the axis at
+ * r = 0.  All quantities SI. */
+typedef struct {
+  int32_t geom;          /* 0 quasi-1D nozzle, 1 axisymmetric plume */
+  int32_t nx, nr;        /* cells (nr ignored for geom 0) */
+  int32_t bc_xlo;        /* 0 inflow profile (plume) / total-condition inlet (nozzle), 1 wall */
+  int32_t bc_xhi;        /* 0 outflow (zero gradient), 1 wall */
+  int32_t bc_rhi;        /* 0 far field (ambient), 1 wall, 2 outflow */
+  int32_t phase_change;  /* 0: all phase-change sources off */
+  int32_t freezing;      /* 0: no freezing */
+  double lx, lr;
+  double area_a, x_throat;
+  double d_core, d_fan, wall_len;          /* wall_len > 0: duct wall at r = d_fan/2, x < wall_len */
+  double T_amb, p_amb, S_ice_amb, mach_coflow;
+  double T_core, u_core, Yv_core, T_byp, u_byp;
+  double n_soot, soot_rm, soot_sigma;      /* exit soot per m^3; lognormal median, sigma_g */
+  double p0, T0, Yv_inlet;                 /* nozzle inlet total conditions */
+  double seed_l_n, seed_l_r, seed_s_n, seed_s_r; /* initial monodisperse populations in the core */
+  double mix_width;                        /* > 0: core blends into ambient over this width */
+} ct_case;
+
+/* Diagnostics record of the last completed step (CT_NDIAG doubles):
+ *   0 dt of the step, 1 total mass, 2 total water (vapour + liquid + ice), 3 total energy
+ *   (volume integrals per radian for geom 1, per unit throat area for geom 0),
+ *   4..6 mass, water and energy that entered through the boundary during the step
+ *   (RK2 rule), 7 active cells in stage 2, 8 non-finite values, 9..22 max-norm of
+ *   (U^{n+1}-U^n)/dt per field, 23 max log10 J_hom, 24 max log10 J_het (m^-3 s^-1),
+ *   25 dt of the next step, 26 surrogate fallback cells (CT_FP32_MLP), 27 steps taken. */
+
+/* Bytes of device workspace needed by a case at a precision (boundary states, reduction
+ * partials, time step and diagnostics).  Returns 0 for an invalid case. */
+size_t ct_workspace_bytes(const ct_case *c, int precision);
+
+/* Validate the case and prepare the workspace: inflow profile per row (row velocity
+ * factors ufac_rows_host[nr], host, may be NULL = all 1), ambient state, counters.
+ * Must precede every other call on that workspace.  Enqueued on `stream`. */
+ct_status ct_setup(const ct_case *c, int precision, const double *ufac_rows_host, void *work,
+                   size_t work_bytes, void *stream);
+
+/* Initial state into U (device, CT_NFIELDS*N elements of the precision's type): the plume
+ * inflow profile extended over the domain (with the optional seed populations), or the
+ * isentropic area-Mach solution of the nozzle.  Also computes the first time step for
+ * `cfl`.  Enqueued on `stream`. */
+ct_status ct_init_state(const ct_case *c, int precision, void *work, void *U, double cfl,
+                        void *stream);
+
+/* Load a caller-provided state (device, same layout and type as U) and compute its time
+ * step for `cfl`: use after ct_setup to start from a checkpoint. */
+ct_status ct_load_state(const ct_case *c, int precision, void *work, const void *U_src, void *U,
+                        double cfl, void *stream);
+
+/* Advance U by nsteps explicit SSP-RK2 steps (Sec. 3.2) with the global CFL number `cfl`.
+ * U1 is a stage buffer of the same size.  The time step of each step is the CFL limit
+ * of the state at its start, computed on the device; no host synchronisation happens.
+ * Enqueued on `stream`. */
+ct_status ct_step(const ct_case *c, int precision, void *U, void *U1, void *work, int nsteps,
+                  double cfl, void *stream);
+
+/* End-to-end variant with host buffers: copies U_host_in (pinned or pageable host memory,
+ * state layout, precision's type) to U, computes its time step, advances nsteps and copies
+ * the result to U_host_out; synchronises `stream`.  U, U1 and work (after ct_setup) are
+ * caller-provided device memory. */
+ct_status ct_step_host(const ct_case *c, int precision, const void *U_host_in, void *U_host_out,
+                       void *U, void *U1, void *work, int nsteps, double cfl, void *stream);
+
+/* Copy the diagnostics record of the last step (nout <= CT_NDIAG doubles) to host memory;
+ * synchronises `stream`.  Returns CT_ERR_NONFINITE when that step produced a non-finite
+ * value (the record and the state stay readable). */
+ct_status ct_diagnostics(const void *work, double *host_out, int nout, void *stream);
+
+/* Per-cell derived quantity of state U into out (device, N doubles): which =
+ * 0 T, 1 p, 2 ln S_l, 3 ln S_i, 4 log10 J_hom, 5 log10 J_het,eff, 6 active flag,
+ * 7 r_crit, 8 Kantrowitz phi, 9 G_l(r20), 10 G_s(r20), 11 Koop log10 J_s (cm^-3 s^-1),
+ * 12 per-droplet freezing rate omega.  Non-applicable values are -inf (logs) or 0.
+ * dt enters only the limiters. */
+ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, double dt,
+                     double *out, void *stream);
+
+/* Phase-change source (Sec. 2.2) of n independent cells: U (device, n x CT_NFIELDS
+ * doubles, row-major conserved states) -> Q (device, n x CT_NFIELDS) and aux (device,
+ * n x CT_NAUX: ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s,
+ * Koop log10 J_s, omega), evaluated at the given precision with limiters of step dt. */
+ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int n, double dt,
+                          double *Q, double *aux, void *stream);
+
+/* Thread-local description of the last error. */
+const char *ct_last_error(void);
+
+/* Library version string. */
+const char *ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONTRAIL_H */

@@ -6,7 +6,7 @@
  * shares no code, header, table or constant with the CUDA library: every constant and
  * formula below is written out here a second time, directly from the paper
  * (Tegethoff & Wheeler, "Non-Equilibrium Phase Changes in Aircraft Exhaust", arXiv
- * 2504.20742) and from the readings listed in DESIGN.md ("Readings of the paper").
+ * 2504.20742), with the readings noted at each function where the paper is silent.
  *
  * Equation numbers follow the order of appearance in the paper (its source carries no
  * numbers): Eq. (1) saturation ratio, (3) Kelvin radius and barrier, (4) CNT rate,
@@ -109,7 +109,8 @@ typedef struct {
  * 0 dt, 1 total mass, 2 total water, 3 total energy (all after the step),
  * 4 boundary mass inflow over the step, 5 boundary water inflow, 6 boundary energy inflow,
  * 7 number of active cells in stage 2, 8 non-finite count,
- * 9..22 L2 residual per field, 23 max log10 J_hom over cells, 24 max log10 J_het. */
+ * 9..22 max-norm residual max |U^{n+1}-U^n|/dt per field, 23 max log10 J_hom over cells,
+ * 24 max log10 J_het. */
 
 /* ------------------------------------------------------------------------------------
  * Thermophysical closed forms (Sec. 2.1; readings B, C, E, G).
@@ -360,6 +361,36 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
     double Tsat = or_tsat(pv, 1);
     Gs = or_growth(r20, T, Tsat, lnSi, SIGMA_SV, RHOS, hsg, lam_g, lbar, gam_g, cp_g);
   }
+  /* Stage relaxation limiter (reading J): the vapour-growth exchange relaxes the driving
+   * potential D = Delta T (1 - r_crit/r) of Eq. (16) towards zero at the rate
+   * 1/tau = 4 pi rho_d mu2 (lambda/den) |dD/dY|, with dD/dY from the linearised saturation
+   * curve and the latent heat of reading E.  Over a stage of length dt the exchanged mass
+   * follows the exact exponential solution, i.e. G is scaled by (1 - exp(-x))/x with
+   * x = dt/tau (both phases together), so that no stage overshoots the equilibrium. */
+  double xsum = 0.0;
+  if (present_l) {
+    double r20 = sqrt(ml[2] / ml[0]);
+    double Tsat = or_tsat(pv, 0);
+    double nu = young_nu(Tsat, hfg, gam_g, cp_g);
+    double Kn = lbar / (2.0 * r20);
+    double cond = lam_g / (RHOL * hfg * r20 * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Kn) + 3.78 * (1.0 - nu) * Kn / PR));
+    double dD = Rv * Tsat * Tsat / hfg / w->Yv + (1.0 - Rv * Tsat * Tsat / (hfg * T)) * (hfg - Rv * T) / w->cv;
+    xsum += dt * 4.0 * PI * RHOL * ml[2] * cond * fabs(dD);
+  }
+  if (present_s) {
+    double r20 = sqrt(ms[2] / ms[0]);
+    double Tsat = or_tsat(pv, 1);
+    double nu = young_nu(Tsat, hsg, gam_g, cp_g);
+    double Kn = lbar / (2.0 * r20);
+    double cond = lam_g / (RHOS * hsg * r20 * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Kn) + 3.78 * (1.0 - nu) * Kn / PR));
+    double dD = Rv * Tsat * Tsat / hsg / w->Yv + (1.0 - Rv * Tsat * Tsat / (hsg * T)) * (hsg - Rv * T) / w->cv;
+    xsum += dt * 4.0 * PI * RHOS * ms[2] * cond * fabs(dD);
+  }
+  if (xsum > 0.0) {
+    double theta = -expm1(-xsum) / xsum;
+    Gl *= theta;
+    Gs *= theta;
+  }
   aux[7] = Gl;
   aux[8] = Gs;
 
@@ -375,7 +406,8 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
     if (chi > 1.0) chi = 1.0;
     double omega = Js * (4.0 / 3.0 * PI * rv * rv * rv) + K_IMM * NS_SITE * 4.0 * PI * sp->rp2 * chi;
     aux[10] = omega;
-    Nf = ml[0] * omega;
+    /* freezing over the stage as exact first-order decay of the droplet number (reading J) */
+    Nf = ml[0] * (-expm1(-omega * dt) / dt);
     rf = rv * cbrt(RHOL / RHOS);
   }
 
@@ -960,12 +992,12 @@ int or_step(or_ctx *g, double *U, int nsteps, double cfl, double *diag) {
       for (size_t m = 0; m < NF * N; ++m) nonfinite += !isfinite(U[m]);
       d[8] = nonfinite;
       for (int f = 0; f < NF; ++f) {
-        double s2 = 0.0;
+        double m = 0.0;
         for (size_t n = 0; n < N; ++n) {
-          double r = (U[(size_t)f * N + n] - g->U0[(size_t)f * N + n]) / dt;
-          s2 += r * r;
+          double r = fabs(U[(size_t)f * N + n] - g->U0[(size_t)f * N + n]) / dt;
+          if (r > m) m = r;
         }
-        d[9 + f] = sqrt(s2 / (double)N);
+        d[9 + f] = m;
       }
       double mh = -INFINITY, mt = -INFINITY;
       for (size_t n = 0; n < N; ++n) {

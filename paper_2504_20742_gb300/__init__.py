@@ -1,0 +1,12 @@
+"""GB300-native contrail finite-volume step (arXiv 2504.20742): CUDA library + binding.
+
+The compute path is libcontrail.so (hand-written sm_103a kernels behind the C ABI in
+include/contrail.h); this package only marshals arguments.  Importing the binding fails
+loudly when the library has not been built: there is no CPU fallback.
+"""
+from ._lib import (  # noqa: F401
+    CT_FP64, CT_FP32, CT_FP32_MLP, NF, NDIAG, NAUX, CtCase, ContrailError, lib_path,
+    ct_workspace_bytes, ct_setup, ct_init_state, ct_load_state, ct_step, ct_step_host,
+    ct_diagnostics, ct_derived, ct_source_batch, ct_last_error, ct_version,
+)
+from .solver import Solver  # noqa: F401

@@ -1,0 +1,173 @@
+"""ctypes binding of libcontrail.so: same names as the C ABI of include/contrail.h.
+
+Arguments are marshalled only (torch tensors -> device pointers, dicts -> ct_case); every
+step of the computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libcontrail.so")
+
+CT_FP64, CT_FP32, CT_FP32_MLP = 0, 1, 2
+NF, NDIAG, NAUX = 14, 32, 11
+
+# ct_case fields, in the order of include/contrail.h
+_CASE_FIELDS = (
+    ("geom", "i"), ("nx", "i"), ("nr", "i"), ("bc_xlo", "i"), ("bc_xhi", "i"), ("bc_rhi", "i"),
+    ("phase_change", "i"), ("freezing", "i"), ("lx", "d"), ("lr", "d"), ("area_a", "d"),
+    ("x_throat", "d"), ("d_core", "d"), ("d_fan", "d"), ("wall_len", "d"), ("T_amb", "d"),
+    ("p_amb", "d"), ("S_ice_amb", "d"), ("mach_coflow", "d"), ("T_core", "d"), ("u_core", "d"),
+    ("Yv_core", "d"), ("T_byp", "d"), ("u_byp", "d"), ("n_soot", "d"), ("soot_rm", "d"),
+    ("soot_sigma", "d"), ("p0", "d"), ("T0", "d"), ("Yv_inlet", "d"), ("seed_l_n", "d"),
+    ("seed_l_r", "d"), ("seed_s_n", "d"), ("seed_s_r", "d"), ("mix_width", "d"),
+)
+
+
+class CtCase(C.Structure):
+    _fields_ = [(k, C.c_int32 if t == "i" else C.c_double) for k, t in _CASE_FIELDS]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "CtCase":
+        s = cls()
+        for k, t in _CASE_FIELDS:
+            setattr(s, k, int(d.get(k, 0)) if t == "i" else float(d.get(k, 0.0)))
+        return s
+
+
+class ContrailError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"contrail status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp, _dp, _cp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(CtCase)
+
+_SIGS = {
+    "ct_workspace_bytes": (C.c_size_t, [_cp, C.c_int]),
+    "ct_setup": (C.c_int, [_cp, C.c_int, _dp, _vp, C.c_size_t, _vp]),
+    "ct_init_state": (C.c_int, [_cp, C.c_int, _vp, _vp, C.c_double, _vp]),
+    "ct_load_state": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_double, _vp]),
+    "ct_step": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
+    "ct_step_host": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
+    "ct_diagnostics": (C.c_int, [_vp, _dp, C.c_int, _vp]),
+    "ct_derived": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp]),
+    "ct_source_batch": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "ct_last_error": (C.c_char_p, []),
+    "ct_version": (C.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def exported_symbols():
+    return tuple(_SIGS)
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(
+                f"libcontrail.so not built ({_LIB_PATH}); run paper_2504_20742_gb300.build.build() "
+                "(nvcc, sm_103a). There is no CPU fallback.")
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _case(c) -> CtCase:
+    return c if isinstance(c, CtCase) else CtCase.from_dict(c)
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, numpy array, int address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int):
+    if status != 0:
+        raise ContrailError(status, _L().ct_last_error().decode())
+
+
+def ct_workspace_bytes(case, precision: int) -> int:
+    return _L().ct_workspace_bytes(C.byref(_case(case)), precision)
+
+
+def ct_setup(case, precision, ufac_rows, work, work_bytes, stream=None):
+    u = None
+    if ufac_rows is not None:
+        arr = np.ascontiguousarray(ufac_rows, dtype=np.float64)
+        u = arr.ctypes.data_as(_dp)
+    _check(_L().ct_setup(C.byref(_case(case)), precision, u, _ptr(work), work_bytes, _stream(stream)))
+
+
+def ct_init_state(case, precision, work, U, cfl, stream=None):
+    _check(_L().ct_init_state(C.byref(_case(case)), precision, _ptr(work), _ptr(U), cfl, _stream(stream)))
+
+
+def ct_load_state(case, precision, work, U_src, U, cfl, stream=None):
+    _check(_L().ct_load_state(C.byref(_case(case)), precision, _ptr(work), _ptr(U_src), _ptr(U), cfl,
+                              _stream(stream)))
+
+
+def ct_step(case, precision, U, U1, work, nsteps, cfl, stream=None):
+    _check(_L().ct_step(C.byref(_case(case)), precision, _ptr(U), _ptr(U1), _ptr(work), nsteps, cfl,
+                        _stream(stream)))
+
+
+def ct_step_host(case, precision, U_host_in, U_host_out, U, U1, work, nsteps, cfl, stream=None):
+    _check(_L().ct_step_host(C.byref(_case(case)), precision, _ptr(U_host_in), _ptr(U_host_out), _ptr(U),
+                             _ptr(U1), _ptr(work), nsteps, cfl, _stream(stream)))
+
+
+def ct_diagnostics(work, stream=None, nout: int = NDIAG, raise_nonfinite: bool = False) -> np.ndarray:
+    out = np.zeros(nout)
+    st = _L().ct_diagnostics(_ptr(work), out.ctypes.data_as(_dp), nout, _stream(stream))
+    if st != 0 and (st != 3 or raise_nonfinite):
+        _check(st)
+    return out
+
+
+def ct_derived(case, precision, U, which, dt, out, stream=None):
+    _check(_L().ct_derived(C.byref(_case(case)), precision, _ptr(U), which, dt, _ptr(out), _stream(stream)))
+
+
+def ct_source_batch(case, precision, U, n, dt, Q, aux, stream=None):
+    _check(_L().ct_source_batch(C.byref(_case(case)), precision, _ptr(U), n, dt, _ptr(Q), _ptr(aux),
+                                _stream(stream)))
+
+
+def ct_last_error() -> str:
+    return _L().ct_last_error().decode()
+
+
+def ct_version() -> str:
+    return _L().ct_version().decode()

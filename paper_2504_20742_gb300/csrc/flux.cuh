@@ -1,0 +1,98 @@
+// flux.cuh -- MUSCL/van Leer reconstruction and Roe flux with Harten's entropy fix
+// (Sec. 3.2 of Tegethoff & Wheeler, arXiv 2504.20742; the paper's PGIRoe scheme is not
+// published in detail, so this is Roe's flux for the frozen ideal mixture with formation
+// energies, passive quantities carried by the upwind mass flux).
+#pragma once
+#include "physics.cuh"
+
+namespace ct {
+
+// van Leer limited slope psi(r) (q_i - q_{i-1}), psi(r) = (r+|r|)/(1+|r|), in its
+// harmonic-mean form 2 dm dp/(dm+dp) (zero unless dm and dp share a sign).
+template <class T>
+__device__ __forceinline__ T vl_slope(T dm, T dp) {
+  const bool same = (dm > T(0) && dp > T(0)) || (dm < T(0) && dp < T(0));
+  return same ? T(2) * dm * fdiv(dp, dm + dp) : T(0);
+}
+
+// Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns.
+// Roe flux in direction DIR (0: normal velocity u, 1: normal velocity v) -> F[14].
+template <class T, int DIR>
+__device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
+  // face thermodynamics (frozen composition)
+  T gL, gR, HL, HR, efL, efR, c2L, c2R;
+  {
+    const T* q = qL;
+    const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
+    const T Ya = T(1) - q[4] - Yl - Ys;
+    const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
+    const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
+    const T pr = fdiv(q[3], q[0]);
+    efL = q[4] * T(k::E0V) + Ys * T(k::E0S);
+    const T gm1 = fdiv(Rg, cv);
+    gL = T(1) + gm1;
+    HL = pr * fdiv(cv, Rg) + efL + pr + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
+    c2L = gL * pr;
+  }
+  {
+    const T* q = qR;
+    const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
+    const T Ya = T(1) - q[4] - Yl - Ys;
+    const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
+    const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
+    const T pr = fdiv(q[3], q[0]);
+    efR = q[4] * T(k::E0V) + Ys * T(k::E0S);
+    const T gm1 = fdiv(Rg, cv);
+    gR = T(1) + gm1;
+    HR = pr * fdiv(cv, Rg) + efR + pr + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
+    c2R = gR * pr;
+  }
+  const T unL = DIR == 0 ? qL[1] : qL[2], utL = DIR == 0 ? qL[2] : qL[1];
+  const T unR = DIR == 0 ? qR[1] : qR[2], utR = DIR == 0 ? qR[2] : qR[1];
+  const T mL = qL[0] * unL, mR = qR[0] * unR;
+  // Roe averages
+  const T sL = m_sqrt(qL[0]), sR = m_sqrt(qR[0]);
+  const T isum = frcp(sL + sR);
+  const T wL = sL * isum, wR = sR * isum;
+  const T rt = sL * sR;
+  const T un = wL * unL + wR * unR;
+  const T ut = wL * utL + wR * utR;
+  const T H = wL * HL + wR * HR;
+  const T ef = wL * efL + wR * efR;
+  const T gam = T(0.5) * (gL + gR);
+  const T q2 = un * un + ut * ut;
+  T c2 = (gam - T(1)) * (H - T(0.5) * q2 - ef);
+  const T c2min = T(0.01) * (c2L < c2R ? c2L : c2R);
+  c2 = c2 < c2min ? c2min : c2;
+  const T c = m_sqrt(c2);
+  const T ic2 = frcp(c2);
+  const T dp = qR[3] - qL[3];
+  const T dun = unR - unL;
+  const T a1 = (dp - rt * c * dun) * T(0.5) * ic2;
+  const T a5 = (dp + rt * c * dun) * T(0.5) * ic2;
+  const T a2 = (qR[0] - qL[0]) - dp * ic2;
+  const T a3 = rt * (utR - utL);
+  const T delta = T(0.1) * (m_fabs(un) + c);
+  T l1 = m_fabs(un - c), l5 = m_fabs(un + c);
+  const T l2 = m_fabs(un);
+  if (l1 < delta) l1 = fdiv(l1 * l1 + delta * delta, T(2) * delta);
+  if (l5 < delta) l5 = fdiv(l5 * l5 + delta * delta, T(2) * delta);
+  const T w1 = l1 * a1, w2 = l2 * a2, w3 = l2 * a3, w5 = l5 * a5;
+  const T D0 = w1 + w2 + w5;
+  const T D1 = w1 * (un - c) + w2 * un + w5 * (un + c);
+  const T D2 = (w1 + w2 + w5) * ut + w3;
+  const T D3 = w1 * (H - un * c) + w2 * T(0.5) * q2 + w3 * ut + w5 * (H + un * c);
+  const T fm = T(0.5) * (mL + mR - D0);
+  const T fn = T(0.5) * (mL * unL + qL[3] + mR * unR + qR[3] - D1);
+  const T ft = T(0.5) * (mL * utL + mR * utR - D2);
+  const T fe = T(0.5) * (mL * HL + mR * HR - D3);
+  F[0] = fm;
+  F[1] = DIR == 0 ? fn : ft;
+  F[2] = DIR == 0 ? ft : fn;
+  F[3] = fe;
+  const T* qu = fm >= T(0) ? qL : qR;
+#pragma unroll
+  for (int f = 4; f < NF; ++f) F[f] = fm * qu[f];
+}
+
+}  // namespace ct

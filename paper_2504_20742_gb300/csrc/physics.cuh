@@ -1,0 +1,399 @@
+// physics.cuh -- device thermophysics and phase-change source of the contrail step.
+//
+// Closed forms of Sec. 2.1-2.2 of Tegethoff & Wheeler (arXiv 2504.20742), written for the
+// GPU: templated on the state precision T (double or float) with the FP64 islands the
+// mixed-precision path keeps (ln S, the nucleation exponent and exp(-dG*/kT)).  Moments are
+// handled in scaled radius units (1 um) throughout, so that FP32 stays in range.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ct {
+
+constexpr int NF = 14;
+constexpr int NAUX = 11;
+
+// ---- constants (SI) ------------------------------------------------------------------
+namespace k {
+constexpr double NA = 6.02214076e23;
+constexpr double KB = 1.380649e-23;
+constexpr double RU = 8.314462618;
+constexpr double MW = 0.018015;
+constexpr double RV = RU / MW;                 // vapour gas constant
+constexpr double RA = 287.05;                  // dry-air pseudo-component
+constexpr double CVA = RA / 0.4;               // gamma_air = 1.4
+constexpr double CPA = CVA + RA;
+constexpr double CPV = 1859.0;
+constexpr double CVV = CPV - RV;
+constexpr double CL = 4186.0;
+constexpr double CS = 2100.0;
+constexpr double RHOL = 1000.0;
+constexpr double RHOS = 917.0;
+constexpr double TREF = 273.15;
+constexpr double HLV0 = 2.501e6;               // h_v - h_l at TREF
+constexpr double HSL0 = 3.337e5;               // h_l - h_s at TREF
+constexpr double E0V = HLV0 - (CPV - CL) * TREF;   // vapour formation energy
+constexpr double E0S = (CL - CS) * TREF - HSL0;    // ice formation energy
+constexpr double PI = 3.14159265358979323846;
+constexpr double FOUR_PI_3 = 4.0 * PI / 3.0;
+constexpr double YL3 = FOUR_PI_3 * RHOL * 1e-18;   // Y_l per scaled mu3 (um^3/kg)
+constexpr double YS3 = FOUR_PI_3 * RHOS * 1e-18;
+constexpr double QC = 1.0;                     // condensation coefficient
+constexpr double FTHETA = 0.5;                 // Eq. (9) at theta = 90 deg
+constexpr double ALPHA_Y = 11.0, BETA_Y = 0.0; // Eq. (16)
+constexpr double PR = 0.71;
+constexpr double NS_SITE = 1.0e8;              // Eq. (14)
+constexpr double K_IMM = 1.0;                  // s^-1
+constexpr double SIGMA_SV = 0.106;
+constexpr double MU_MIN = 1.0e-6;
+constexpr double LN100 = 4.605170185988091368;   // hPa -> Pa
+constexpr double RHOL_OVER_RHOS_CBRT = 1.0293037494292043;   // (1000/917)^(1/3)
+}  // namespace k
+
+// ---- precision-dependent arithmetic ------------------------------------------------------
+// The FP64 path keeps IEEE division (parity with the CPU oracle); the FP32 path uses the
+// fast approximate division (2 ulp), whose error is far below the FP32 state's own rounding.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+template <class T>
+__device__ __forceinline__ T frcp(T a) { return fdiv(T(1), a); }
+// Explicit precision overloads: a templated call must never promote float to double (the
+// FP64 pipe of GB300 is a small fraction of its FP32 rate).
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_cbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double m_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
+
+// ---- Sonntag (1994) saturation pressures, ln of p in Pa --------------------------------
+template <class R>
+__device__ __forceinline__ R ln_psat_liq(R T) {
+  return R(-6096.9385) / T + R(16.635794 + k::LN100) + T * (R(-2.711193e-2) + T * R(1.673952e-5)) +
+         R(2.433502) * m_log(T);
+}
+template <class R>
+__device__ __forceinline__ R ln_psat_ice(R T) {
+  return R(-6024.5282) / T + R(24.7219 + k::LN100) + T * (R(1.0613868e-2) + T * R(-1.3198825e-5)) -
+         R(0.49382577) * m_log(T);
+}
+template <class R>
+__device__ __forceinline__ R dln_psat_liq(R T) {
+  R it = R(1) / T;
+  return R(6096.9385) * it * it + R(-2.711193e-2) + R(2.0 * 1.673952e-5) * T + R(2.433502) * it;
+}
+template <class R>
+__device__ __forceinline__ R dln_psat_ice(R T) {
+  R it = R(1) / T;
+  return R(6024.5282) * it * it + R(1.0613868e-2) - R(2.0 * 1.3198825e-5) * T - R(0.49382577) * it;
+}
+
+// Saturation temperature at vapour pressure pv: Newton, Clausius-Clapeyron start, 6 steps.
+template <class R, bool ICE>
+__device__ __forceinline__ R t_sat(R lnpv) {
+  const R h0 = ICE ? R(k::HLV0 + k::HSL0) : R(k::HLV0);
+  R T = R(1) / (R(1.0 / k::TREF) - R(k::RV) * (lnpv - R(6.415424237852311)) / h0);  // ln 611.2
+#pragma unroll
+  for (int it = 0; it < 6; ++it) {
+    R f = (ICE ? ln_psat_ice(T) : ln_psat_liq(T)) - lnpv;
+    R df = ICE ? dln_psat_ice(T) : dln_psat_liq(T);
+    T -= f / df;
+  }
+  return T;
+}
+
+// IAPWS (1994) surface tension of liquid water, N/m.
+template <class R>
+__device__ __forceinline__ R sigma_liq(R T) {
+  R tau = R(1) - T * R(1.0 / 647.096);
+  return R(0.2358) * m_exp(R(1.256) * m_log(tau)) * (R(1) - R(0.625) * tau);
+}
+
+// Koop et al. (2000): log10 J (cm^-3 s^-1) from Delta a_w, clamped to [0.26, 0.34].
+template <class R>
+__device__ __forceinline__ R koop_log10(R daw) {
+  R d = daw > R(0.34) ? R(0.34) : daw;
+  return R(-906.7) + d * (R(8502.0) + d * (R(-26924.0) + d * R(29180.0)));
+}
+
+// ---- primitive recovery (Eq. (23), ideal mixture with formation energies) --------------
+template <class T>
+struct Prim {
+  T rho, u, v, p, Tg, Yv, Yl, Ys, ml[4], ms[4], ns, cv, Rg, c2;
+};
+
+template <class T>
+__device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
+  const T rho = U[0];
+  const T ir = frcp(rho);
+  w.rho = rho;
+  w.u = U[1] * ir;
+  w.v = U[2] * ir;
+  w.Yv = U[4] * ir;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    w.ml[q] = U[5 + q] * ir;
+    w.ms[q] = U[9 + q] * ir;
+  }
+  w.ns = U[13] * ir;
+  w.Yl = T(k::YL3) * w.ml[3];
+  w.Ys = T(k::YS3) * w.ms[3];
+  const T Ya = T(1) - w.Yv - w.Yl - w.Ys;
+  const T e = U[3] * ir - T(0.5) * (w.u * w.u + w.v * w.v);
+  w.cv = Ya * T(k::CVA) + w.Yv * T(k::CVV) + w.Yl * T(k::CL) + w.Ys * T(k::CS);
+  const T icv = frcp(w.cv);
+  w.Tg = (e - w.Yv * T(k::E0V) - w.Ys * T(k::E0S)) * icv;
+  w.Rg = Ya * T(k::RA) + w.Yv * T(k::RV);
+  w.p = rho * w.Rg * w.Tg;
+  w.c2 = (T(1) + w.Rg * icv) * w.p * ir;
+}
+
+// Conserved state from (p, T, u, v, Y_v, scaled moments, soot per kg).
+template <class T>
+__device__ __forceinline__ void prim_to_cons(double p, double Tg, double u, double v, double Yv,
+                                             const double* ml, const double* ms, double ns, T* U) {
+  const double Yl = k::YL3 * ml[3], Ys = k::YS3 * ms[3];
+  const double Ya = 1.0 - Yv - Yl - Ys;
+  const double Rg = Ya * k::RA + Yv * k::RV;
+  const double rho = p / (Rg * Tg);
+  const double cv = Ya * k::CVA + Yv * k::CVV + Yl * k::CL + Ys * k::CS;
+  const double e = cv * Tg + Yv * k::E0V + Ys * k::E0S;
+  U[0] = T(rho);
+  U[1] = T(rho * u);
+  U[2] = T(rho * v);
+  U[3] = T(rho * (e + 0.5 * (u * u + v * v)));
+  U[4] = T(rho * Yv);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    U[5 + q] = T(rho * ml[q]);
+    U[9 + q] = T(rho * ms[q]);
+  }
+  U[13] = T(rho * ns);
+}
+
+// ---- phase-change source (Sec. 2.2; Eqs. (1)-(21)) -------------------------------------
+struct SrcCase {
+  double n_soot_ref;   // exit soot number per m^3 (0: no heterogeneous nucleation)
+  double rp2;          // lognormal soot <r_p^2> (m^2)
+  int phase_change, freezing;
+};
+
+// Young's growth law, Eq. (16), split as G = cond * D: cond = lambda / den (m/s per K) and
+// the driving potential D = Delta T (1 - r_crit/r) (K), with
+// Delta T * r_crit written through Delta T / ln S so that S = 1 is regular.
+template <class T>
+struct Growth {
+  T cond, D;
+};
+template <class T>
+__device__ __forceinline__ Growth<T> young_growth(T r, T Tg, T Tsat, T lnS, T sig, T rho_d, T h, T lam,
+                                                  T lbar, T gam, T cp) {
+  const T Kn = lbar / (T(2) * r);
+  const T ih = T(1) / h;
+  const T nu = T(k::RV) * Tsat * ih *
+               (T(k::ALPHA_Y - 0.5) - T((2.0 - k::QC) / (2.0 * k::QC)) * (gam + T(1)) / (T(2) * gam) * cp * Tsat * ih);
+  const T dT = Tsat - Tg;
+  const T dT_lnS = m_fabs(lnS) < T(1e-8) ? T(k::RV) * Tg * Tsat * ih : dT / lnS;
+  const T dT_rc = dT_lnS * T(2) * sig / (rho_d * T(k::RV) * Tg);
+  const T den = rho_d * h * r * (T(1) / (T(1) + T(2 * k::BETA_Y) * Kn) + T(3.78) * (T(1) - nu) * Kn * T(1.0 / k::PR));
+  Growth<T> g;
+  g.cond = lam / den;
+  g.D = dT - dT_rc / r;
+  return g;
+}
+
+// |dD/dY| of the linearised vapour-condensate exchange at fixed density and energy:
+// saturation curve slope R_v Tsat^2/h per ln p_v, latent heating (h - R_v T)/c_v per unit Y.
+template <class T>
+__device__ __forceinline__ T relax_slope(T Tsat, T Tg, T h, T Yv, T cv) {
+  const T a = T(k::RV) * Tsat * Tsat / h;
+  return m_fabs(a / Yv + (T(1) - a / Tg) * (h - T(k::RV) * Tg) / cv);
+}
+
+// Source of one cell.  w: primitives of the stage input; the limiters keep the
+// flux-updated state A + dt Q non-negative; Q gets fields 4..12.
+// aux (optional): ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s,
+// Koop log10 J, omega.  Returns true for an active cell.
+// U: conserved stage input of the cell; acc (may be null): its flux-only residual, so that
+// the limiters act on A = U + dt acc.
+template <class T>
+__device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
+                                             T* Q, double* lnJ2, double* aux) {
+#pragma unroll
+  for (int f = 4; f < 13; ++f) Q[f] = T(0);
+  if (aux) {
+#pragma unroll
+    for (int a = 0; a < NAUX; ++a) aux[a] = 0.0;
+    aux[2] = aux[3] = aux[9] = -INFINITY;
+  }
+  lnJ2[0] = lnJ2[1] = -INFINITY;
+  if (!sc.phase_change) return false;
+  const T Tg = w.Tg, rho = w.rho;
+  const bool pres_l = w.ml[0] > T(k::MU_MIN) && w.ml[1] > T(0) && w.ml[2] > T(0) && w.ml[3] > T(0);
+  const bool pres_s = w.ms[0] > T(k::MU_MIN) && w.ms[1] > T(0) && w.ms[2] > T(0) && w.ms[3] > T(0);
+  if (sizeof(T) == 4 && !aux && !pres_l && !pres_s) {
+    // FP32 screen: a cell clearly below liquid saturation with no population has an exactly
+    // zero source; only cells near or above saturation pay for the FP64 island below.
+    float pvf = float(rho) * float(w.Yv) * float(k::RV) * float(Tg);
+    pvf = pvf < 1e-30f ? 1e-30f : pvf;
+    if (logf(pvf) - ln_psat_liq<float>(float(Tg)) < -1e-3f) return false;
+  }
+  // Eq. (1) in FP64: ln S = ln p_v - ln p_sat(T)
+  double pv = double(rho) * double(w.Yv) * k::RV * double(Tg);
+  pv = pv < 1e-30 ? 1e-30 : pv;
+  const double lnpv = m_log(pv);
+  const double lnpsl = ln_psat_liq<double>(double(Tg)), lnpsi = ln_psat_ice<double>(double(Tg));
+  const double lnSl = lnpv - lnpsl, lnSi = lnpv - lnpsi;
+  if (aux) { aux[0] = lnSl; aux[1] = lnSi; }
+  const bool active = lnSl > 0.0 || pres_l || pres_s;
+  if (aux) aux[4] = active ? 1.0 : 0.0;
+  if (!active) return false;
+
+  // gas-phase properties (reading G)
+  const T Yg = T(1) - w.Yl - w.Ys;
+  const T Ya = Yg - w.Yv;
+  const T iYg = T(1) / Yg;
+  const T cp_g = (Ya * T(k::CPA) + w.Yv * T(k::CPV)) * iYg;
+  const T cv_g = (Ya * T(k::CVA) + w.Yv * T(k::CVV)) * iYg;
+  const T gam_g = cp_g / cv_g;
+  const T Rg_g = (Ya * T(k::RA) + w.Yv * T(k::RV)) * iYg;
+  const T mu_g = T(1.716e-5 * (273.15 + 110.4)) * Tg * m_sqrt(Tg * T(1.0 / 273.15)) * T(1.0 / 273.15) / (Tg + T(110.4));
+  const T lam = mu_g * cp_g * T(1.0 / k::PR);
+  const T lbar = T(1.5) * mu_g * m_sqrt(Rg_g * Tg) / w.p;
+  const T hfg = T(k::CPV - k::CL) * Tg + T(k::E0V);
+  const T hsg = T(k::CPV - k::CS) * Tg + T(k::E0V - k::E0S);
+  const T lnpv_t = T(lnpv);
+
+  // nucleation, Eqs. (3)-(6), (10); soot-gated heterogeneous rate
+  T Jeff = T(0), rc_um = T(0);
+  T Tsat_l = T(0);
+  bool have_tsat_l = false;
+  if (lnSl > 0.0) {
+    const T sig = sigma_liq(Tg);
+    const double sigd = double(sig);
+    const double rc = 2.0 * sigd / (k::RHOL * k::RV * double(Tg) * lnSl);
+    const double dGkT = k::FOUR_PI_3 * sigd * rc * rc / (k::KB * double(Tg));
+    const double rhov = double(rho) * double(w.Yv);
+    // ln A = ln q_c + 1/2 ln(2 sigma N_A^3 / (pi M^3)) + 2 ln rho_v - ln rho_l
+    const double lnA = 0.5 * m_log(2.0 * sigd) + 0.5 * m_log(k::NA * k::NA * k::NA / (k::PI * k::MW * k::MW * k::MW)) +
+                       2.0 * m_log(rhov) - m_log(k::RHOL);
+    const double lnJhom = lnA - dGkT;
+    const double lnJhet = lnA - k::FTHETA * dGkT;
+    double Jsum = m_exp(lnJhom);
+    lnJ2[0] = lnJhom;
+    const double nsv = double(rho) * double(w.ns);
+    if (sc.n_soot_ref > 0.0 && nsv > 0.0) {
+      const double gate = nsv / sc.n_soot_ref;
+      Jsum += m_exp(lnJhet) * gate;
+      lnJ2[1] = lnJhet + m_log(gate);
+    }
+    // Eq. (5) with alpha_crit from Young's law at r_crit (reading F)
+    Tsat_l = t_sat<T, false>(lnpv_t);
+    have_tsat_l = true;
+    const T rcT = T(rc);
+    const T ih = T(1) / hfg;
+    const T nu = T(k::RV) * Tsat_l * ih *
+                 (T(k::ALPHA_Y - 0.5) - T(0.5) * (gam_g + T(1)) / (T(2) * gam_g) * cp_g * Tsat_l * ih);
+    const T Knc = lbar / (T(2) * rcT);
+    const T alpha_c = lam / (rcT * (T(1) + T(3.78) * (T(1) - nu) * Knc * T(1.0 / k::PR)));
+    const T phi = T(k::QC) * T(rhov) / alpha_c * m_sqrt(T(k::RV) * Tg * T(1.0 / (2.0 * k::PI))) *
+                  (hfg * hfg / (T(k::RV) * Tg * Tg) - hfg / Tg);
+    Jeff = T(Jsum) / (T(1) + phi);
+    rc_um = T(rc * 1e6);
+    if (aux) { aux[2] = lnJ2[0]; aux[3] = lnJ2[1]; aux[5] = rc; aux[6] = double(phi); }
+  }
+
+  // growth at r20, Eqs. (16), (21) -- G in um/s; the stage relaxation limiter scales both
+  // phases by (1 - exp(-x))/x, x = dt/tau of the linearised exchange (reading J)
+  T Gl = T(0), Gs = T(0), xsum = T(0);
+  if (pres_l) {
+    if (!have_tsat_l) Tsat_l = t_sat<T, false>(lnpv_t);
+    const T r20 = m_sqrt(w.ml[2] / w.ml[0]) * T(1e-6);
+    const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), sigma_liq(Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
+    Gl = g.cond * g.D * T(1e6);
+    xsum += dt * T(4.0 * k::PI * k::RHOL * 1e-12) * w.ml[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
+  }
+  if (pres_s) {
+    const T Tsat_i = t_sat<T, true>(lnpv_t);
+    const T r20 = m_sqrt(w.ms[2] / w.ms[0]) * T(1e-6);
+    const Growth<T> g = young_growth<T>(r20, Tg, Tsat_i, T(lnSi), T(k::SIGMA_SV), T(k::RHOS), hsg, lam, lbar, gam_g, cp_g);
+    Gs = g.cond * g.D * T(1e6);
+    xsum += dt * T(4.0 * k::PI * k::RHOS * 1e-12) * w.ms[2] * g.cond * relax_slope(Tsat_i, Tg, hsg, w.Yv, w.cv);
+  }
+  if (xsum > T(0)) {
+    const T theta = -m_expm1(-xsum) / xsum;
+    Gl *= theta;
+    Gs *= theta;
+  }
+  if (aux) { aux[7] = double(Gl) * 1e-6; aux[8] = double(Gs) * 1e-6; }
+
+  // freezing, Eqs. (12)-(15) (reading H)
+  T Nf = T(0), rv = T(0), rf = T(0);
+  if (sc.freezing && pres_l && Tg < T(k::TREF)) {
+    rv = m_cbrt(w.ml[3] / w.ml[0]);   // um
+    const T daw = T(1) - T(m_exp(lnpsi - lnpsl));
+    T Js = T(0);
+    if (daw >= T(0.26)) {
+      const T l10 = koop_log10(daw);
+      Js = m_exp(l10 * T(2.302585092994045684)) * T(1e6);
+      if (aux) aux[9] = double(l10);
+    }
+    T chi = w.ns / w.ml[0];
+    chi = chi > T(1) ? T(1) : chi;
+    const T rvm = rv * T(1e-6);
+    const T omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
+    if (aux) aux[10] = double(omega);
+    Nf = w.ml[0] * (-m_expm1(-omega * dt) / dt);   // first-order decay over the stage
+    rf = rv * T(k::RHOL_OVER_RHOS_CBRT);
+  }
+
+  // moment sources (per kg, scaled units), Eq. (21)
+  const T jr = Jeff / rho;
+  T dml[4], dms[4];
+  {
+    T rck = T(1), rvk = T(1), rfk = T(1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dml[q] = (q ? T(q) * w.ml[q - 1] * Gl : T(0)) + jr * rck - Nf * rvk;
+      dms[q] = (q ? T(q) * w.ms[q - 1] * Gs : T(0)) + Nf * rfk;
+      rck *= rc_um;
+      rvk *= rv;
+      rfk *= rf;
+    }
+  }
+  // limiters on the flux-updated stage state (reading J)
+  auto A = [&](int f) { return acc ? U[f] + dt * acc[f] : U[f]; };
+  const T ir = T(1) / rho;
+  const T idt = T(1) / dt;
+  if (A(8) * ir + dt * dml[3] <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dml[q] = -(A(5 + q) * ir) * idt;
+  }
+  if (A(12) * ir + dt * dms[3] <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dms[q] = -(A(9 + q) * ir) * idt;
+  }
+  T dYv = -(T(k::YL3) * dml[3] + T(k::YS3) * dms[3]);
+  const T av = A(4) * ir;
+  if (av + dt * dYv < T(0)) {
+    const T th = av > T(0) ? av / (-dt * dYv) : T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { dml[q] *= th; dms[q] *= th; }
+    dYv *= th;
+  }
+  Q[4] = rho * dYv;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Q[5 + q] = rho * dml[q];
+    Q[9 + q] = rho * dms[q];
+  }
+  return true;
+}
+
+}  // namespace ct

@@ -12,6 +12,7 @@ from .cases import (  # noqa: F401
     plume_case_mixed_precision,
     batch_cases,
     mixing_layer_case,
+    freezing_case,
     closed_box_case,
     shock_tube_case,
 )

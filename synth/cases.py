@@ -133,6 +133,17 @@ def mixing_layer_case(nx: int = 96, nr: int = 40, seeded: bool = True, freezing:
     return c, ufac
 
 
+def freezing_case(nx: int = 96, nr: int = 40) -> tuple[dict, np.ndarray]:
+    """Cold core (232 K, vapour at about 0.97 of liquid saturation, 1.45 of ice saturation)
+    carrying seeded droplets (0.2 um, 1e10/kg) and crystals (1 um, 1e8/kg) next to
+    ice-supersaturated ambient air: homogeneous and immersion freezing, ice deposition
+    growth and droplet evaporation run everywhere in the core, without nucleation bursts."""
+    c, ufac = mixing_layer_case(nx=nx, nr=nr, seeded=True)
+    c.update(mix_width=0.0, T_core=232.0, Yv_core=4.2468e-4, T_amb=225.0, S_ice_amb=1.3,
+             u_core=250.0, mach_coflow=0.6)
+    return c, ufac
+
+
 def closed_box_case(geom: int = 1, nx: int = 48, nr: int = 24) -> tuple[dict, np.ndarray]:
     """Mixing-layer physics at rest with reflective walls on every side (the axis is a
     mirror): a closed box, whose total mass, water and energy stay constant.  For geom 0

@@ -1,0 +1,63 @@
+"""Host-side tests of the CUDA library (no GPU needed): it loads, exports every entry point
+declared in include/contrail.h, and rejects invalid arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2504_20742_gb300 import build
+    build.build()
+    import paper_2504_20742_gb300 as P
+    return P
+
+
+def test_exports_every_declared_symbol(P):
+    hdr = open(os.path.join(ROOT, "include", "contrail.h")).read()
+    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(ct_[a-z_0-9]+)\s*\(", hdr, re.M))
+    assert {"ct_setup", "ct_step", "ct_init_state", "ct_diagnostics"} <= names
+    lib = ctypes.CDLL(P.lib_path())
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert P.ct_version().startswith("contrail-gb300")
+
+
+def test_workspace_size_and_case_validation(P):
+    from synth import cases
+    c, _ = cases.plume_case()
+    assert P.ct_workspace_bytes(c, P.CT_FP64) > 256 * 14 * 8
+    bad = dict(c, nx=1)
+    assert P.ct_workspace_bytes(bad, P.CT_FP64) == 0
+    assert "nx" in P.ct_last_error()
+    assert P.ct_workspace_bytes(c, 7) == 0
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(P):
+    from synth import cases
+    c, _ = cases.plume_case(nx=64, nr=16)
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_step(c, P.CT_FP64, 0x1000, 0x1000, 0x2000, 1, 0.5)
+    assert e.value.status == 1
+    with pytest.raises(P.ContrailError):
+        P.ct_step(c, P.CT_FP64, 0x1000, 0x3000, 0x2000, -1, 0.5)
+    with pytest.raises(P.ContrailError):
+        P.ct_step(c, P.CT_FP64, 0x1000, 0x3000, 0x2000, 1, 1.5)
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_setup(c, P.CT_FP64, None, 0x1000, 16, None)
+    assert e.value.status == 6
+    with pytest.raises(P.ContrailError):
+        P.ct_setup(c, P.CT_FP64, None, 0x1001, 1 << 30, None)
+    with pytest.raises(P.ContrailError):
+        P.ct_derived(c, P.CT_FP64, 0x1000, 99, 1e-6, 0x2000)
+
+
+def test_binding_has_no_oracle_dependency():
+    src = open(os.path.join(ROOT, "paper_2504_20742_gb300", "_lib.py")).read()
+    src += open(os.path.join(ROOT, "paper_2504_20742_gb300", "solver.py")).read()
+    assert "oracle" not in src and "synth" not in src

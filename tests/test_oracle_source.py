@@ -251,7 +251,8 @@ def test_freezing_transfers_mass_without_loss():
     Q, aux = O.source_batch(_case(), U, 1e-12)
     omega = aux[0, 10]
     assert omega > 0
-    Nf = n * omega
+    dt = 1e-12
+    Nf = n * (-math.expm1(-omega * dt) / dt)     # first-order decay over the stage
     rf = r * (1000.0 / 917.0) ** (1.0 / 3.0)
     rho = U[0]
     for k in range(4):
@@ -268,3 +269,34 @@ def test_koop_threshold_temperature():
     235-237 K, the homogeneous freezing limit of pure water droplets."""
     daw = 1 - math.exp(O.ln_psat_i(236.0) - O.ln_psat_l(236.0))
     assert 8.0 < O.koop_log10J(daw) < 13.0
+
+
+@pytest.mark.parametrize("S", [1.05, 1.5, 0.7])
+@pytest.mark.parametrize("dt", [1e-6, 1e-4, 1e-2])
+def test_growth_stage_never_overshoots_equilibrium(S, dt):
+    """Reading J: over one stage the growth exchange follows the exponential solution of the
+    linearised relaxation, so a dense supersaturated (subsaturated) population condenses
+    (evaporates) towards saturation without crossing it, for any stage length."""
+    T, p = 230.0, 24e3
+    Yv = _yv_for_S(S, T, p)
+    r, n = 5e-7, 1e10
+    ml = tuple(n * (r / 1e-6) ** k for k in range(4))
+    U = _state(p, T, Yv, ml=ml)
+    c = _case(freezing=0)
+    Q, aux = O.source_batch(c, U, dt)
+    lnS0 = aux[0, 0]
+    U1 = U + dt * Q
+    _, aux1 = O.source_batch(c, U1, dt)
+    lnS1 = aux1[0, 0]
+    kelvin = 2 * O.sigma_lg(T) / (1000.0 * O.const("R_v") * T * r)   # equilibrium ln S of the drops
+    assert abs(lnS1 - kelvin) <= abs(lnS0 - kelvin) * (1 + 1e-9)
+    assert (lnS1 - kelvin) * (lnS0 - kelvin) >= -1e-3 * abs(lnS0 - kelvin) ** 2
+
+
+def test_growth_limiter_reduces_to_explicit_rate_for_short_stages():
+    T, p = 230.0, 24e3
+    U = _state(p, T, _yv_for_S(1.3, T, p), ml=tuple(1e8 * (1e-7 / 1e-6) ** k for k in range(4)))
+    c = _case(freezing=0)
+    _, a1 = O.source_batch(c, U, 1e-14)
+    _, a2 = O.source_batch(c, U, 1e-13)
+    assert a1[0, 7] == pytest.approx(a2[0, 7], rel=1e-9)
