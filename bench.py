@@ -52,6 +52,32 @@ def _workload(name):
     return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 transport + FP64 islands", 1
 
 
+# Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/):
+# FP64 arithmetic per cell-stage (mean of the two stages: 1283 and 1472 flops) and DRAM
+# bytes per cell per launch (mean of the two stages).  Set to None when the kernel changes.
+FP64_FLOPS_PER_CELL_STAGE = 1377.7
+FP64_TRAFFIC_PER_CELL_LAUNCH = 171.7
+FP32_TRAFFIC_PER_CELL_LAUNCH = 134.2
+
+
+def measure_dgemm_tflops(dev) -> float:
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn_like(a)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize(dev)
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * 4096**3 / best / 1e12
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -159,14 +185,30 @@ def run_cuda(args):
         return
     value = world * cells / (step_ms * 1e-3) / 1e9
     peaks, peak_kind = _peaks()
-    launch_ms = step_ms / 2.0     # two launches of the fused stage kernel per step
+    # mean duration of one fused stage launch: CUDA events on the launching stream around
+    # each timed step (two launches of k_stage per step)
+    launch_ms_ev = step_ms / 2.0
     elem = 8 if prec == 0 else 4
-    alg_bytes = cells * 14 * elem * 2.5          # stage 1: read U, write U1; stage 2: read U1, U, write U
-    bw = alg_bytes / (launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": None,
-            "kernel": "ct::k_stage", "peak_source": peak_kind,
-            "note": "algorithmic bytes 2.5*14*w per cell per launch (mean of the two stages)"}
+    if prec == 0:
+        # FP64 path: bound by the FP64 pipe.  Algorithmic flops per cell and stage are the
+        # kernel's FP64 arithmetic (2 DFMA + DADD + DMUL), counted once with ncu
+        # (profiles/k_stage_fp64_plume1024x256.md); the peak is cuBLAS DGEMM measured here.
+        fpk = measure_dgemm_tflops(dev)
+        flops = cells * FP64_FLOPS_PER_CELL_STAGE
+        ach = flops / (launch_ms_ev * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
+                "frac": round(ach / fpk, 4), "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells,
+                "kernel": "ct::k_stage<double>",
+                "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
+                "note": f"{FP64_FLOPS_PER_CELL_STAGE} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"}
+    else:
+        alg_bytes = cells * 14 * elem * 2.5      # stage 1: read U, write U1; stage 2: read U1, U, write U
+        bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells,
+                "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
+                "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
+                        f"mean launch {launch_ms_ev:.4f} ms"}
     bytes_state = cells * 14 * elem
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -37,18 +37,45 @@ def _run_pair(P, c, uf, nsteps, precision=0, cfl=0.5):
     return s, o, U0g, s.state64(), Uo, np.array(diags), do
 
 
-# Well-conditioned cases: 100 steps.  The nucleating mixing layers amplify a 1e-14
-# perturbation of the oracle's own input to O(1) within about 50 steps (pinned in
-# test_oracle_solver.py) and to 1e-9 within a few steps, so their trajectories are compared
-# over 3 steps; their sources are compared pointwise in test_source_batch_parity.
+# Well-conditioned cases: 100 steps at 1e-9.  The nucleating mixing layers amplify a
+# rounding-level perturbation of the oracle's own input to O(1) within about 50 steps
+# (pinned in test_oracle_solver.py); they are checked by shadowing in
+# test_fp64_shadowing_of_chaotic_cases and pointwise in test_source_batch_parity.
 CASES = {
     "nozzle400": (lambda: (cases.nozzle_case(nx=400), None), 100),
     "freezing96x40": (lambda: cases.freezing_case(), 100),
     "freezing_ragged_77x29": (lambda: cases.freezing_case(nx=77, nr=29), 100),
-    "mixing96x40": (lambda: cases.mixing_layer_case(), 3),
-    "mixing_ragged_77x29": (lambda: cases.mixing_layer_case(nx=77, nr=29), 3),
-    "closed_box": (lambda: cases.closed_box_case(), 3),
+    "mixing96x40_2steps": (lambda: cases.mixing_layer_case(), 2),
+    "closed_box_2steps": (lambda: cases.closed_box_case(), 2),
 }
+
+CHAOTIC = {
+    "mixing96x40": lambda: cases.mixing_layer_case(),
+    "mixing_ragged_77x29": lambda: cases.mixing_layer_case(nx=77, nr=29),
+    "closed_box": lambda: cases.closed_box_case(),
+}
+
+
+@pytest.mark.parametrize("name", list(CHAOTIC))
+def test_fp64_shadowing_of_chaotic_cases(P, name):
+    """GPU and oracle trajectories stay as close as two oracle trajectories whose inputs
+    differ by 1e-13 (relative, random): the GPU path is within the rounding-level
+    uncertainty of the oracle's own trajectory, step by step for 20 steps."""
+    c, uf = CHAOTIC[name]()
+    s = P.Solver(c, uf)
+    s.init_state(0.5)
+    o = O.Oracle(c, uf)
+    Uo = o.init_state()
+    Up = Uo * (1.0 + 1e-13 * np.random.default_rng(3).standard_normal(Uo.shape))
+    worst = 0.0
+    for k in range(20):
+        s.step(1, 0.5)
+        o.step(Uo, 1, 0.5)
+        o.step(Up, 1, 0.5)
+        e_gpu = field_rel_err(s.state64(), Uo).max()
+        e_self = field_rel_err(Up, Uo).max()
+        worst = max(worst, e_gpu / max(e_self, 1e-12))
+        assert e_gpu <= max(1e-9, 10.0 * e_self), (k, e_gpu, e_self)
 
 
 @pytest.mark.parametrize("name", list(CASES))
