@@ -140,6 +140,29 @@ ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, 
 ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int n, double dt,
                           double *Q, double *aux, void *stream);
 
+/* Maximum scratch of ct_step_static, in bytes (4 MiB: about 16,000 tiles of 32x8 cells,
+ * e.g. a 4096 x 1024 plume). */
+#define CT_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* Allocation-free variant of ct_step.  The paper has no counterpart: this serves callers
+ * that cannot allocate device memory (a host framework whose allocator they may not call,
+ * a launcher that owns only the buffers it was handed, a process under a fixed memory
+ * budget).  Instead of a caller workspace, the step's scratch (inflow profile, time step,
+ * reduction partials, diagnostics) lives in one statically allocated device array of
+ * CT_STATIC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ * Arguments: ufac_rows_dev (device, nr doubles of inlet velocity factors, or NULL = all 1);
+ * U (device, in/out state, precision's type); U1 (device, same size, receives the
+ * first-stage state of the last step).  Each call prepares the scratch from the case,
+ * computes the time step of U and advances nsteps SSP-RK2 steps on `stream`,
+ * asynchronously; it calls no cudaMalloc or cudaFree and no allocating library routine.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make it before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams, other threads) race.  Errors: CT_ERR_SIZE when the case needs more scratch than
+ * CT_STATIC_SCRATCH_BYTES; CT_ERR_ARG for invalid arguments (CT_FP32_MLP is rejected). */
+ct_status ct_step_static(const ct_case *c, int precision, const double *ufac_rows_dev, void *U, void *U1,
+                         int nsteps, double cfl, void *stream);
+
 /* Thread-local description of the last error. */
 const char *ct_last_error(void);
 

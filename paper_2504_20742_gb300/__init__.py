@@ -7,6 +7,6 @@ loudly when the library has not been built: there is no CPU fallback.
 from ._lib import (  # noqa: F401
     CT_FP64, CT_FP32, CT_FP32_MLP, NF, NDIAG, NAUX, CtCase, ContrailError, lib_path,
     ct_workspace_bytes, ct_setup, ct_init_state, ct_load_state, ct_step, ct_step_host,
-    ct_diagnostics, ct_derived, ct_source_batch, ct_last_error, ct_version,
+    ct_diagnostics, ct_derived, ct_source_batch, ct_step_static, ct_last_error, ct_version,
 )
 from .solver import Solver  # noqa: F401

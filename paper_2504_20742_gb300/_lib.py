@@ -58,6 +58,7 @@ _SIGS = {
     "ct_diagnostics": (C.c_int, [_vp, _dp, C.c_int, _vp]),
     "ct_derived": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp]),
     "ct_source_batch": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "ct_step_static": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_last_error": (C.c_char_p, []),
     "ct_version": (C.c_char_p, []),
 }
@@ -163,6 +164,12 @@ def ct_derived(case, precision, U, which, dt, out, stream=None):
 def ct_source_batch(case, precision, U, n, dt, Q, aux, stream=None):
     _check(_L().ct_source_batch(C.byref(_case(case)), precision, _ptr(U), n, dt, _ptr(Q), _ptr(aux),
                                 _stream(stream)))
+
+
+def ct_step_static(case, precision, ufac_rows_dev, U, U1, nsteps, cfl, stream=None):
+    """Allocation-free step: scratch in the library's static device array (see contrail.h)."""
+    _check(_L().ct_step_static(C.byref(_case(case)), precision, _ptr(ufac_rows_dev), _ptr(U), _ptr(U1),
+                               nsteps, cfl, _stream(stream)))
 
 
 def ct_last_error() -> str:

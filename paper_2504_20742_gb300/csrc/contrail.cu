@@ -974,6 +974,75 @@ ct_status ct_source_batch(const ct_case* c, int precision, const double* U, int 
   return cuda_check("k_source_batch");
 }
 
+// ---- allocation-free variant of ct_step ----------------------------------------------------
+// Some callers cannot allocate device memory at all: code running inside a host framework
+// whose allocator is reserved or already captured, firmware-style launchers that only own
+// the buffers they were handed, or processes under a memory budget that forbids new
+// allocations.  For them the workspace of ct_step (inflow profile, time step, reduction
+// partials, diagnostics) lives in this file-scope device array instead of caller memory.
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)CT_STATIC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+static void* g_static_ptr[MAX_DEVICES];   // device address of g_static_scratch, per device
+
+__global__ void k_scratch_reset(int nblocks) {
+  // everything of the header that must start at zero for a fresh run
+  WsHeader* h = reinterpret_cast<WsHeader*>(g_static_scratch);
+  if (threadIdx.x == 0) {
+    memset(h, 0, sizeof(WsHeader));
+    h->setup_magic = SETUP_MAGIC;
+    h->nblocks = nblocks;
+  }
+}
+
+static ct_status static_scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_check("cudaGetDevice");
+  if (dev < 0 || dev >= MAX_DEVICES) return fail(CT_ERR_ARG, "device index beyond the static scratch table");
+  if (!g_static_ptr[dev]) {
+    // host code cannot use g_static_scratch's name as a device address: ask the runtime,
+    // with this device current, once per device
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      snprintf(g_err, sizeof(g_err), "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+      return CT_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return CT_OK;
+}
+
+extern "C" ct_status ct_step_static(const ct_case* c, int precision, const double* ufac_rows_dev, void* U, void* U1,
+                                    int nsteps, double cfl, void* stream) {
+  ct_status s = validate(c, precision);
+  if (s != CT_OK) return s;
+  if (!U || !U1) return fail(CT_ERR_ARG, "null state buffer");
+  if (U == U1) return fail(CT_ERR_ARG, "U and U1 must be distinct buffers");
+  if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
+  if (precision == CT_FP32_MLP) return fail(CT_ERR_ARG, "CT_FP32_MLP is not supported by ct_step_static");
+  const size_t need = ws_bytes(c);
+  if (need > STATIC_SCRATCH_BYTES) {
+    snprintf(g_err, sizeof(g_err),
+             "case needs %zu bytes of scratch but the static scratch holds %zu (about %d tiles of %dx%d cells); "
+             "use ct_step with a caller workspace",
+             need, STATIC_SCRATCH_BYTES, (int)((STATIC_SCRATCH_BYTES - HDR_BYTES) / (NPART * sizeof(double))), TX, TY);
+    return CT_ERR_SIZE;
+  }
+  void* work = nullptr;
+  if ((s = static_scratch_address(&work)) != CT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCase d = make_dev(c, work);
+  k_scratch_reset<<<1, 32, 0, st>>>(d.nblocks);
+  if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_rows_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr);
+  if ((s = cuda_check("ct_step_static setup")) != CT_OK) return s;
+  if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
+  return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st);
+}
+
 const char* ct_last_error(void) { return g_err; }
 const char* ct_version(void) { return "contrail-gb300 0.1 (sm_103a)"; }
 
