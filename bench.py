@@ -56,8 +56,8 @@ def _workload(name):
 # FP64 arithmetic per cell-stage (mean of the two stages: 1283 and 1472 flops) and DRAM
 # bytes per cell per launch (mean of the two stages).  Set to None when the kernel changes.
 FP64_FLOPS_PER_CELL_STAGE = 1377.7
-FP64_TRAFFIC_PER_CELL_LAUNCH = 171.7
-FP32_TRAFFIC_PER_CELL_LAUNCH = 134.2
+FP64_TRAFFIC_PER_CELL_LAUNCH = 172.4
+FP32_TRAFFIC_PER_CELL_LAUNCH = 134.3
 
 
 def measure_dgemm_tflops(dev) -> float:
@@ -285,7 +285,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
     ap.add_argument("--workload", default="fp64", choices=("fp64", "fp32"))
