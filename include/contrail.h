@@ -38,6 +38,9 @@ extern "C" {
 #define CT_NFIELDS 14
 #define CT_NDIAG 32
 #define CT_NAUX 11
+#define CT_MLP_IN 16       /* surrogate inputs */
+#define CT_MLP_HIDDEN 128  /* width of its 4 hidden SiLU layers */
+#define CT_MLP_OUT 10      /* surrogate outputs */
 
 typedef enum {
   CT_OK = 0,
@@ -139,6 +142,48 @@ ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, 
  * Koop log10 J_s, omega), evaluated at the given precision with limiters of step dt. */
 ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int n, double dt,
                           double *Q, double *aux, void *stream);
+
+/* ---- source surrogate (Sec. 2.2 rates; the network is this library's, not the paper's) ----
+ * A 16 -> 4x128 (SiLU) -> 10 multilayer perceptron stands in for the stiff pointwise rates
+ * of Sec. 2.2 (nucleation Eqs. 3-6/10, growth Eq. 16, the stage relaxation rates) in the
+ * FP32 path.  Parameters: one flat FP32 vector, per layer W (out x in, row-major) then b.
+ * All pointers below are device pointers; all calls enqueue on `stream`. */
+
+/* Inputs X (n x CT_MLP_IN), targets Y and masks M (n x CT_MLP_OUT, mask 0 where a target is
+ * undefined, e.g. nucleation below liquid saturation) of n conserved states U (n x 14
+ * doubles, row-major), computed with the FP64 plain source of the case's physics.
+ * Inputs: ln p, T, ln rho, ln Y_v, ln of the 8 scaled moments, ln soot per m^3,
+ * ln <r_p^2>/um^2, ln S_l, ln S_i.  Targets: ln J/(1+phi) (floored at -60), ln r_crit/um,
+ * asinh(G_l/1 um/s), asinh(G_s/1 um/s), ln of the two relaxation rates 1/tau, ln J_hom,
+ * ln J_het,eff (floored), ln(1+phi), T_sat,l - T. */
+ct_status ct_mlp_dataset(const ct_case *c, const double *U, int n, float *X, float *Y, float *M, void *stream);
+
+/* Number of FP32 parameters of the network. */
+int ct_mlp_param_count(void);
+
+/* Bytes of device work memory needed by ct_mlp_forward / ct_mlp_loss_grad for n rows. */
+size_t ct_mlp_work_bytes(int n);
+
+/* FP32 forward pass: Y (n x CT_MLP_OUT) = net(X (n x CT_MLP_IN)); inputs and outputs in the
+ * standardised units the network was trained in. */
+ct_status ct_mlp_forward(const float *params, const float *X, int n, float *Y, void *work, size_t work_bytes,
+                         void *stream);
+
+/* Masked mean-squared error L = sum M (net(X) - Y)^2 / max(1, sum M) into loss (1 float) and
+ * its gradient with respect to params into grad (overwritten). */
+ct_status ct_mlp_loss_grad(const float *params, const float *X, const float *Y, const float *M, int n, float *grad,
+                           float *loss, void *work, size_t work_bytes, void *stream);
+
+/* One Adam step (bias-corrected, step >= 1) on nparam parameters. */
+ct_status ct_mlp_adam(float *params, const float *grad, float *m, float *v, int nparam, float lr, float beta1,
+                      float beta2, float eps, int step, void *stream);
+
+/* Column statistics of X (n x d, optional mask M of the same shape): out (4 x d floats) =
+ * mean, standard deviation, minimum, maximum. */
+ct_status ct_mlp_colstats(const float *X, const float *M, int n, int d, float *out, void *stream);
+
+/* In-place standardisation X = (X - mean)/sd, column-wise (sd <= 0 treated as 1). */
+ct_status ct_mlp_standardize(float *X, int n, int d, const float *mean, const float *sd, void *stream);
 
 /* Maximum scratch of ct_step_static, in bytes (4 MiB: about 16,000 tiles of 32x8 cells,
  * e.g. a 4096 x 1024 plume). */

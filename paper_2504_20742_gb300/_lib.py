@@ -15,6 +15,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libcontrail.so")
 
 CT_FP64, CT_FP32, CT_FP32_MLP = 0, 1, 2
 NF, NDIAG, NAUX = 14, 32, 11
+CT_MLP_IN, CT_MLP_HIDDEN, CT_MLP_OUT = 16, 128, 10
 
 # ct_case fields, in the order of include/contrail.h
 _CASE_FIELDS = (
@@ -59,6 +60,15 @@ _SIGS = {
     "ct_derived": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp]),
     "ct_source_batch": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
     "ct_step_static": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
+    "ct_mlp_dataset": (C.c_int, [_cp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "ct_mlp_param_count": (C.c_int, []),
+    "ct_mlp_work_bytes": (C.c_size_t, [C.c_int]),
+    "ct_mlp_forward": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp]),
+    "ct_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "ct_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                              _vp]),
+    "ct_mlp_colstats": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp]),
+    "ct_mlp_standardize": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp]),
     "ct_last_error": (C.c_char_p, []),
     "ct_version": (C.c_char_p, []),
 }
@@ -170,6 +180,40 @@ def ct_step_static(case, precision, ufac_rows_dev, U, U1, nsteps, cfl, stream=No
     """Allocation-free step: scratch in the library's static device array (see contrail.h)."""
     _check(_L().ct_step_static(C.byref(_case(case)), precision, _ptr(ufac_rows_dev), _ptr(U), _ptr(U1),
                                nsteps, cfl, _stream(stream)))
+
+
+def ct_mlp_dataset(case, U, n, X, Y, M, stream=None):
+    _check(_L().ct_mlp_dataset(C.byref(_case(case)), _ptr(U), n, _ptr(X), _ptr(Y), _ptr(M), _stream(stream)))
+
+
+def ct_mlp_param_count() -> int:
+    return _L().ct_mlp_param_count()
+
+
+def ct_mlp_work_bytes(n: int) -> int:
+    return _L().ct_mlp_work_bytes(n)
+
+
+def ct_mlp_forward(params, X, n, Y, work, work_bytes, stream=None):
+    _check(_L().ct_mlp_forward(_ptr(params), _ptr(X), n, _ptr(Y), _ptr(work), work_bytes, _stream(stream)))
+
+
+def ct_mlp_loss_grad(params, X, Y, M, n, grad, loss, work, work_bytes, stream=None):
+    _check(_L().ct_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), n, _ptr(grad), _ptr(loss), _ptr(work),
+                                 work_bytes, _stream(stream)))
+
+
+def ct_mlp_adam(params, grad, m, v, nparam, lr, beta1, beta2, eps, step, stream=None):
+    _check(_L().ct_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), nparam, lr, beta1, beta2, eps, step,
+                            _stream(stream)))
+
+
+def ct_mlp_colstats(X, M, n, d, out, stream=None):
+    _check(_L().ct_mlp_colstats(_ptr(X), _ptr(M), n, d, _ptr(out), _stream(stream)))
+
+
+def ct_mlp_standardize(X, n, d, mean, sd, stream=None):
+    _check(_L().ct_mlp_standardize(_ptr(X), n, d, _ptr(mean), _ptr(sd), _stream(stream)))
 
 
 def ct_last_error() -> str:

@@ -671,6 +671,45 @@ __global__ void k_source_batch(SrcCase sc, const double* __restrict__ U, int n, 
   }
 }
 
+// ---- surrogate training data: inputs and masked targets from the FP64 plain source ------
+// Targets: 0 ln Jeff (floored), 1 ln r_crit/um, 2 asinh(G_l/G0), 3 asinh(G_s/G0), 4 ln 1/tau_l,
+// 5 ln 1/tau_s, 6 ln J_hom (floored), 7 ln J_het,eff (floored), 8 ln(1+phi), 9 T_sat,l - T.
+__global__ void k_mlp_dataset(SrcCase sc, const double* __restrict__ U, int n, float* __restrict__ X,
+                              float* __restrict__ Y, float* __restrict__ M) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double u14[NF];
+    for (int f = 0; f < NF; ++f) u14[f] = U[(size_t)m * NF + f];
+    Prim<double> w;
+    cons_to_prim<double>(u14, w);
+    const Sat<double> st = saturation(w);
+    float x[CT_MLP_IN];
+    mlp_features<double>(w, st, sc.rp2, x);
+    double ext[10];
+    for (int q = 0; q < 10; ++q) ext[q] = 0.0;
+    ext[0] = ext[6] = ext[7] = -INFINITY;
+    double lnJ2[2] = {-INFINITY, -INFINITY};
+    plain_rates<double>(w, st, sc, lnJ2, nullptr, ext);
+    const bool nuc = st.lnSl > 0.0;
+    const bool soot = sc.n_soot_ref > 0.0 && w.rho * w.ns > 0.0;
+    float y[CT_MLP_OUT], mk[CT_MLP_OUT];
+    y[0] = (float)fmax(ext[0], (double)MLP_LNJ_FLOOR); mk[0] = nuc;
+    y[1] = nuc ? (float)ext[1] : 0.0f;                   mk[1] = nuc;
+    y[2] = asinhf((float)ext[2] / MLP_G0);               mk[2] = st.pres_l;
+    y[3] = asinhf((float)ext[3] / MLP_G0);               mk[3] = st.pres_s;
+    y[4] = logf(fmaxf((float)ext[4], 1e-30f));           mk[4] = st.pres_l;
+    y[5] = logf(fmaxf((float)ext[5], 1e-30f));           mk[5] = st.pres_s;
+    y[6] = (float)fmax(ext[6], (double)MLP_LNJ_FLOOR);  mk[6] = nuc;
+    y[7] = (float)fmax(ext[7], (double)MLP_LNJ_FLOOR);  mk[7] = nuc && soot;
+    y[8] = nuc ? (float)ext[8] : 0.0f;                   mk[8] = nuc;
+    y[9] = (float)ext[9];                                mk[9] = 1.0f;
+    for (int q = 0; q < CT_MLP_IN; ++q) X[(size_t)m * CT_MLP_IN + q] = x[q];
+    for (int q = 0; q < CT_MLP_OUT; ++q) {
+      Y[(size_t)m * CT_MLP_OUT + q] = mk[q] != 0.0f ? y[q] : 0.0f;
+      M[(size_t)m * CT_MLP_OUT + q] = mk[q];
+    }
+  }
+}
+
 }  // namespace ct
 
 // =========================================================================================
@@ -1043,7 +1082,22 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st);
 }
 
+ct_status ct_mlp_dataset(const ct_case* c, const double* U, int n, float* X, float* Y, float* M, void* stream) {
+  ct_status s = validate(c, CT_FP64);
+  if (s != CT_OK) return s;
+  if (n < 0) return fail(CT_ERR_ARG, "n < 0");
+  if (n == 0) return CT_OK;
+  if (!U || !X || !Y || !M) return fail(CT_ERR_ARG, "null buffer");
+  DevCase d = make_dev(c, nullptr);
+  int grid = std::min((n + 255) / 256, 8192);
+  k_mlp_dataset<<<grid, 256, 0, (cudaStream_t)stream>>>(d.sc, U, n, X, Y, M);
+  return cuda_check("k_mlp_dataset");
+}
+
 const char* ct_last_error(void) { return g_err; }
+
+// shared by the other translation units of the library (not part of the public header)
+ct_status ct__set_error(ct_status s, const char* msg) { return fail(s, msg); }
 const char* ct_version(void) { return "contrail-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -216,45 +216,139 @@ __device__ __forceinline__ T relax_slope(T Tsat, T Tg, T h, T Yv, T cv) {
   return m_fabs(a / Yv + (T(1) - a / Tg) * (h - T(k::RV) * Tg) / cv);
 }
 
-// Source of one cell.  w: primitives of the stage input; the limiters keep the
-// flux-updated state A + dt Q non-negative; Q gets fields 4..12.
-// aux (optional): ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s,
-// Koop log10 J, omega.  Returns true for an active cell.
-// U: conserved stage input of the cell; acc (may be null): its flux-only residual, so that
-// the limiters act on A = U + dt acc.
+// Expensive part of the source (what the surrogate stands in for): the effective nucleation
+// rate J/(1+phi) (m^-3 s^-1) and critical radius (um), the raw growth rates G(r20) (um/s) and
+// the relaxation rates 1/tau of the linearised vapour exchange (1/s) of both phases.
 template <class T>
-__device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
-                                             T* Q, double* lnJ2, double* aux) {
-#pragma unroll
-  for (int f = 4; f < 13; ++f) Q[f] = T(0);
-  if (aux) {
-#pragma unroll
-    for (int a = 0; a < NAUX; ++a) aux[a] = 0.0;
-    aux[2] = aux[3] = aux[9] = -INFINITY;
-  }
-  lnJ2[0] = lnJ2[1] = -INFINITY;
-  if (!sc.phase_change) return false;
-  const T Tg = w.Tg, rho = w.rho;
-  const bool pres_l = w.ml[0] > T(k::MU_MIN) && w.ml[1] > T(0) && w.ml[2] > T(0) && w.ml[3] > T(0);
-  const bool pres_s = w.ms[0] > T(k::MU_MIN) && w.ms[1] > T(0) && w.ms[2] > T(0) && w.ms[3] > T(0);
-  if (sizeof(T) == 4 && !aux && !pres_l && !pres_s) {
-    // FP32 screen: a cell clearly below liquid saturation with no population has an exactly
-    // zero source; only cells near or above saturation pay for the FP64 island below.
-    float pvf = float(rho) * float(w.Yv) * float(k::RV) * float(Tg);
-    pvf = pvf < 1e-30f ? 1e-30f : pvf;
-    if (logf(pvf) - ln_psat_liq<float>(float(Tg)) < -1e-3f) return false;
-  }
-  // Eq. (1) in FP64: ln S = ln p_v - ln p_sat(T)
-  double pv = double(rho) * double(w.Yv) * k::RV * double(Tg);
-  pv = pv < 1e-30 ? 1e-30 : pv;
-  const double lnpv = m_log(pv);
-  const double lnpsl = ln_psat_liq<double>(double(Tg)), lnpsi = ln_psat_ice<double>(double(Tg));
-  const double lnSl = lnpv - lnpsl, lnSi = lnpv - lnpsi;
-  if (aux) { aux[0] = lnSl; aux[1] = lnSi; }
-  const bool active = lnSl > 0.0 || pres_l || pres_s;
-  if (aux) aux[4] = active ? 1.0 : 0.0;
-  if (!active) return false;
+struct Rates {
+  T Jeff, rc_um, Gl, Gs, xl, xs;
+};
 
+// Cheap part of the source, shared by the plain and the surrogate paths: relaxation
+// limiter, freezing, moment assembly (Eq. 21), vapour sink (Eqs. 18, 25) and the
+// flux-aware limiters of reading J.  U: conserved stage input of the cell; acc (may be
+// null): its flux-only residual, so that the limiters act on A = U + dt acc.
+template <class T>
+__device__ __forceinline__ void source_tail(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
+                                            bool pres_l, bool pres_s, double lnSl, double lnSi, Rates<T> r, T* Q,
+                                            double* aux) {
+  const T Tg = w.Tg, rho = w.rho;
+  // growth over the stage: the exponential solution of the linearised exchange
+  const T xsum = dt * (r.xl + r.xs);
+  if (xsum > T(0)) {
+    const T theta = -m_expm1(-xsum) / xsum;
+    r.Gl *= theta;
+    r.Gs *= theta;
+  }
+  if (aux) { aux[7] = double(r.Gl) * 1e-6; aux[8] = double(r.Gs) * 1e-6; }
+
+  // freezing, Eqs. (12)-(15) (reading H)
+  T Nf = T(0), rv = T(0), rf = T(0);
+  if (sc.freezing && pres_l && Tg < T(k::TREF)) {
+    rv = m_cbrt(w.ml[3] / w.ml[0]);   // um
+    const T daw = T(1) - T(m_exp(lnSl - lnSi));   // 1 - p_sat,i / p_sat,l
+    T Js = T(0);
+    if (daw >= T(0.26)) {
+      const T l10 = koop_log10(daw);
+      Js = m_exp(l10 * T(2.302585092994045684)) * T(1e6);
+      if (aux) aux[9] = double(l10);
+    }
+    T chi = w.ns / w.ml[0];
+    chi = chi > T(1) ? T(1) : chi;
+    const T rvm = rv * T(1e-6);
+    const T omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
+    if (aux) aux[10] = double(omega);
+    Nf = w.ml[0] * (-m_expm1(-omega * dt) / dt);   // first-order decay over the stage
+    rf = rv * T(k::RHOL_OVER_RHOS_CBRT);
+  }
+
+  // moment sources (per kg, scaled units), Eq. (21)
+  const T jr = r.Jeff / rho;
+  T dml[4], dms[4];
+  {
+    T rck = T(1), rvk = T(1), rfk = T(1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dml[q] = (q ? T(q) * w.ml[q - 1] * r.Gl : T(0)) + jr * rck - Nf * rvk;
+      dms[q] = (q ? T(q) * w.ms[q - 1] * r.Gs : T(0)) + Nf * rfk;
+      rck *= r.rc_um;
+      rvk *= rv;
+      rfk *= rf;
+    }
+  }
+  // limiters on the flux-updated stage state (reading J)
+  auto A = [&](int f) { return acc ? U[f] + dt * acc[f] : U[f]; };
+  const T ir = T(1) / rho;
+  const T idt = T(1) / dt;
+  if (A(8) * ir + dt * dml[3] <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dml[q] = -(A(5 + q) * ir) * idt;
+  }
+  if (A(12) * ir + dt * dms[3] <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dms[q] = -(A(9 + q) * ir) * idt;
+  }
+  T dYv = -(T(k::YL3) * dml[3] + T(k::YS3) * dms[3]);
+  const T av = A(4) * ir;
+  if (av + dt * dYv < T(0)) {
+    const T th = av > T(0) ? av / (-dt * dYv) : T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { dml[q] *= th; dms[q] *= th; }
+    dYv *= th;
+  }
+  Q[4] = rho * dYv;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Q[5 + q] = rho * dml[q];
+    Q[9 + q] = rho * dms[q];
+  }
+}
+
+// Saturation state of a cell (Eq. 1, FP64): ln S over liquid and ice, ln p_v, populations.
+template <class T>
+struct Sat {
+  double lnSl, lnSi, lnpv;
+  bool pres_l, pres_s, active;
+};
+
+template <class T>
+__device__ __forceinline__ bool populations(const Prim<T>& w, bool& pres_l, bool& pres_s) {
+  pres_l = w.ml[0] > T(k::MU_MIN) && w.ml[1] > T(0) && w.ml[2] > T(0) && w.ml[3] > T(0);
+  pres_s = w.ms[0] > T(k::MU_MIN) && w.ms[1] > T(0) && w.ms[2] > T(0) && w.ms[3] > T(0);
+  return pres_l || pres_s;
+}
+
+// FP32 screen: a cell clearly below liquid saturation with no population has an exactly
+// zero source; only cells near or above saturation pay for the FP64 island.
+template <class T>
+__device__ __forceinline__ bool clearly_inactive(const Prim<T>& w) {
+  float pvf = float(w.rho) * float(w.Yv) * float(k::RV) * float(w.Tg);
+  pvf = pvf < 1e-30f ? 1e-30f : pvf;
+  return logf(pvf) - ln_psat_liq<float>(float(w.Tg)) < -1e-3f;
+}
+
+template <class T>
+__device__ __forceinline__ Sat<T> saturation(const Prim<T>& w) {
+  Sat<T> s;
+  populations(w, s.pres_l, s.pres_s);
+  // Eq. (1) in FP64: ln S = ln p_v - ln p_sat(T)
+  double pv = double(w.rho) * double(w.Yv) * k::RV * double(w.Tg);
+  pv = pv < 1e-30 ? 1e-30 : pv;
+  s.lnpv = m_log(pv);
+  s.lnSl = s.lnpv - ln_psat_liq<double>(double(w.Tg));
+  s.lnSi = s.lnpv - ln_psat_ice<double>(double(w.Tg));
+  s.active = s.lnSl > 0.0 || s.pres_l || s.pres_s;
+  return s;
+}
+
+// Plain rates, Sec. 2.2.  ext (optional, the surrogate's training targets): 0 ln Jeff,
+// 1 ln r_crit/um, 2 G_l raw (um/s), 3 G_s raw, 4 1/tau_l, 5 1/tau_s, 6 ln J_hom,
+// 7 ln J_het,eff, 8 ln(1+phi), 9 T_sat,l - T.
+template <class T>
+__device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& st, const SrcCase& sc, double* lnJ2,
+                                                double* aux, double* ext) {
+  const T Tg = w.Tg, rho = w.rho;
+  Rates<T> r = {T(0), T(0), T(0), T(0), T(0), T(0)};
   // gas-phase properties (reading G)
   const T Yg = T(1) - w.Yl - w.Ys;
   const T Ya = Yg - w.Yv;
@@ -268,10 +362,10 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
   const T lbar = T(1.5) * mu_g * m_sqrt(Rg_g * Tg) / w.p;
   const T hfg = T(k::CPV - k::CL) * Tg + T(k::E0V);
   const T hsg = T(k::CPV - k::CS) * Tg + T(k::E0V - k::E0S);
-  const T lnpv_t = T(lnpv);
+  const T lnpv_t = T(st.lnpv);
+  const double lnSl = st.lnSl, lnSi = st.lnSi;
 
   // nucleation, Eqs. (3)-(6), (10); soot-gated heterogeneous rate
-  T Jeff = T(0), rc_um = T(0);
   T Tsat_l = T(0);
   bool have_tsat_l = false;
   if (lnSl > 0.0) {
@@ -304,95 +398,92 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
     const T alpha_c = lam / (rcT * (T(1) + T(3.78) * (T(1) - nu) * Knc * T(1.0 / k::PR)));
     const T phi = T(k::QC) * T(rhov) / alpha_c * m_sqrt(T(k::RV) * Tg * T(1.0 / (2.0 * k::PI))) *
                   (hfg * hfg / (T(k::RV) * Tg * Tg) - hfg / Tg);
-    Jeff = T(Jsum) / (T(1) + phi);
-    rc_um = T(rc * 1e6);
+    r.Jeff = T(Jsum) / (T(1) + phi);
+    r.rc_um = T(rc * 1e6);
     if (aux) { aux[2] = lnJ2[0]; aux[3] = lnJ2[1]; aux[5] = rc; aux[6] = double(phi); }
+    if (ext) {
+      ext[0] = m_log(Jsum) - m_log(1.0 + double(phi));
+      ext[1] = m_log(rc * 1e6);
+      ext[6] = lnJ2[0];
+      ext[7] = lnJ2[1];
+      ext[8] = m_log(1.0 + double(phi));
+    }
   }
 
-  // growth at r20, Eqs. (16), (21) -- G in um/s; the stage relaxation limiter scales both
-  // phases by (1 - exp(-x))/x, x = dt/tau of the linearised exchange (reading J)
-  T Gl = T(0), Gs = T(0), xsum = T(0);
-  if (pres_l) {
+  // growth at r20, Eqs. (16), (21) -- G in um/s, relaxation rates of reading J
+  if (st.pres_l) {
     if (!have_tsat_l) Tsat_l = t_sat<T, false>(lnpv_t);
     const T r20 = m_sqrt(w.ml[2] / w.ml[0]) * T(1e-6);
     const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), sigma_liq(Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
-    Gl = g.cond * g.D * T(1e6);
-    xsum += dt * T(4.0 * k::PI * k::RHOL * 1e-12) * w.ml[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
+    r.Gl = g.cond * g.D * T(1e6);
+    r.xl = T(4.0 * k::PI * k::RHOL * 1e-12) * w.ml[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
   }
-  if (pres_s) {
+  if (st.pres_s) {
     const T Tsat_i = t_sat<T, true>(lnpv_t);
     const T r20 = m_sqrt(w.ms[2] / w.ms[0]) * T(1e-6);
     const Growth<T> g = young_growth<T>(r20, Tg, Tsat_i, T(lnSi), T(k::SIGMA_SV), T(k::RHOS), hsg, lam, lbar, gam_g, cp_g);
-    Gs = g.cond * g.D * T(1e6);
-    xsum += dt * T(4.0 * k::PI * k::RHOS * 1e-12) * w.ms[2] * g.cond * relax_slope(Tsat_i, Tg, hsg, w.Yv, w.cv);
+    r.Gs = g.cond * g.D * T(1e6);
+    r.xs = T(4.0 * k::PI * k::RHOS * 1e-12) * w.ms[2] * g.cond * relax_slope(Tsat_i, Tg, hsg, w.Yv, w.cv);
   }
-  if (xsum > T(0)) {
-    const T theta = -m_expm1(-xsum) / xsum;
-    Gl *= theta;
-    Gs *= theta;
+  if (ext) {
+    ext[2] = double(r.Gl);
+    ext[3] = double(r.Gs);
+    ext[4] = double(r.xl);
+    ext[5] = double(r.xs);
+    if (!have_tsat_l) Tsat_l = t_sat<T, false>(lnpv_t);
+    ext[9] = double(Tsat_l - Tg);
   }
-  if (aux) { aux[7] = double(Gl) * 1e-6; aux[8] = double(Gs) * 1e-6; }
+  return r;
+}
 
-  // freezing, Eqs. (12)-(15) (reading H)
-  T Nf = T(0), rv = T(0), rf = T(0);
-  if (sc.freezing && pres_l && Tg < T(k::TREF)) {
-    rv = m_cbrt(w.ml[3] / w.ml[0]);   // um
-    const T daw = T(1) - T(m_exp(lnpsi - lnpsl));
-    T Js = T(0);
-    if (daw >= T(0.26)) {
-      const T l10 = koop_log10(daw);
-      Js = m_exp(l10 * T(2.302585092994045684)) * T(1e6);
-      if (aux) aux[9] = double(l10);
-    }
-    T chi = w.ns / w.ml[0];
-    chi = chi > T(1) ? T(1) : chi;
-    const T rvm = rv * T(1e-6);
-    const T omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
-    if (aux) aux[10] = double(omega);
-    Nf = w.ml[0] * (-m_expm1(-omega * dt) / dt);   // first-order decay over the stage
-    rf = rv * T(k::RHOL_OVER_RHOS_CBRT);
-  }
+// ---- surrogate inputs and targets ---------------------------------------------------------
+constexpr float MLP_G0 = 1.0f;       // um/s, scale of asinh(G/G0)
+constexpr float MLP_LNJ_FLOOR = -60.0f;
 
-  // moment sources (per kg, scaled units), Eq. (21)
-  const T jr = Jeff / rho;
-  T dml[4], dms[4];
-  {
-    T rck = T(1), rvk = T(1), rfk = T(1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      dml[q] = (q ? T(q) * w.ml[q - 1] * Gl : T(0)) + jr * rck - Nf * rvk;
-      dms[q] = (q ? T(q) * w.ms[q - 1] * Gs : T(0)) + Nf * rfk;
-      rck *= rc_um;
-      rvk *= rv;
-      rfk *= rf;
-    }
-  }
-  // limiters on the flux-updated stage state (reading J)
-  auto A = [&](int f) { return acc ? U[f] + dt * acc[f] : U[f]; };
-  const T ir = T(1) / rho;
-  const T idt = T(1) / dt;
-  if (A(8) * ir + dt * dml[3] <= T(0)) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dml[q] = -(A(5 + q) * ir) * idt;
-  }
-  if (A(12) * ir + dt * dms[3] <= T(0)) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dms[q] = -(A(9 + q) * ir) * idt;
-  }
-  T dYv = -(T(k::YL3) * dml[3] + T(k::YS3) * dms[3]);
-  const T av = A(4) * ir;
-  if (av + dt * dYv < T(0)) {
-    const T th = av > T(0) ? av / (-dt * dYv) : T(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { dml[q] *= th; dms[q] *= th; }
-    dYv *= th;
-  }
-  Q[4] = rho * dYv;
+// 16 inputs of a cell: ln p, T, ln rho, ln Y_v, ln of the 8 scaled moments, ln soot per m^3,
+// ln <r_p^2>/um^2, ln S_l, ln S_i (the last two from the FP64 island).
+template <class T>
+__device__ __forceinline__ void mlp_features(const Prim<T>& w, const Sat<T>& st, double rp2, float* x) {
+  x[0] = logf(float(w.p));
+  x[1] = float(w.Tg);
+  x[2] = logf(float(w.rho));
+  x[3] = logf(fmaxf(float(w.Yv), 1e-12f));
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    Q[5 + q] = rho * dml[q];
-    Q[9 + q] = rho * dms[q];
+    x[4 + q] = logf(fmaxf(float(w.ml[q]), 1e-30f));
+    x[8 + q] = logf(fmaxf(float(w.ms[q]), 1e-30f));
   }
+  x[12] = logf(fmaxf(float(w.rho) * float(w.ns), 1.0f));
+  x[13] = logf(float(rp2 * 1e12) + 1e-30f);
+  x[14] = float(st.lnSl);
+  x[15] = float(st.lnSi);
+}
+
+// Source of one cell (plain method).  w: primitives of the stage input; the limiters keep
+// the flux-updated state A = U + dt acc non-negative; Q gets fields 4..12.  aux (optional):
+// ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s, Koop log10 J, omega.
+// Returns true for an active cell.
+template <class T>
+__device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
+                                             T* Q, double* lnJ2, double* aux, double* ext = nullptr) {
+#pragma unroll
+  for (int f = 4; f < 13; ++f) Q[f] = T(0);
+  if (aux) {
+#pragma unroll
+    for (int a = 0; a < NAUX; ++a) aux[a] = 0.0;
+    aux[2] = aux[3] = aux[9] = -INFINITY;
+  }
+  lnJ2[0] = lnJ2[1] = -INFINITY;
+  if (!sc.phase_change) return false;
+  if (sizeof(T) == 4 && !aux && !ext) {
+    bool pl, ps;
+    if (!populations(w, pl, ps) && clearly_inactive(w)) return false;
+  }
+  const Sat<T> st = saturation(w);
+  if (aux) { aux[0] = st.lnSl; aux[1] = st.lnSi; aux[4] = st.active ? 1.0 : 0.0; }
+  if (!st.active) return false;
+  const Rates<T> r = plain_rates<T>(w, st, sc, lnJ2, aux, ext);
+  source_tail<T>(w, U, acc, dt, sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, aux);
   return true;
 }
 
