@@ -185,6 +185,21 @@ ct_status ct_mlp_colstats(const float *X, const float *M, int n, int d, float *o
 /* In-place standardisation X = (X - mean)/sd, column-wise (sd <= 0 treated as 1). */
 ct_status ct_mlp_standardize(float *X, int n, int d, const float *mean, const float *sd, void *stream);
 
+/* Bytes of the device blob of a packed surrogate (BF16 weights in tensor-core operand
+ * order, FP32 biases, input/output standardisation and the training hull). */
+size_t ct_mlp_blob_bytes(void);
+
+/* Pack trained FP32 parameters and statistics (16-float device arrays: input mean, sd,
+ * training-hull min and max; output mean and sd, first CT_MLP_OUT used) into blob (device,
+ * ct_mlp_blob_bytes(), 16-byte aligned). */
+ct_status ct_mlp_pack(const float *params, const float *x_mean, const float *x_sd, const float *x_min,
+                      const float *x_max, const float *y_mean, const float *y_sd, void *blob, void *stream);
+
+/* BF16 tensor-core inference (tcgen05, FP32 accumulation) of n raw input rows X
+ * (n x CT_MLP_IN floats) into raw outputs Y (n x CT_MLP_OUT).  err_flag (device int) is set
+ * to 1 if a bounded wait for the tensor cores timed out. */
+ct_status ct_mlp_infer(const void *blob, const float *X, int n, float *Y, int *err_flag, void *stream);
+
 /* Maximum scratch of ct_step_static, in bytes (4 MiB: about 16,000 tiles of 32x8 cells,
  * e.g. a 4096 x 1024 plume). */
 #define CT_STATIC_SCRATCH_BYTES (4u << 20)

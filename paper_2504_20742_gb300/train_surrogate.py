@@ -1,0 +1,107 @@
+"""Train the phase-change source surrogate on the GPU and write data/surrogate.npz.
+
+    python -m paper_2504_20742_gb300.train_surrogate [--rows N] [--epochs E] [--out PATH]
+
+States are sampled from FP64 runs of the library itself, active cells only (with the
+kerosene plume's boundary conditions no cell is ever active, so the samples come from the
+condensing nozzle and from hydrogen-like mixing and freezing plumes over a sweep of ambient
+temperature, humidity and exhaust water).  Targets come from the FP64 plain source.  5 % of
+the rows are held out; the report gives the validation error of every output in its own
+units and of log10 J_hom where J_hom >= 1 m^-3 s^-1.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2504_20742_gb300 import surrogate as S  # noqa: E402
+from synth import cases  # noqa: E402
+
+OUT_NAMES = ("lnJeff", "ln_rc_um", "asinh_Gl", "asinh_Gs", "ln_relax_l", "ln_relax_s", "lnJhom", "lnJhet",
+             "ln1p_phi", "dT_l")
+
+
+def training_cases():
+    """(case, row factors, steps, sampling interval) of the sampled runs."""
+    out = [(cases.nozzle_case(nx=400), None, 3000, 3)]
+    base, uf = cases.mixing_layer_case(nx=96, nr=40)
+    for yv, tc in ((0.2, 330.0), (0.1, 310.0), (0.05, 300.0)):
+        for ta, si in ((205.0, 1.3), (220.0, 1.1)):
+            c = dict(base, Yv_core=yv, T_core=tc, T_amb=ta, S_ice_amb=si)
+            out.append((c, uf, 240, 3))
+    fz, ufz = cases.freezing_case(nx=96, nr=40)
+    out.append((fz, ufz, 300, 3))
+    out.append((dict(fz, T_core=236.0, Yv_core=6.0e-4), ufz, 300, 3))
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rows", type=int, default=4_000_000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--out", default=S.default_path())
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    Xs, Ys, Ms = [], [], []
+    for c, uf, nsteps, every in training_cases():
+        U = S.sample_active_states(c, uf, nsteps=nsteps, every=every)
+        if U.shape[0] == 0:
+            continue
+        X, Y, M = S.dataset(c, U)
+        Xs.append(X)
+        Ys.append(Y)
+        Ms.append(M)
+    X, Y, M = torch.cat(Xs), torch.cat(Ys), torch.cat(Ms)
+    keep = torch.isfinite(X).all(1) & torch.isfinite(Y).all(1)
+    X, Y, M = X[keep], Y[keep], M[keep]
+    n_all = X.shape[0]
+    g = torch.Generator(device=X.device)
+    g.manual_seed(1)
+    perm = torch.randperm(n_all, generator=g, device=X.device)
+    if n_all > args.rows:
+        perm = perm[:args.rows]
+    n = perm.numel()
+    nval = max(1, n // 20)
+    iv, it = perm[:nval], perm[nval:]
+    t1 = time.time()
+    sur = S.train(X[it], Y[it], M[it], epochs=args.epochs, batch=args.batch, lr=args.lr, verbose=True)
+    t2 = time.time()
+    # validation in the targets' own units
+    Yp = sur.predict(X[iv])
+    Yv, Mv = Y[iv], M[iv]
+    rep = {"rows_sampled": int(n_all), "rows_used": int(n), "rows_validation": int(nval),
+           "sample_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1), "final_loss": float(sur.history[-1]),
+           "rmse": {}, "max_abs": {}}
+    for q, name in enumerate(OUT_NAMES):
+        m = Mv[:, q] > 0
+        if int(m.sum()) == 0:
+            continue
+        e = (Yp[m, q] - Yv[m, q]).abs()
+        rep["rmse"][name] = float(torch.sqrt((e * e).mean()))
+        rep["max_abs"][name] = float(e.max())
+    m = (Mv[:, 6] > 0) & (Yv[:, 6] >= 0.0)
+    if int(m.sum()) > 0:
+        e10 = ((Yp[m, 6] - Yv[m, 6]) / np.log(10.0)).abs()
+        rep["log10_Jhom_where_J_ge_1"] = {"n": int(m.sum()), "mean_abs": float(e10.mean()),
+                                          "p99_abs": float(torch.quantile(e10, 0.99)), "max_abs": float(e10.max())}
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    sur.save(args.out)
+    rep["out"] = args.out
+    print(json.dumps(rep))
+    return sur, rep
+
+
+if __name__ == "__main__":
+    main()
