@@ -152,8 +152,9 @@ ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int 
 /* Inputs X (n x CT_MLP_IN), targets Y and masks M (n x CT_MLP_OUT, mask 0 where a target is
  * undefined, e.g. nucleation below liquid saturation) of n conserved states U (n x 14
  * doubles, row-major), computed with the FP64 plain source of the case's physics.
- * Inputs: ln p, T, ln rho, ln Y_v, ln of the 8 scaled moments, ln soot per m^3,
- * ln <r_p^2>/um^2, ln S_l, ln S_i.  Targets: ln J/(1+phi) (floored at -60), ln r_crit/um,
+ * Inputs: ln p, T, 1/max(ln S_l, 1/4)^2 (the CNT barrier shape), ln Y_v, ln of the 8
+ * scaled moments, ln soot per m^3, ln <r_p^2>/um^2, ln S_l, ln S_i.  Targets: ln J/(1+phi)
+ * (floored at -30), ln r_crit/um,
  * asinh(G_l/1 um/s), asinh(G_s/1 um/s), ln of the two relaxation rates 1/tau, ln J_hom,
  * ln J_het,eff (floored), ln(1+phi), T_sat,l - T. */
 ct_status ct_mlp_dataset(const ct_case *c, const double *U, int n, float *X, float *Y, float *M, void *stream);
@@ -190,15 +191,26 @@ ct_status ct_mlp_standardize(float *X, int n, int d, const float *mean, const fl
 size_t ct_mlp_blob_bytes(void);
 
 /* Pack trained FP32 parameters and statistics (16-float device arrays: input mean, sd,
- * training-hull min and max; output mean and sd, first CT_MLP_OUT used) into blob (device,
- * ct_mlp_blob_bytes(), 16-byte aligned). */
+ * training-hull min and max; output mean, sd, min and max over the training targets, first
+ * CT_MLP_OUT used) into blob (device, ct_mlp_blob_bytes(), 16-byte aligned).  The fused step
+ * holds every network output to its training range. */
 ct_status ct_mlp_pack(const float *params, const float *x_mean, const float *x_sd, const float *x_min,
-                      const float *x_max, const float *y_mean, const float *y_sd, void *blob, void *stream);
+                      const float *x_max, const float *y_mean, const float *y_sd, const float *y_min,
+                      const float *y_max, void *blob, void *stream);
 
 /* BF16 tensor-core inference (tcgen05, FP32 accumulation) of n raw input rows X
  * (n x CT_MLP_IN floats) into raw outputs Y (n x CT_MLP_OUT).  err_flag (device int) is set
  * to 1 if a bounded wait for the tensor cores timed out. */
 ct_status ct_mlp_infer(const void *blob, const float *X, int n, float *Y, int *err_flag, void *stream);
+
+/* Advance an FP32 state (CT_FP32_MLP) by nsteps SSP-RK2 steps like ct_step, with the
+ * phase-change rates of active cells inside the surrogate's training hull taken from the
+ * BF16 tensor-core network in `blob` (ct_mlp_pack) instead of the plain source (Sec. 2.2);
+ * cells outside the hull use the plain source (counted in diagnostics slot 26).  The moment
+ * assembly, freezing, limiters and water bookkeeping are the plain path's, so conservation
+ * is unaffected.  U, U1, work as for ct_step (workspace set up with CT_FP32_MLP). */
+ct_status ct_step_surrogate(const ct_case *c, void *U, void *U1, void *work, const void *blob, int nsteps, double cfl,
+                            void *stream);
 
 /* Maximum scratch of ct_step_static, in bytes (4 MiB: about 16,000 tiles of 32x8 cells,
  * e.g. a 4096 x 1024 plume). */

@@ -70,8 +70,9 @@ _SIGS = {
     "ct_mlp_colstats": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp]),
     "ct_mlp_standardize": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp]),
     "ct_mlp_blob_bytes": (C.c_size_t, []),
-    "ct_mlp_pack": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ct_mlp_pack": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ct_mlp_infer": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
+    "ct_step_surrogate": (C.c_int, [_cp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_last_error": (C.c_char_p, []),
     "ct_version": (C.c_char_p, []),
 }
@@ -223,13 +224,18 @@ def ct_mlp_blob_bytes() -> int:
     return _L().ct_mlp_blob_bytes()
 
 
-def ct_mlp_pack(params, x_mean, x_sd, x_min, x_max, y_mean, y_sd, blob, stream=None):
+def ct_mlp_pack(params, x_mean, x_sd, x_min, x_max, y_mean, y_sd, y_min, y_max, blob, stream=None):
     _check(_L().ct_mlp_pack(_ptr(params), _ptr(x_mean), _ptr(x_sd), _ptr(x_min), _ptr(x_max), _ptr(y_mean),
-                            _ptr(y_sd), _ptr(blob), _stream(stream)))
+                            _ptr(y_sd), _ptr(y_min), _ptr(y_max), _ptr(blob), _stream(stream)))
 
 
 def ct_mlp_infer(blob, X, n, Y, err_flag, stream=None):
     _check(_L().ct_mlp_infer(_ptr(blob), _ptr(X), n, _ptr(Y), _ptr(err_flag), _stream(stream)))
+
+
+def ct_step_surrogate(case, U, U1, work, blob, nsteps, cfl, stream=None):
+    _check(_L().ct_step_surrogate(C.byref(_case(case)), _ptr(U), _ptr(U1), _ptr(work), _ptr(blob), nsteps, cfl,
+                                  _stream(stream)))
 
 
 def ct_last_error() -> str:

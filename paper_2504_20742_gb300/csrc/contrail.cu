@@ -18,6 +18,7 @@
 
 #include "../../include/contrail.h"
 #include "flux.cuh"
+#include "mlp_tc.cuh"
 #include "physics.cuh"
 
 namespace ct {
@@ -198,9 +199,144 @@ __device__ bool last_block_reduce(const DevCase& dc, double* red_smem) {
 constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
 template <class T>
 constexpr size_t stage_smem() { return sizeof(T) * (size_t)NF * (HX * HY + 3 * NFACE); }
+// shared memory of the surrogate phase, reusing the (then dead) stencil buffers:
+// activations, streamed weights, outputs, blob header, TMEM slot, mbarrier
+constexpr size_t SM_A = 0, SM_W = SM_A + mlp::ABYTES, SM_OUT = SM_W + 32768, SM_HDR = SM_OUT + 128 * 10 * 4,
+                 SM_TSLOT = SM_HDR + mlp::NFLOAT * 4, SM_MBAR = SM_TSLOT + 16, SURR_SMEM = SM_MBAR + 16;
+constexpr size_t stage_smem_surr() { return stage_smem<float>() > SURR_SMEM ? stage_smem<float>() : SURR_SMEM; }
 
-template <class T, int STAGE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout) {
+// Source of the FP32 + surrogate path for the cells of one tile (called by all threads).
+// Active cells inside the surrogate's training hull are compacted into 128-row tiles and
+// run through the BF16 tensor-core network; their rates feed the same tail as the plain
+// source (so conservation and the limiters are exact).  Active cells outside the hull take
+// the plain source and count as fallbacks.  Adds the source to acc.
+template <class T>
+__device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsigned char* __restrict__ blob, bool cell,
+                                                 const Prim<T>& w, const T* u14, T* acc, T dt, int& nactive,
+                                                 int& nfallback, int& nbad, T& lnJh, T& lnJt, unsigned char* smem) {
+  __shared__ int wcnt[NT / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* ghdr = reinterpret_cast<const float*>(blob);
+  int kind = 0;   // 0 inactive, 1 plain source (outside the hull), 2 surrogate
+  Sat<T> st;
+  st.lnSl = st.lnSi = st.lnpv = 0.0;
+  st.pres_l = st.pres_s = st.active = false;
+  float x[CT_MLP_IN];
+  T Q[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Q[f] = T(0);
+  double lnJ2[2] = {-INFINITY, -INFINITY};
+  if (cell && dc.sc.phase_change) {
+    bool pl, ps;
+    const bool pops = populations(w, pl, ps);
+    if (pops || !clearly_inactive(w)) {
+      st = saturation(w);
+      if (st.active) {
+        mlp_features<T>(w, st, dc.sc.rp2, x);
+        bool inside = true;
+#pragma unroll
+        for (int q = 0; q < CT_MLP_IN; ++q)
+          inside = inside && x[q] >= ghdr[mlp::F_HMIN + q] && x[q] <= ghdr[mlp::F_HMAX + q];
+        kind = inside ? 2 : 1;
+      }
+    }
+  }
+  if (kind == 1) {
+    const Rates<T> r = plain_rates<T>(w, st, dc.sc, lnJ2, nullptr, nullptr);
+    source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
+    nfallback = 1;
+  }
+  // compaction of the surrogate cells; the stencil buffers are dead from here on
+  __syncthreads();
+  const unsigned mask = __ballot_sync(0xffffffffu, kind == 2);
+  if (lane == 0) wcnt[warp] = __popc(mask);
+  __syncthreads();
+  int off = 0, total = 0;
+  for (int w2 = 0; w2 < NT / 32; ++w2) {
+    off += w2 < warp ? wcnt[w2] : 0;
+    total += wcnt[w2];
+  }
+  const int row = off + __popc(mask & ((1u << lane) - 1u));
+  if (total > 0) {
+    unsigned char* A = smem + SM_A;
+    unsigned char* W = smem + SM_W;
+    float* outs = reinterpret_cast<float*>(smem + SM_OUT);
+    float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TSLOT);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SM_MBAR);
+    for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
+    if (warp == 0) {
+      tc::tmem_alloc(tc::smem_addr(tslot), 128);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+      tc::mbar_init(tc::smem_addr(mbar), 1);
+      tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int c0 = 0; c0 < total; c0 += 128) {
+      const bool mine = kind == 2 && row >= c0 && row < c0 + 128;
+      if (mine) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = (x[q] - hdr[mlp::F_XMEAN + q]) * hdr[mlp::F_XISD + q];
+        mlp::store_row16(A, row - c0, 0, 16, v);
+      }
+      float o[10];
+      ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(mbar), phase, o, blob + mlp::WOFF) && ok;
+      if (tid < 128) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
+      }
+      __syncthreads();
+      if (mine) {
+        // network outputs, held to the range their targets spanned in training
+        float y[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q)
+          y[q] = fminf(fmaxf(outs[(row - c0) * 10 + q], hdr[mlp::F_YMIN + q]), hdr[mlp::F_YMAX + q]);
+        const bool nuc = st.lnSl > 0.0;
+        Rates<T> r;
+        r.Jeff = nuc ? T(__expf(y[0])) : T(0);
+        // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
+        r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
+                          (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
+                      : T(0);
+        r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
+        r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
+        r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
+        r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
+        if (nuc) {
+          lnJ2[0] = y[6];
+          if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
+        }
+        source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
+      }
+      __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (!ok && tid == 0) nbad += 1;   // a tensor-core wait timed out: the step reports failure
+  }
+  if (cell) {
+    nactive = kind != 0 ? 1 : 0;
+    lnJh = T(lnJ2[0]);
+    lnJt = T(lnJ2[1]);
+#pragma unroll
+    for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+  }
+}
+
+template <class T, int STAGE, bool SURR>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T (*qs)[HY][HX] = reinterpret_cast<T (*)[HY][HX]>(smem_raw);                      // primitives
   T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NF * HX * HY);   // face fluxes
@@ -361,13 +497,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stage(DevCase dc
 #pragma unroll
   for (int f = 0; f < NF; ++f) rmax[f] = T(0);
   T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
-  int nactive = 0, nbad = 0;
+  int nactive = 0, nbad = 0, nfallback = 0;
+  T u14[NF];
+  Prim<T> w;
   if (cell) {
     const size_t n = (size_t)j * nx + i;
-    T u14[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-    Prim<T> w;
     cons_to_prim<T>(u14, w);
     if (dc.geom == 1) {
       const T ijh = frcp(T(j) + T(0.5));
@@ -394,12 +530,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stage(DevCase dc
     // phase-change source limited on the flux-updated state
     T Q[NF];
     double lnJ2[2];
-    const bool act = phase_source<T>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
-    nactive = act ? 1 : 0;
-    lnJh = T(lnJ2[0]);
-    lnJt = T(lnJ2[1]);
+    if (!SURR) {
+      const bool act = phase_source<T>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
+      nactive = act ? 1 : 0;
+      lnJh = T(lnJ2[0]);
+      lnJt = T(lnJ2[1]);
 #pragma unroll
-    for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+      for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+    }
+  }
+  if (SURR) surrogate_source<T>(dc, blob, cell, w, u14, acc, dt, nactive, nfallback, nbad, lnJh, lnJt, smem_raw);
+  if (cell) {
+    const size_t n = (size_t)j * nx + i;
     // RK combine
     T out[NF];
     if (STAGE == 1) {
@@ -452,7 +594,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_stage(DevCase dc
     }
     v = warp_max(lnJh); if (lane == 0) red[warp][23] = double(v);
     v = warp_max(lnJt); if (lane == 0) red[warp][24] = double(v);
-    if (lane == 0) red[warp][25] = 0.0;
+    a = warp_sum(nfallback); if (lane == 0) red[warp][25] = a;
   }
   __syncthreads();
   if (tid < NPART) {
@@ -899,20 +1041,30 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   return launch_dt(c, precision, work, U, cfl, st);
 }
 
-static bool g_attr_done[2] = {false, false};
+static bool g_attr_done[3] = {false, false, false};
 
 static ct_status set_stage_attrs(int precision) {
-  const int p = precision == CT_FP64 ? 0 : 1;
+  const int p = precision == CT_FP64 ? 0 : (precision == CT_FP32 ? 1 : 2);
   if (g_attr_done[p]) return CT_OK;
   cudaError_t e;
   if (p == 0) {
-    e = cudaFuncSetAttribute(k_stage<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<double>());
+    e = cudaFuncSetAttribute(k_stage<double, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stage_smem<double>());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<double>());
+      e = cudaFuncSetAttribute(k_stage<double, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stage_smem<double>());
+  } else if (p == 1) {
+    e = cudaFuncSetAttribute(k_stage<float, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stage_smem<float>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage<float, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stage_smem<float>());
   } else {
-    e = cudaFuncSetAttribute(k_stage<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<float>());
+    e = cudaFuncSetAttribute(k_stage<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stage_smem_surr());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<float>());
+      e = cudaFuncSetAttribute(k_stage<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stage_smem_surr());
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
   g_attr_done[p] = true;
@@ -920,24 +1072,41 @@ static ct_status set_stage_attrs(int precision) {
 }
 
 static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
-                               cudaStream_t st) {
+                               cudaStream_t st, const void* blob = nullptr) {
   ct_status s = set_stage_attrs(precision);
   if (s != CT_OK) return s;
   DevCase d = make_dev(c, work);
   d.cfl = cfl;
   dim3 grid(tiles_x(c), tiles_y(c));
+  const unsigned char* b = (const unsigned char*)blob;
   for (int k2 = 0; k2 < nsteps; ++k2) {
     if (precision == CT_FP64) {
       const size_t sm = stage_smem<double>();
-      k_stage<double, 1><<<grid, NT, sm, st>>>(d, (const double*)U, nullptr, (double*)U1);
-      k_stage<double, 2><<<grid, NT, sm, st>>>(d, (const double*)U1, (const double*)U, (double*)U);
-    } else {
+      k_stage<double, 1, false><<<grid, NT, sm, st>>>(d, (const double*)U, nullptr, (double*)U1, nullptr);
+      k_stage<double, 2, false><<<grid, NT, sm, st>>>(d, (const double*)U1, (const double*)U, (double*)U, nullptr);
+    } else if (precision == CT_FP32) {
       const size_t sm = stage_smem<float>();
-      k_stage<float, 1><<<grid, NT, sm, st>>>(d, (const float*)U, nullptr, (float*)U1);
-      k_stage<float, 2><<<grid, NT, sm, st>>>(d, (const float*)U1, (const float*)U, (float*)U);
+      k_stage<float, 1, false><<<grid, NT, sm, st>>>(d, (const float*)U, nullptr, (float*)U1, nullptr);
+      k_stage<float, 2, false><<<grid, NT, sm, st>>>(d, (const float*)U1, (const float*)U, (float*)U, nullptr);
+    } else {
+      const size_t sm = stage_smem_surr();
+      k_stage<float, 1, true><<<grid, NT, sm, st>>>(d, (const float*)U, nullptr, (float*)U1, b);
+      k_stage<float, 2, true><<<grid, NT, sm, st>>>(d, (const float*)U1, (const float*)U, (float*)U, b);
     }
   }
   return cuda_check("k_stage");
+}
+
+ct_status ct_step_surrogate(const ct_case* c, void* U, void* U1, void* work, const void* blob, int nsteps, double cfl,
+                            void* stream) {
+  ct_status s = validate(c, CT_FP32_MLP);
+  if (s != CT_OK) return s;
+  if (!U || !U1 || !work || !blob) return fail(CT_ERR_ARG, "null buffer");
+  if (U == U1) return fail(CT_ERR_ARG, "U and U1 must be distinct buffers");
+  if (((uintptr_t)blob & 15) != 0) return fail(CT_ERR_ARG, "surrogate blob must be 16-byte aligned");
+  if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
+  return enqueue_steps(c, CT_FP32_MLP, U, U1, work, nsteps, cfl, (cudaStream_t)stream, blob);
 }
 
 ct_status ct_step(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
@@ -948,7 +1117,7 @@ ct_status ct_step(const ct_case* c, int precision, void* U, void* U1, void* work
   if (U == U1) return fail(CT_ERR_ARG, "U and U1 must be distinct buffers");
   if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
   if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
-  if (precision == CT_FP32_MLP) return fail(CT_ERR_ARG, "CT_FP32_MLP needs a loaded surrogate");
+  if (precision == CT_FP32_MLP) return fail(CT_ERR_ARG, "CT_FP32_MLP steps go through ct_step_surrogate");
   return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, (cudaStream_t)stream);
 }
 

@@ -16,7 +16,8 @@ namespace mlp {
 // params: flat FP32 (per layer W out x in, then b); stats: 16-float arrays.
 __global__ void k_pack(const float* __restrict__ params, const float* __restrict__ x_mean,
                        const float* __restrict__ x_sd, const float* __restrict__ x_min, const float* __restrict__ x_max,
-                       const float* __restrict__ y_mean, const float* __restrict__ y_sd, unsigned char* __restrict__ blob) {
+                       const float* __restrict__ y_mean, const float* __restrict__ y_sd, const float* __restrict__ y_min,
+                       const float* __restrict__ y_max, unsigned char* __restrict__ blob) {
   float* hdr = reinterpret_cast<float*>(blob);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
   for (int i = tid; i < 16; i += nt) {
@@ -26,6 +27,8 @@ __global__ void k_pack(const float* __restrict__ params, const float* __restrict
     hdr[F_YSD + i] = i < CT_MLP_OUT ? y_sd[i] : 0.0f;
     hdr[F_HMIN + i] = x_min[i];
     hdr[F_HMAX + i] = x_max[i];
+    hdr[F_YMIN + i] = i < CT_MLP_OUT ? y_min[i] : 0.0f;
+    hdr[F_YMAX + i] = i < CT_MLP_OUT ? y_max[i] : 0.0f;
   }
   // flat parameter offsets
   int po = 0;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(128, 1) k_infer(const unsigned char* __restric
     for (int i = 0; i < 16; ++i) v[i] = row < n ? (X[(size_t)row * 16 + i] - hdr[F_XMEAN + i]) * hdr[F_XISD + i] : 0.0f;
     store_row16(A, tid, 0, 16, v);
     float o[10];
-    const bool tile_ok = run_tile(A, W, hdr + F_BIAS, tmem, tc::smem_addr(mbar), phase, o);
+    const bool tile_ok = run_tile<false>(A, W, hdr + F_BIAS, tmem, tc::smem_addr(mbar), phase, o);
     ok = __syncthreads_and(tile_ok ? 1 : 0) != 0;   // CTA-uniform, so the loop stays convergent
     if (row < n) {
 #pragma unroll
@@ -106,11 +109,12 @@ extern "C" {
 size_t ct_mlp_blob_bytes(void) { return (size_t)BLOB_BYTES; }
 
 ct_status ct_mlp_pack(const float* params, const float* x_mean, const float* x_sd, const float* x_min,
-                      const float* x_max, const float* y_mean, const float* y_sd, void* blob, void* stream) {
-  if (!params || !x_mean || !x_sd || !x_min || !x_max || !y_mean || !y_sd || !blob)
+                      const float* x_max, const float* y_mean, const float* y_sd, const float* y_min,
+                      const float* y_max, void* blob, void* stream) {
+  if (!params || !x_mean || !x_sd || !x_min || !x_max || !y_mean || !y_sd || !y_min || !y_max || !blob)
     return ct__set_error(CT_ERR_ARG, "ct_mlp_pack: null pointer");
   if (((uintptr_t)blob & 15) != 0) return ct__set_error(CT_ERR_ARG, "ct_mlp_pack: blob must be 16-byte aligned");
-  k_pack<<<64, 256, 0, (cudaStream_t)stream>>>(params, x_mean, x_sd, x_min, x_max, y_mean, y_sd,
+  k_pack<<<64, 256, 0, (cudaStream_t)stream>>>(params, x_mean, x_sd, x_min, x_max, y_mean, y_sd, y_min, y_max,
                                                 (unsigned char*)blob);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CT_OK : ct__set_error(CT_ERR_CUDA, cudaGetErrorString(e));

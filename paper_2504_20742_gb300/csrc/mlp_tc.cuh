@@ -12,9 +12,10 @@ namespace ct {
 namespace mlp {
 
 // Device blob: a float header, then the BF16 weights in K-major core-matrix order.
-constexpr int F_XMEAN = 0, F_XISD = 16, F_YMEAN = 32, F_YSD = 48, F_HMIN = 64, F_HMAX = 80, F_BIAS = 96;
-constexpr int NFLOAT = F_BIAS + 4 * 128 + 16;   // 624
-constexpr int WOFF = 2560;                      // byte offset of the weights
+constexpr int F_XMEAN = 0, F_XISD = 16, F_YMEAN = 32, F_YSD = 48, F_HMIN = 64, F_HMAX = 80, F_YMIN = 96,
+              F_YMAX = 112, F_BIAS = 128;
+constexpr int NFLOAT = F_BIAS + 4 * 128 + 16;   // 656
+constexpr int WOFF = 2688;                      // byte offset of the weights (128-byte aligned)
 __host__ __device__ constexpr int kdim(int l) { return l == 0 ? 16 : 128; }
 __host__ __device__ constexpr int ndim(int l) { return l == 4 ? 16 : 128; }      // padded output width
 __host__ __device__ constexpr int wbytes(int l) { return ndim(l) * kdim(l) * 2; }
@@ -24,7 +25,7 @@ __host__ __device__ constexpr int woff(int l) {
   return o;
 }
 constexpr int WBYTES = woff(5);                 // 106,496
-constexpr int BLOB_BYTES = WOFF + WBYTES;       // 109,056
+constexpr int BLOB_BYTES = WOFF + WBYTES;       // 109,184
 constexpr int ABYTES = 128 * 128 * 2;           // activation operand, 32 KB
 
 __device__ __forceinline__ float silu(float z) { return z * (1.0f / (1.0f + __expf(-z))); }
@@ -51,8 +52,12 @@ __device__ __forceinline__ void store_row16(unsigned char* buf, int row, int c16
 // 0..127 and return the 10 standardised outputs of their row in `out`.  `W`: weights in
 // shared memory; `bias`: the 4x128 + 16 biases; `tmem`: 128 allocated TMEM columns;
 // `mbar`/`phase`: the MMA-completion barrier.  Returns false if a wait timed out.
-__device__ __forceinline__ bool run_tile(unsigned char* A, const unsigned char* W, const float* bias, uint32_t tmem,
-                                         uint32_t mbar, uint32_t& phase, float* out) {
+// STREAM: W is a 32 KB shared buffer and each layer's weights are copied into it from the
+// global blob weights Wg just before that layer's MMA (keeps the fused step at 2 CTAs/SM).
+template <bool STREAM = false>
+__device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, const float* bias, uint32_t tmem,
+                                         uint32_t mbar, uint32_t& phase, float* out,
+                                         const unsigned char* __restrict__ Wg = nullptr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   bool ok = true;
@@ -62,8 +67,17 @@ __device__ __forceinline__ bool run_tile(unsigned char* A, const unsigned char* 
   tc::fence_after_sync();
   for (int l = 0; l < 5; ++l) {
     const int K = kdim(l), N = ndim(l);
+    if (STREAM) {
+      const uint4* src = reinterpret_cast<const uint4*>(Wg + woff(l));
+      uint4* dst = reinterpret_cast<uint4*>(W);
+      for (int i = tid; i < wbytes(l) / 16; i += blockDim.x) dst[i] = src[i];
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
     if (tid == 0) {
-      const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(W + woff(l));
+      const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(STREAM ? W : W + woff(l));
       const uint32_t sbo = (uint32_t)(K / 8) * 128u;
       const uint32_t idesc = tc::idesc_bf16_f32(128, N);
       for (int s = 0; s < K / 16; ++s)

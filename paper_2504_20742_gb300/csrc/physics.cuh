@@ -438,15 +438,19 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
 
 // ---- surrogate inputs and targets ---------------------------------------------------------
 constexpr float MLP_G0 = 1.0f;       // um/s, scale of asinh(G/G0)
-constexpr float MLP_LNJ_FLOOR = -60.0f;
+constexpr float MLP_LNJ_FLOOR = -30.0f;   // J below 1e-13 m^-3 s^-1 is physically zero
 
-// 16 inputs of a cell: ln p, T, ln rho, ln Y_v, ln of the 8 scaled moments, ln soot per m^3,
+// 16 inputs of a cell: ln p, T, the CNT barrier shape 1/max(ln S_l, 1/4)^2 (the barrier of
+// Eq. 3 scales as 1/ln^2 S), ln Y_v, ln of the 8 scaled moments, ln soot per m^3,
 // ln <r_p^2>/um^2, ln S_l, ln S_i (the last two from the FP64 island).
 template <class T>
 __device__ __forceinline__ void mlp_features(const Prim<T>& w, const Sat<T>& st, double rp2, float* x) {
   x[0] = logf(float(w.p));
   x[1] = float(w.Tg);
-  x[2] = logf(float(w.rho));
+  {
+    const float ls = fmaxf(float(st.lnSl), 0.25f);
+    x[2] = 1.0f / (ls * ls);
+  }
   x[3] = logf(fmaxf(float(w.Yv), 1e-12f));
 #pragma unroll
   for (int q = 0; q < 4; ++q) {

@@ -36,8 +36,15 @@ class Solver:
         src = U_src.to(device=self.device, dtype=self.dtype).contiguous()
         L.ct_load_state(self.case, self.precision, self.work, src, self.U, cfl, self.stream)
 
+    def attach_surrogate(self, blob: torch.Tensor):
+        """Device blob of a packed surrogate (CT_FP32_MLP solvers)."""
+        self.blob = blob
+
     def step(self, nsteps: int, cfl: float = 0.5):
-        L.ct_step(self.case, self.precision, self.U, self.U1, self.work, nsteps, cfl, self.stream)
+        if self.precision == L.CT_FP32_MLP:
+            L.ct_step_surrogate(self.case, self.U, self.U1, self.work, self.blob, nsteps, cfl, self.stream)
+        else:
+            L.ct_step(self.case, self.precision, self.U, self.U1, self.work, nsteps, cfl, self.stream)
 
     def diagnostics(self) -> np.ndarray:
         return L.ct_diagnostics(self.work, self.stream)

@@ -83,16 +83,30 @@ class Surrogate:
     x_max: np.ndarray
     y_mean: np.ndarray
     y_sd: np.ndarray
+    y_min: np.ndarray           # range of the training targets (the fused step clamps to it)
+    y_max: np.ndarray
     history: np.ndarray         # loss per epoch
 
     def save(self, path: str):
         np.savez(path, params=self.params, x_mean=self.x_mean, x_sd=self.x_sd, x_min=self.x_min,
-                 x_max=self.x_max, y_mean=self.y_mean, y_sd=self.y_sd, history=self.history)
+                 x_max=self.x_max, y_mean=self.y_mean, y_sd=self.y_sd, y_min=self.y_min, y_max=self.y_max,
+                 history=self.history)
 
     @classmethod
     def load(cls, path: str) -> "Surrogate":
         z = np.load(path)
-        return cls(**{k: z[k] for k in ("params", "x_mean", "x_sd", "x_min", "x_max", "y_mean", "y_sd", "history")})
+        keys = ("params", "x_mean", "x_sd", "x_min", "x_max", "y_mean", "y_sd", "y_min", "y_max", "history")
+        return cls(**{k: z[k] for k in keys})
+
+    def blob(self, device="cuda") -> torch.Tensor:
+        """Pack into the device blob of the BF16 tensor-core kernels (ct_mlp_pack)."""
+        dev = torch.device(device)
+        t = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+        pad = lambda a: np.concatenate([a, np.zeros(16 - a.size, dtype=np.float32)])
+        out = torch.zeros(L.ct_mlp_blob_bytes() // 4 + 16, dtype=torch.float32, device=dev)
+        L.ct_mlp_pack(t(self.params), t(self.x_mean), t(self.x_sd), t(self.x_min), t(self.x_max),
+                      t(pad(self.y_mean)), t(pad(self.y_sd)), t(pad(self.y_min)), t(pad(self.y_max)), out)
+        return out
 
     def predict(self, X: torch.Tensor) -> torch.Tensor:
         """FP32 forward in raw units (for checks; the fused step runs the BF16 kernel)."""
@@ -153,7 +167,8 @@ def train(X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int = 20, b
             print(f"epoch {ep}: loss {hist[-1]:.5f}", flush=True)
     return Surrogate(params=P.cpu().numpy(), x_mean=sx[0].cpu().numpy(), x_sd=x_sd.cpu().numpy(),
                      x_min=sx[2].cpu().numpy(), x_max=sx[3].cpu().numpy(), y_mean=sy[0].cpu().numpy(),
-                     y_sd=y_sd.cpu().numpy(), history=np.array(hist))
+                     y_sd=y_sd.cpu().numpy(), y_min=sy[2].cpu().numpy(), y_max=sy[3].cpu().numpy(),
+                     history=np.array(hist))
 
 
 def default_path() -> str:

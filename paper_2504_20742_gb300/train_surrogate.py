@@ -33,7 +33,9 @@ OUT_NAMES = ("lnJeff", "ln_rc_um", "asinh_Gl", "asinh_Gs", "ln_relax_l", "ln_rel
 
 def training_cases():
     """(case, row factors, steps, sampling interval) of the sampled runs."""
-    out = [(cases.nozzle_case(nx=400), None, 3000, 3)]
+    out = []
+    for p0, yv in ((40.0e3, 0.02), (30.0e3, 0.015), (50.0e3, 0.025), (40.0e3, 0.03)):
+        out.append((dict(cases.nozzle_case(nx=400), p0=p0, Yv_inlet=yv), None, 3000, 3))
     base, uf = cases.mixing_layer_case(nx=96, nr=40)
     for yv, tc in ((0.2, 330.0), (0.1, 310.0), (0.05, 300.0)):
         for ta, si in ((205.0, 1.3), (220.0, 1.1)):
@@ -48,7 +50,7 @@ def training_cases():
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--rows", type=int, default=4_000_000)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=S.default_path())

@@ -90,7 +90,7 @@ def test_dataset_targets_match_oracle_quantities(P):
     assert np.allclose(X[:, 14], aux[:, 0], rtol=1e-5, atol=1e-5)
     assert np.allclose(X[:, 15], aux[:, 1], rtol=1e-5, atol=1e-5)
     fin = nuc & np.isfinite(aux[:, 2])
-    assert np.allclose(Y[fin, 6], np.maximum(aux[fin, 2], -60.0), rtol=1e-5, atol=1e-4)
+    assert np.allclose(Y[fin, 6], np.maximum(aux[fin, 2], -30.0), rtol=1e-5, atol=1e-4)
     assert np.allclose(Y[nuc, 1], np.log(aux[nuc, 5] * 1e6), rtol=1e-5, atol=1e-5)
     assert np.allclose(Y[nuc, 8], np.log1p(aux[nuc, 6]), rtol=1e-4, atol=1e-6)
     pl = M[:, 2] > 0

@@ -61,7 +61,8 @@ def test_tensor_core_inference_matches_bf16_emulation_and_fp32(P):
     d = "cuda"
     t = lambda a: torch.tensor(np.ascontiguousarray(a), device=d)
     blob = torch.zeros(P.ct_mlp_blob_bytes() // 4 + 16, dtype=torch.float32, device=d)
-    P.ct_mlp_pack(t(theta), t(x_mean), t(x_sd), t(X.min(0)), t(X.max(0)), t(y_mean), t(y_sd), blob)
+    P.ct_mlp_pack(t(theta), t(x_mean), t(x_sd), t(X.min(0)), t(X.max(0)), t(y_mean), t(y_sd),
+                  t(np.full(16, -1e30, np.float32)), t(np.full(16, 1e30, np.float32)), blob)
     n = X.shape[0]
     Y = torch.zeros((n, 10), dtype=torch.float32, device=d)
     err = torch.zeros(1, dtype=torch.int32, device=d)
