@@ -48,8 +48,16 @@ def _workload(name):
     if name == "fp64":
         c, uf = cases.plume_case()
         return c, uf, "axisymmetric coaxial plume 1024x256, FP64 plain method", 0
-    c, uf = cases.plume_case_mixed_precision()
-    return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 transport + FP64 islands", 1
+    if name in ("fp32", "fp32_mlp"):
+        c, uf = cases.plume_case_mixed_precision()
+        if name == "fp32":
+            return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 transport + FP64 islands", 1
+        return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 + BF16 tensor-core source surrogate", 2
+    # active-heavy hydrogen-like mixing plume: the source fires in ~10 % of the cells
+    c, uf = cases.mixing_layer_case(nx=2048, nr=512)
+    if name == "active_fp32":
+        return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + FP64 islands", 1
+    return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
 # Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/):
@@ -142,6 +150,9 @@ def run_cuda(args):
     with torch.cuda.stream(stream):
         s = P.Solver(c, uf, precision=prec, device=dev, stream=stream)
         s.init_state(cfl)
+        if prec == P.CT_FP32_MLP:
+            from paper_2504_20742_gb300 import surrogate as S
+            s.attach_surrogate(S.Surrogate.load(S.default_path()).blob(dev))
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         for _ in range(args.warmup):
             s.step(1, cfl)
@@ -168,11 +179,20 @@ def run_cuda(args):
         host_in = s.U.detach().cpu().pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         e2e_steps = max(3, min(args.steps, 10))
-        P.ct_step_host(c, prec, host_in, host_out, s.U, s.U1, s.work, 1, cfl, stream)   # warm
+        def e2e_step():
+            if prec == P.CT_FP32_MLP:      # host buffers around the surrogate step
+                s.U.copy_(host_in, non_blocking=True)
+                P.ct_load_state(c, prec, s.work, s.U, s.U, cfl, stream)
+                s.step(1, cfl)
+                host_out.copy_(s.U, non_blocking=True)
+                stream.synchronize()
+            else:
+                P.ct_step_host(c, prec, host_in, host_out, s.U, s.U1, s.work, 1, cfl, stream)
+        e2e_step()
         stream.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            P.ct_step_host(c, prec, host_in, host_out, s.U, s.U1, s.work, 1, cfl, stream)
+            e2e_step()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     ms_t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device=dev)
     if dist:
@@ -213,7 +233,8 @@ def run_cuda(args):
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32+bf16"),
         "data": "synthetic", "impl": "cuda",
         "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
@@ -223,7 +244,8 @@ def run_cuda(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
-        "diag": {"dt": d[0], "active_cells": d[7], "nonfinite": d[8]},
+        "diag": {"dt": d[0], "active_cells": d[7], "active_frac": round(d[7] / cells, 5), "nonfinite": d[8],
+                 "surrogate_fallback_cells": d[26]},
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(c, uf, args.cpu_seconds)
@@ -288,7 +310,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
-    ap.add_argument("--workload", default="fp64", choices=("fp64", "fp32"))
+    ap.add_argument("--workload", default="fp64", choices=("fp64", "fp32", "fp32_mlp", "active_fp32", "active_mlp"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

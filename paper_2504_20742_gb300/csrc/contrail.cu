@@ -202,30 +202,98 @@ constexpr size_t stage_smem() { return sizeof(T) * (size_t)NF * (HX * HY + 3 * N
 // shared memory of the surrogate phase, reusing the (then dead) stencil buffers:
 // activations, streamed weights, outputs, blob header, TMEM slot, mbarrier
 constexpr size_t SM_A = 0, SM_W = SM_A + mlp::ABYTES, SM_OUT = SM_W + 32768, SM_HDR = SM_OUT + 128 * 10 * 4,
-                 SM_TSLOT = SM_HDR + mlp::NFLOAT * 4, SM_MBAR = SM_TSLOT + 16, SURR_SMEM = SM_MBAR + 16;
+                 SM_TSLOT = SM_HDR + mlp::NFLOAT * 4, SM_MBAR = SM_TSLOT + 16, SM_RES = SM_MBAR + 16,
+                 SURR_SMEM = SM_RES + 288 * 10 * 4;
 constexpr size_t stage_smem_surr() { return stage_smem<float>() > SURR_SMEM ? stage_smem<float>() : SURR_SMEM; }
 
-// Source of the FP32 + surrogate path for the cells of one tile (called by all threads).
-// Active cells inside the surrogate's training hull are compacted into 128-row tiles and
-// run through the BF16 tensor-core network; their rates feed the same tail as the plain
-// source (so conservation and the limiters are exact).  Active cells outside the hull take
-// the plain source and count as fallbacks.  Adds the source to acc.
+// Surrogate cells of one tile (called by all threads, only when the tile has at least one):
+// compaction into 128-row tiles and the BF16 tensor-core network.  Each surrogate cell's
+// thread finds its 10 outputs (raw units, held to the training range of their targets) in
+// res[10 * threadIdx.x ...] afterwards.  x: the cell's 16 raw inputs (kind == 2 only).
+__device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ blob, int kind, const float* x, int& nbad,
+                                            unsigned char* smem) {
+  __shared__ int wcnt[NT / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* ghdr = reinterpret_cast<const float*>(blob);
+  const unsigned mask = __ballot_sync(0xffffffffu, kind == 2);
+  if (lane == 0) wcnt[warp] = __popc(mask);
+  __syncthreads();
+  int off = 0, total = 0;
+  for (int w2 = 0; w2 < NT / 32; ++w2) {
+    off += w2 < warp ? wcnt[w2] : 0;
+    total += wcnt[w2];
+  }
+  const int row = off + __popc(mask & ((1u << lane) - 1u));
+  unsigned char* A = smem + SM_A;
+  unsigned char* W = smem + SM_W;
+  float* outs = reinterpret_cast<float*>(smem + SM_OUT);
+  float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
+  float* res = reinterpret_cast<float*>(smem + SM_RES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TSLOT);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SM_MBAR);
+  for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_addr(tslot), 128);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_addr(mbar), 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int c0 = 0; c0 < total; c0 += 128) {
+    const bool mine = kind == 2 && row >= c0 && row < c0 + 128;
+    if (mine) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = (x[q] - hdr[mlp::F_XMEAN + q]) * hdr[mlp::F_XISD + q];
+      mlp::store_row16(A, row - c0, 0, 16, v);
+    }
+    float o[10];
+    ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(mbar), phase, o, blob + mlp::WOFF,
+                             total - c0) && ok;
+    if (tid < 128) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
+    }
+    __syncthreads();
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q)
+        res[tid * 10 + q] = fminf(fmaxf(outs[(row - c0) * 10 + q], hdr[mlp::F_YMIN + q]), hdr[mlp::F_YMAX + q]);
+    }
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (!ok && tid == 0) nbad += 1;   // a tensor-core wait timed out: the step reports failure
+}
+
+// Source of the FP32 + surrogate path (called by all threads): active cells inside the
+// surrogate's training hull take their rates from the network, the others the plain source
+// (counted as fallbacks); both feed the plain path's tail, so conservation and the limiters
+// are exact.  Adds the source to acc.
 template <class T>
 __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsigned char* __restrict__ blob, bool cell,
                                                  const Prim<T>& w, const T* u14, T* acc, T dt, int& nactive,
                                                  int& nfallback, int& nbad, T& lnJh, T& lnJt, unsigned char* smem) {
-  __shared__ int wcnt[NT / 32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float* ghdr = reinterpret_cast<const float*>(blob);
   int kind = 0;   // 0 inactive, 1 plain source (outside the hull), 2 surrogate
   Sat<T> st;
   st.lnSl = st.lnSi = st.lnpv = 0.0;
   st.pres_l = st.pres_s = st.active = false;
-  float x[CT_MLP_IN];
   T Q[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) Q[f] = T(0);
   double lnJ2[2] = {-INFINITY, -INFINITY};
+  float x[CT_MLP_IN];
   if (cell && dc.sc.phase_change) {
     bool pl, ps;
     const bool pops = populations(w, pl, ps);
@@ -246,84 +314,28 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
     source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
     nfallback = 1;
   }
-  // compaction of the surrogate cells; the stencil buffers are dead from here on
-  __syncthreads();
-  const unsigned mask = __ballot_sync(0xffffffffu, kind == 2);
-  if (lane == 0) wcnt[warp] = __popc(mask);
-  __syncthreads();
-  int off = 0, total = 0;
-  for (int w2 = 0; w2 < NT / 32; ++w2) {
-    off += w2 < warp ? wcnt[w2] : 0;
-    total += wcnt[w2];
-  }
-  const int row = off + __popc(mask & ((1u << lane) - 1u));
-  if (total > 0) {
-    unsigned char* A = smem + SM_A;
-    unsigned char* W = smem + SM_W;
-    float* outs = reinterpret_cast<float*>(smem + SM_OUT);
-    float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TSLOT);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SM_MBAR);
-    for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
-    if (warp == 0) {
-      tc::tmem_alloc(tc::smem_addr(tslot), 128);
-      tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-      tc::mbar_init(tc::smem_addr(mbar), 1);
-      tc::fence_mbar_init();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = *tslot;
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int c0 = 0; c0 < total; c0 += 128) {
-      const bool mine = kind == 2 && row >= c0 && row < c0 + 128;
-      if (mine) {
-        float v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = (x[q] - hdr[mlp::F_XMEAN + q]) * hdr[mlp::F_XISD + q];
-        mlp::store_row16(A, row - c0, 0, 16, v);
+  // the stencil buffers are dead from here on; tiles without a surrogate cell skip the rest
+  if (__syncthreads_or(kind == 2)) {
+    surrogate_tile(blob, kind, x, nbad, smem);
+    if (kind == 2) {
+      const float* y = reinterpret_cast<const float*>(smem + SM_RES) + 10 * threadIdx.x;
+      const bool nuc = st.lnSl > 0.0;
+      Rates<T> r;
+      r.Jeff = nuc ? T(__expf(y[0])) : T(0);
+      // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
+      r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
+                        (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
+                    : T(0);
+      r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
+      r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
+      r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
+      r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
+      if (nuc) {
+        lnJ2[0] = y[6];
+        if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
       }
-      float o[10];
-      ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(mbar), phase, o, blob + mlp::WOFF) && ok;
-      if (tid < 128) {
-#pragma unroll
-        for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
-      }
-      __syncthreads();
-      if (mine) {
-        // network outputs, held to the range their targets spanned in training
-        float y[10];
-#pragma unroll
-        for (int q = 0; q < 10; ++q)
-          y[q] = fminf(fmaxf(outs[(row - c0) * 10 + q], hdr[mlp::F_YMIN + q]), hdr[mlp::F_YMAX + q]);
-        const bool nuc = st.lnSl > 0.0;
-        Rates<T> r;
-        r.Jeff = nuc ? T(__expf(y[0])) : T(0);
-        // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
-        r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
-                          (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
-                      : T(0);
-        r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
-        r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
-        r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
-        r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
-        if (nuc) {
-          lnJ2[0] = y[6];
-          if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
-        }
-        source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
-      }
-      __syncthreads();
+      source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
-    if (!ok && tid == 0) nbad += 1;   // a tensor-core wait timed out: the step reports failure
   }
   if (cell) {
     nactive = kind != 0 ? 1 : 0;

@@ -54,12 +54,19 @@ __device__ __forceinline__ void store_row16(unsigned char* buf, int row, int c16
 // `mbar`/`phase`: the MMA-completion barrier.  Returns false if a wait timed out.
 // STREAM: W is a 32 KB shared buffer and each layer's weights are copied into it from the
 // global blob weights Wg just before that layer's MMA (keeps the fused step at 2 CTAs/SM).
+// nrows: rows of the tile that carry data; 32-row groups beyond it skip the epilogue.  With
+// 8 or more warps, warps w and w+4 share the lane quarter of TMEM and split the columns.
 template <bool STREAM = false>
 __device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, const float* bias, uint32_t tmem,
                                          uint32_t mbar, uint32_t& phase, float* out,
-                                         const unsigned char* __restrict__ Wg = nullptr) {
+                                         const unsigned char* __restrict__ Wg = nullptr, int nrows = 128) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int quarter = warp & 3;                  // TMEM lanes 32*quarter .. +31
+  const int half = nwarps >= 8 ? (warp >> 2) : 0;   // column half handled by this warp
+  const bool epi = warp < (nwarps >= 8 ? 8 : 4) && 32 * quarter < nrows;
+  const int row = 32 * quarter + (tid & 31);
   bool ok = true;
   tc::fence_async_smem();
   tc::fence_before_sync();
@@ -88,17 +95,18 @@ __device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, con
     if (!tc::mbar_wait(mbar, phase)) ok = false;
     phase ^= 1u;
     tc::fence_after_sync();
-    if (tid < 128) {
-      const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    if (epi) {
+      const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
       if (l < 4) {
-        for (int c = 0; c < 8; ++c) {
+        const int c_lo = nwarps >= 8 ? 4 * half : 0, c_hi = nwarps >= 8 ? c_lo + 4 : 8;
+        for (int c = c_lo; c < c_hi; ++c) {
           float v[16];
           tc::tmem_ld16(lane_addr + 16u * c, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = silu(v[i] + bias[l * 128 + 16 * c + i]);
-          store_row16(A, tid, c, 128, v);
+          store_row16(A, row, c, 128, v);
         }
-      } else {
+      } else if (half == 0) {
         float v[16];
         tc::tmem_ld16(lane_addr, v);
 #pragma unroll

@@ -98,3 +98,25 @@ def test_surrogate_trajectory_vs_oracle_on_nozzle(P, sur):
     print("nozzle 300 steps, errors vs FP64 oracle (rho max rel, liquid number total, liquid mass total):", res)
     assert res["fp32"][0] < 1e-3 and res["fp32"][2] < 1e-2
     assert res["fp32_mlp"][0] < 5e-2
+
+
+def test_surrogate_gain_on_an_active_workload(P, sur):
+    """What the network buys: step time of the FP32 path and of the FP32 + surrogate path on
+    a hydrogen-like mixing plume whose source fires in many cells, same state and steps."""
+    c, uf = cases.mixing_layer_case(nx=1024, nr=256)
+    times = {}
+    for name, prec in (("fp32", P.CT_FP32), ("fp32_mlp", P.CT_FP32_MLP)):
+        s = _solver(P, sur, c, uf, prec)
+        s.step(3, 0.5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(20, 0.5)
+        e1.record(s.stream)
+        e1.synchronize()
+        d = s.diagnostics()
+        assert d[8] == 0
+        times[name] = (e0.elapsed_time(e1) / 20, d[7] / (1024 * 256), d[26])
+    print("ms/step, active fraction, fallbacks:", times,
+          "speedup of the surrogate path:", times["fp32"][0] / times["fp32_mlp"][0])
+    assert times["fp32_mlp"][1] > 0.02
