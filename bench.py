@@ -1,15 +1,21 @@
 """Benchmark of the contrail finite-volume step on GB300.
 
 Workloads (synthetic plumes shaped like the paper's turbofan exhaust, Sec. 4.1):
-  fp64  -- axisymmetric coaxial plume, 1024 x 256 cells, plain FP64 method (default)
-  fp32  -- the same plume on 4096 x 1024 cells, FP32 transport with FP64 islands
+  fp64      -- axisymmetric coaxial plume, 1024 x 256 cells, plain FP64 method (default)
+  fp32      -- the same plume on 4096 x 1024 cells, FP32 transport with FP64 islands
+  fp32_mlp  -- the 4096 x 1024 plume with the BF16 tensor-core source surrogate
+  active_fp32 / active_mlp -- a hydrogen-like mixing plume (2048 x 512) whose source fires
+               in about half of the cells, without / with the surrogate
+  batch64   -- 64 plume cases of uneven grids (256 x 64 .. 2048 x 512) and conditions in
+               one persistent, graph-captured launch per stage, FP32 + surrogate, autotuned
+               tile shape
 
 One benchmark step = one explicit SSP-RK2 step (two fused stage launches) over the whole
 grid.  `value` is cell-steps per second (whole job) with the state resident in HBM; L2 is
 flushed between timed steps (512 MB write).  `e2e` is the same metric through the C ABI's
 host-buffer entry point (state host->device, one step, state device->host each step).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload fp64|fp32] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 With --impl reference the CPU oracle (the plain FP64 C implementation the GPU path is
 checked against) is timed on the host cores for the same workload and metric.
@@ -23,6 +29,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -43,8 +50,18 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+BATCH_DESC = ("sweep of 64 axisymmetric plumes, grids 256x64..2048x512 (uneven), T_amb 205-235 K, "
+              "S_ice 0.9-1.3, water/fuel 1.25-8.9 kg/kg, duct 0 or 2 D_core, soot 1e10-1e13 m^-3; "
+              "FP32 + BF16 tensor-core surrogate, one persistent graph-captured launch per stage")
+
+
 def _workload(name):
     from synth import cases
+    if name == "batch64":
+        # the oracle's sample for this workload: the smallest case of the sweep
+        bc = cases.batch_cases(n=64)
+        k = int(np.argmin([c["nx"] * c["nr"] for c, _ in bc]))
+        return bc[k][0], bc[k][1], BATCH_DESC, 2
     if name == "fp64":
         c, uf = cases.plume_case()
         return c, uf, "axisymmetric coaxial plume 1024x256, FP64 plain method", 0
@@ -60,9 +77,10 @@ def _workload(name):
     return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
-# Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/):
-# FP64 arithmetic per cell-stage (mean of the two stages: 1283 and 1472 flops) and DRAM
-# bytes per cell per launch (mean of the two stages).  Set to None when the kernel changes.
+# Per-cell figures of the fused stage kernel with 32 x 8 tiles, from one ncu capture each
+# (see profiles/): FP64 arithmetic per cell-stage (mean of the two stages: 1283 and 1472
+# flops) and DRAM bytes per cell per launch (mean of the two stages).  The traffic is
+# reported only when the autotuner keeps that shape.
 FP64_FLOPS_PER_CELL_STAGE = 1377.7
 FP64_TRAFFIC_PER_CELL_LAUNCH = 172.4
 FP32_TRAFFIC_PER_CELL_LAUNCH = 134.3
@@ -92,7 +110,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ct_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -153,6 +171,7 @@ def run_cuda(args):
         if prec == P.CT_FP32_MLP:
             from paper_2504_20742_gb300 import surrogate as S
             s.attach_surrogate(S.Surrogate.load(S.default_path()).blob(dev))
+        shape, tune_ms = s.autotune(reps=3)     # the state is left as it was
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         for _ in range(args.warmup):
             s.step(1, cfl)
@@ -217,7 +236,8 @@ def run_cuda(args):
         flops = cells * FP64_FLOPS_PER_CELL_STAGE
         ach = flops / (launch_ms_ev * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
-                "frac": round(ach / fpk, 4), "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells,
+                "frac": round(ach / fpk, 4),
+                "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells if shape == 0 else None,
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{FP64_FLOPS_PER_CELL_STAGE} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"}
@@ -225,7 +245,8 @@ def run_cuda(args):
         alg_bytes = cells * 14 * elem * 2.5      # stage 1: read U, write U1; stage 2: read U1, U, write U
         bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells,
+                "frac": round(bw / peaks["hbm_gbs"], 4),
+                "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells if shape == 0 else None,
                 "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
@@ -237,6 +258,8 @@ def run_cuda(args):
         "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32+bf16"),
         "data": "synthetic", "impl": "cuda",
         "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
+                   "tile": "%dx%d (autotuned; ms per stage-1 launch per shape: %s)"
+                           % (*P.ct_tile_shape(shape), [round(m, 4) for m in tune_ms]),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
@@ -249,6 +272,115 @@ def run_cuda(args):
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(c, uf, args.cpu_seconds)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_batch(args):
+    """The 64-case sweep stepped by the batched persistent kernel (one replica per GPU)."""
+    import torch
+    import paper_2504_20742_gb300 as P
+    from paper_2504_20742_gb300 import surrogate as S
+    from synth import cases
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    bc = cases.batch_cases(n=64)
+    cells = int(sum(c["nx"] * c["nr"] for c, _ in bc))
+    cfl = 0.5
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        blob = S.Surrogate.load(S.default_path()).blob(dev)
+        b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32_MLP, device=dev, stream=stream,
+                    blob=blob)
+        b.init_state(cfl)
+        shape, tune_ms = b.autotune(reps=2)
+        for _ in range(args.warmup):
+            b.step(1, cfl)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with Clocks(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                starts[k].record(stream)
+                b.step(1, cfl)                # replay of the captured one-step graph
+                ends[k].record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        step_ms = float(np.sum([a.elapsed_time(e) for a, e in zip(starts, ends)])) / args.steps
+        d = b.diagnostics()
+        # end to end: pinned host state in, one step, state out, every step
+        host_in = b.U.detach().cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+
+        def e2e_step():
+            b.U.copy_(host_in, non_blocking=True)
+            b.load_state(b.U, cfl)
+            b.step(1, cfl)
+            host_out.copy_(b.U, non_blocking=True)
+            stream.synchronize()
+        e2e_step()
+        e2e_steps = max(3, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ms_t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    step_ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * cells / (step_ms * 1e-3) / 1e9
+    peaks, peak_kind = _peaks()
+    launch_ms = step_ms / 2.0
+    bw = cells * 14 * 4 * 2.5 / (launch_ms * 1e-3) / 1e9
+    tx, ty = P.ct_tile_shape(shape)
+    bytes_state = cells * 14 * 4
+    line = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic", "impl": "cuda",
+        "config": {"workload": BATCH_DESC, "cases": len(bc), "cells": cells, "cfl": cfl,
+                   "tile": f"{tx}x{ty} (autotuned; ms per stage-1 launch per shape: "
+                           f"{[round(m, 4) for m in tune_ms]})",
+                   "l2": "inputs larger than L2 (1.25 GB per FP32 state copy)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": None,
+                     "kernel": "ct::k_batch_stage<float, surrogate>", "peak_source": peak_kind,
+                     "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
+                             f"mean launch {launch_ms:.4f} ms"},
+        "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
+                "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": round(wall, 3),
+        "diag": {"dt_min": float(d[:, 0].min()), "dt_max": float(d[:, 0].max()),
+                 "active_cells": float(d[:, 7].sum()), "active_frac": round(float(d[:, 7].sum()) / cells, 5),
+                 "nonfinite": float(d[:, 8].sum()), "surrogate_fallback_cells": float(d[:, 26].sum())},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        c, uf, _, _ = _workload("batch64")
+        cb = cpu_baseline(c, uf, args.cpu_seconds)
+        cb["sample"] = f"the sweep's smallest case ({c['nx']}x{c['nr']}), plain FP64: " + cb["sample"]
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -299,7 +431,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": desc, "cells": cells},
             "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} whole-grid steps (of {args.steps} requested)"},
+                             "sample": f"{steps} whole-grid steps (of {args.steps} requested)"
+                                       + (f" of the sweep's smallest case ({c['nx']}x{c['nr']})"
+                                          if args.workload == "batch64" else "")},
             "e2e": {"value": round(value, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -310,7 +444,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
-    ap.add_argument("--workload", default="fp64", choices=("fp64", "fp32", "fp32_mlp", "active_fp32", "active_mlp"))
+    ap.add_argument("--workload", default="fp64",
+                    choices=("fp64", "fp32", "fp32_mlp", "active_fp32", "active_mlp", "batch64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -318,6 +453,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_cuda(args)
 

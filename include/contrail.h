@@ -85,7 +85,9 @@ typedef struct {
  *   4..6 mass, water and energy that entered through the boundary during the step
  *   (RK2 rule), 7 active cells in stage 2, 8 non-finite values, 9..22 max-norm of
  *   (U^{n+1}-U^n)/dt per field, 23 max log10 J_hom, 24 max log10 J_het (m^-3 s^-1),
- *   25 dt of the next step, 26 surrogate fallback cells (CT_FP32_MLP), 27 steps taken. */
+ *   25 dt of the next step, 26 surrogate fallback cells (CT_FP32_MLP), 27 steps taken,
+ *   28 tensor-core waits that gave up in either stage (CT_FP32_MLP; ct_diagnostics then
+ *   returns CT_ERR_TIMEOUT). */
 
 /* Bytes of device workspace needed by a case at a precision (boundary states, reduction
  * partials, time step and diagnostics).  Returns 0 for an invalid case. */
@@ -234,6 +236,85 @@ ct_status ct_step_surrogate(const ct_case *c, void *U, void *U1, void *work, con
  * CT_STATIC_SCRATCH_BYTES; CT_ERR_ARG for invalid arguments (CT_FP32_MLP is rejected). */
 ct_status ct_step_static(const ct_case *c, int precision, const double *ufac_rows_dev, void *U, void *U1,
                          int nsteps, double cfl, void *stream);
+
+/* ---- tile shapes and the autotuner (no counterpart in the paper) -----------------------
+ * The fused stage kernel is built for several tile shapes (cells per CTA); the state a step
+ * produces does not depend on the shape, only the speed does.  Steps of a case use the
+ * shape registered for its (geometry, nx, nr, precision), else shape 0 (32 x 8). */
+
+/* Number of tile shapes the library is built with. */
+int ct_tile_shape_count(void);
+
+/* Cells per tile of shape `shape` in x and r. */
+ct_status ct_tile_shape(int shape, int *tx, int *ty);
+
+/* Register `shape` for cases with this case's geometry, grid and precision (-1: back to the
+ * default).  CT_ERR_ARG when the shape's kernel does not fit an SM at that precision. */
+ct_status ct_set_tile_shape(const ct_case *c, int precision, int shape);
+
+/* Autotuner: time `reps` first-stage launches of every available shape on state U (device,
+ * left unchanged; U1 receives scratch results), with CUDA events on `stream`, register the
+ * fastest for the case's grid and return it in shape_out (may be NULL).  ms_out (host,
+ * ct_tile_shape_count() floats, may be NULL) receives ms per launch, -1 for shapes not
+ * available.  work must be set up for the case; blob is needed for CT_FP32_MLP.
+ * Synchronises `stream`. */
+ct_status ct_autotune(const ct_case *c, int precision, const void *U, void *U1, void *work, const void *blob, int reps,
+                      void *stream, int *shape_out, float *ms_out);
+
+/* ---- batched step: many plume cases in one persistent, graph-captured launch ----------
+ * A batch advances ncases independent axisymmetric cases (geom 1) of uneven grids and
+ * conditions together.  Each step is two launches of a persistent kernel whose CTAs take
+ * the tiles of all cases from one work list; every case keeps its own CFL time step and
+ * diagnostics.  Batch state layout: the cases' states (each in the single-case layout)
+ * one after another, case k starting at element 14 * sum_{k' < k} nx_k' nr_k'.
+ * FP32 and FP32_MLP only. */
+typedef struct ct_batch ct_batch;   /* host object: case table, tile shape, captured graph */
+
+/* Device workspace bytes of a batch (0 for invalid cases). */
+size_t ct_batch_workspace_bytes(const ct_case *cases, int ncases);
+
+/* Elements of one batch state (sum over cases of 14 nx nr). */
+size_t ct_batch_state_elems(const ct_case *cases, int ncases);
+
+/* Validate 1..256 cases, set up every case's part of `work` (device, 256-byte aligned,
+ * ct_batch_workspace_bytes) with its inflow rows (ufac_rows_host: host, sum of nr doubles,
+ * case after case, or NULL = all 1), and create the host object.  The batch's calls
+ * enqueue on `stream`; the object owns a private stream used only for graph capture.
+ * Synchronises `stream`. */
+ct_status ct_batch_create(const ct_case *cases, int ncases, int precision, const double *ufac_rows_host, void *work,
+                          size_t work_bytes, void *stream, ct_batch **out);
+
+/* Free the host object (not the caller's device memory). */
+void ct_batch_destroy(ct_batch *b);
+
+/* Initial state of every case into U (device, batch layout, float) and their first time
+ * steps, as ct_init_state. */
+ct_status ct_batch_init_state(ct_batch *b, void *U, double cfl);
+
+/* Copy the caller state U_src into U (may be equal) and compute every case's time step. */
+ct_status ct_batch_load_state(ct_batch *b, const void *U_src, void *U, double cfl);
+
+/* Use tile shape `shape` for the batch (the kernel's work list is rebuilt). */
+ct_status ct_batch_set_tile_shape(ct_batch *b, int shape);
+
+/* The batch's current tile shape. */
+int ct_batch_tile_shape(const ct_batch *b);
+
+/* Autotuner of the batched kernel: as ct_autotune, over the whole batch; leaves the
+ * fastest shape set.  U is left unchanged, U1 receives scratch results. */
+ct_status ct_batch_autotune(ct_batch *b, const void *U, void *U1, const void *blob, int reps, int *shape_out,
+                            float *ms_out);
+
+/* Advance every case of the batch by nsteps SSP-RK2 steps (Sec. 3.2), each with its own
+ * CFL time step.  The first call with a given (U, U1, blob, nsteps, cfl, shape) captures
+ * the 2 nsteps launches into a CUDA graph; later calls with the same arguments replay it
+ * with one launch.  blob: packed surrogate for CT_FP32_MLP, else ignored. */
+ct_status ct_batch_step(ct_batch *b, void *U, void *U1, const void *blob, int nsteps, double cfl);
+
+/* Diagnostics records of the last step of every case (host, ncases x CT_NDIAG doubles);
+ * synchronises the batch's stream.  CT_ERR_NONFINITE when any case produced non-finite
+ * values. */
+ct_status ct_batch_diagnostics(ct_batch *b, double *host_out);
 
 /* Thread-local description of the last error. */
 const char *ct_last_error(void);

@@ -73,6 +73,22 @@ _SIGS = {
     "ct_mlp_pack": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ct_mlp_infer": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "ct_step_surrogate": (C.c_int, [_cp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
+    "ct_tile_shape_count": (C.c_int, []),
+    "ct_tile_shape": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ct_set_tile_shape": (C.c_int, [_cp, C.c_int, C.c_int]),
+    "ct_autotune": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp, C.POINTER(C.c_int),
+                              C.POINTER(C.c_float)]),
+    "ct_batch_workspace_bytes": (C.c_size_t, [_cp, C.c_int]),
+    "ct_batch_state_elems": (C.c_size_t, [_cp, C.c_int]),
+    "ct_batch_create": (C.c_int, [_cp, C.c_int, C.c_int, _dp, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
+    "ct_batch_destroy": (None, [_vp]),
+    "ct_batch_init_state": (C.c_int, [_vp, _vp, C.c_double]),
+    "ct_batch_load_state": (C.c_int, [_vp, _vp, _vp, C.c_double]),
+    "ct_batch_set_tile_shape": (C.c_int, [_vp, C.c_int]),
+    "ct_batch_tile_shape": (C.c_int, [_vp]),
+    "ct_batch_autotune": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "ct_batch_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double]),
+    "ct_batch_diagnostics": (C.c_int, [_vp, _dp]),
     "ct_last_error": (C.c_char_p, []),
     "ct_version": (C.c_char_p, []),
 }
@@ -244,3 +260,96 @@ def ct_last_error() -> str:
 
 def ct_version() -> str:
     return _L().ct_version().decode()
+
+
+# ---- tile shapes and the autotuner ----------------------------------------------------------
+def ct_tile_shape_count() -> int:
+    return _L().ct_tile_shape_count()
+
+
+def ct_tile_shape(shape: int) -> tuple[int, int]:
+    tx, ty = C.c_int(), C.c_int()
+    _check(_L().ct_tile_shape(shape, C.byref(tx), C.byref(ty)))
+    return tx.value, ty.value
+
+
+def ct_set_tile_shape(case, precision, shape):
+    _check(_L().ct_set_tile_shape(C.byref(_case(case)), precision, shape))
+
+
+def ct_autotune(case, precision, U, U1, work, blob=None, reps=5, stream=None):
+    """Returns (chosen shape, ms per first-stage launch of every shape, -1 where unavailable)."""
+    n = ct_tile_shape_count()
+    sh = C.c_int()
+    ms = (C.c_float * n)()
+    _check(_L().ct_autotune(C.byref(_case(case)), precision, _ptr(U), _ptr(U1), _ptr(work), _ptr(blob), reps,
+                            _stream(stream), C.byref(sh), ms))
+    return sh.value, [float(v) for v in ms]
+
+
+# ---- batched step ---------------------------------------------------------------------------------
+def _cases(cases):
+    arr = (CtCase * len(cases))()
+    for k, c in enumerate(cases):
+        arr[k] = _case(c)
+    return arr
+
+
+def ct_batch_workspace_bytes(cases) -> int:
+    return _L().ct_batch_workspace_bytes(_cases(cases), len(cases))
+
+
+def ct_batch_state_elems(cases) -> int:
+    return _L().ct_batch_state_elems(_cases(cases), len(cases))
+
+
+def ct_batch_create(cases, precision, ufac_rows, work, work_bytes, stream=None) -> int:
+    """Returns the batch handle (an address; free with ct_batch_destroy)."""
+    u = None
+    if ufac_rows is not None:
+        arr = np.ascontiguousarray(ufac_rows, dtype=np.float64)
+        u = arr.ctypes.data_as(_dp)
+    h = _vp()
+    _check(_L().ct_batch_create(_cases(cases), len(cases), precision, u, _ptr(work), work_bytes, _stream(stream),
+                                C.byref(h)))
+    return h.value
+
+
+def ct_batch_destroy(b):
+    _L().ct_batch_destroy(b)
+
+
+def ct_batch_init_state(b, U, cfl):
+    _check(_L().ct_batch_init_state(b, _ptr(U), cfl))
+
+
+def ct_batch_load_state(b, U_src, U, cfl):
+    _check(_L().ct_batch_load_state(b, _ptr(U_src), _ptr(U), cfl))
+
+
+def ct_batch_set_tile_shape(b, shape):
+    _check(_L().ct_batch_set_tile_shape(b, shape))
+
+
+def ct_batch_tile_shape(b) -> int:
+    return _L().ct_batch_tile_shape(b)
+
+
+def ct_batch_autotune(b, U, U1, blob=None, reps=3):
+    n = ct_tile_shape_count()
+    sh = C.c_int()
+    ms = (C.c_float * n)()
+    _check(_L().ct_batch_autotune(b, _ptr(U), _ptr(U1), _ptr(blob), reps, C.byref(sh), ms))
+    return sh.value, [float(v) for v in ms]
+
+
+def ct_batch_step(b, U, U1, blob, nsteps, cfl):
+    _check(_L().ct_batch_step(b, _ptr(U), _ptr(U1), _ptr(blob), nsteps, cfl))
+
+
+def ct_batch_diagnostics(b, ncases: int, raise_nonfinite: bool = False) -> np.ndarray:
+    out = np.zeros((ncases, NDIAG))
+    st = _L().ct_batch_diagnostics(b, out.ctypes.data_as(_dp))
+    if st != 0 and (st != 3 or raise_nonfinite):
+        _check(st)
+    return out

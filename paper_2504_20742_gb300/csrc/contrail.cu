@@ -1,658 +1,28 @@
-// contrail.cu -- fused finite-volume stage kernels and the C ABI (include/contrail.h).
-//
-// One SSP-RK2 step (Sec. 3.2 of Tegethoff & Wheeler, arXiv 2504.20742) is two launches of
-// one fused stage kernel.  Each CTA owns a TX x TY tile of cells and, in shared memory,
-// the primitive variables of the tile plus a two-cell halo (boundary ghosts are built on
-// the fly).  It computes the x-face and r-face Roe fluxes once per face, the flux
-// divergence with the axisymmetric / area geometric sources, the per-cell phase-change
-// source (limited on the flux-updated state), the RK combine, and block partials of the
-// CFL time step and of the conservation diagnostics.  The last CTA to finish reduces
-// the partials in a fixed order (deterministic) and publishes the next time step to the
-// workspace, so that N steps run without any host round trip.
+// contrail.cu -- the C ABI (include/contrail.h) around the fused stage kernels of
+// stage.cuh, plus the auxiliary kernels: initial time step, inflow profile and ambient
+// state, initial field, derived per-cell quantities, pointwise sources and surrogate
+// training data.  Also the tile-shape autotuner and the batched, graph-captured step.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
-#include "../../include/contrail.h"
-#include "flux.cuh"
-#include "mlp_tc.cuh"
-#include "physics.cuh"
+#include "stage.cuh"
 
 namespace ct {
 
-// ---- workspace layout ------------------------------------------------------------------
-constexpr int NPART = 26;   // per-block partial record
-// partial slots: 0 dt min, 1 M, 2 W, 3 E, 4..6 boundary inflow rate (mass, water, energy),
-// 7 active, 8 non-finite, 9..22 max |dU/dt| per field, 23 max ln J_hom, 24 max ln J_het,
-// 25 surrogate fallback count.
-struct WsHeader {
-  double dt_cur;          // time step of the next step
-  double cfl;
-  double b1[4];           // stage-1 boundary inflow rates
-  double diag[CT_NDIAG];  // last completed step
-  double steps;
-  unsigned int counter;   // last-block-done ticket
-  unsigned int setup_magic;
-  int nblocks;
-  int pad;
-};
-constexpr unsigned int SETUP_MAGIC = 0x43544231u;
-constexpr size_t HDR_BYTES = 1024;
-static_assert(sizeof(WsHeader) <= HDR_BYTES, "header");
-
-struct DevCase {
-  int geom, nx, nr, bc_xlo, bc_xhi, bc_rhi, jw, nblocks;
-  double dx, dr, idx, idr, cfl;
-  double area_a, x_throat, wall_len;
-  double p0, T0, Yv0, cp0, gam0;       // nozzle inlet mixture
-  float fdx, fidx, fdr, fidr, fwall_len, farea_a, fixt;   // FP32 copies of the geometry
-  SrcCase sc;
-  const double* inflow;   // nr x NF (plume)
-  const double* amb;      // NF
-  WsHeader* hdr;
-  double* partials;       // nblocks x NPART
-};
-
-// Tile of TX x TY cells per CTA; NT = (TX+1)*TY... rounded to whole warps so that the
-// x-face (33 x 8) and r-face (32 x 9) passes each take a single round of the CTA.
-constexpr int TX = 32, TY = 8, NT = 288, NCELL = TX * TY;
-constexpr int HX = TX + 4, HY = TY + 4;
-
-// Geometry in the state precision (no double->float conversions inside FP32 kernels).
-template <class T>
-struct Geo {
-  T dx, idx, dr, idr, wall_len, area_a, ixt;
-};
-__device__ __forceinline__ Geo<float> geo_of(const DevCase& d, float) {
-  return {d.fdx, d.fidx, d.fdr, d.fidr, d.fwall_len, d.farea_a, d.fixt};
-}
-__device__ __forceinline__ Geo<double> geo_of(const DevCase& d, double) {
-  return {d.dx, d.idx, d.dr, d.idr, d.wall_len, d.area_a, 1.0 / d.x_throat};
-}
-
-// ---- boundary ghost cells (Sec. 4.1; reading A1) ---------------------------------------
-// Conserved state at (i, j), i in [-2, nx+1], j in [-2, nr+1], not both outside.
-// Out of line on purpose: keeps the nozzle inlet's FP64 arithmetic from being hoisted into
-// the interior path of the FP32 kernels.
-template <class T>
-__device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__ U, size_t N, int i, int j,
-                                        T* u14) {
-  const int nx = dc.nx, nr = dc.nr;
-  if (i < 0) {
-    if (dc.bc_xlo == 1) {   // wall: mirror
-      const size_t n = (size_t)j * nx + (-i - 1);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
-      u14[1] = -u14[1];
-    } else if (dc.geom == 0) {   // total-condition subsonic inlet, interior velocity
-      const size_t n = (size_t)j * nx;
-      double u = double(U[N + n]) / double(U[n]);
-      u = u < 0.0 ? 0.0 : u;
-      const double Tg = dc.T0 - u * u / (2.0 * dc.cp0);
-      const double p = dc.p0 * pow(Tg / dc.T0, dc.gam0 / (dc.gam0 - 1.0));
-      const double z[4] = {0, 0, 0, 0};
-      prim_to_cons<T>(p, Tg, u, 0.0, dc.Yv0, z, z, 0.0, u14);
-    } else {   // plume inflow profile
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = T(dc.inflow[j * NF + f]);
-    }
-    return;
-  }
-  if (i >= nx) {
-    const int ii = dc.bc_xhi == 1 ? 2 * nx - 1 - i : nx - 1;
-    const size_t n = (size_t)j * nx + ii;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
-    if (dc.bc_xhi == 1) u14[1] = -u14[1];
-    return;
-  }
-  if (j < 0) {   // axis: mirror with rho*v negated
-    const size_t n = (size_t)(-j - 1) * nx + i;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
-    u14[2] = -u14[2];
-    return;
-  }
-  if (j >= nr) {
-    if (dc.bc_rhi == 0) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = T(dc.amb[f]);
-    } else {
-      const int jj = dc.bc_rhi == 1 ? 2 * nr - 1 - j : nr - 1;
-      const size_t n = (size_t)jj * nx + i;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
-      if (dc.bc_rhi == 1) u14[2] = -u14[2];
-    }
-    return;
-  }
-  const size_t n = (size_t)j * nx + i;
-#pragma unroll
-  for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
-}
-
-__device__ __forceinline__ double area_q1d(const DevCase& dc, double x) {
-  const double s = x / dc.x_throat - 1.0;
-  return 1.0 + dc.area_a * s * s;
-}
-
-// ---- reductions -------------------------------------------------------------------------
-template <class V>
-__device__ __forceinline__ V warp_sum(V v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-template <class V>
-__device__ __forceinline__ V warp_max(V v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    V w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
-}
-template <class V>
-__device__ __forceinline__ V warp_min(V v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    V w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
-}
-// kind: 0 sum, 1 max, 2 min
-__device__ __forceinline__ int slot_kind(int q) { return q == 0 ? 2 : ((q >= 9 && q <= 24) ? 1 : 0); }
-
-// Last CTA: reduce the partial records of all CTAs in a fixed order; returns true in the
-// CTA that did it (red[] then holds the totals).
-__device__ bool last_block_reduce(const DevCase& dc, double* red_smem) {
-  __shared__ unsigned int ticket;
-  __threadfence();   // every thread that wrote partials makes them visible device-wide
-  __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(&dc.hdr->counter, 1u);
-  __syncthreads();
-  if (ticket != (unsigned int)(dc.nblocks - 1)) return false;
-  __threadfence();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  for (int q = warp; q < NPART; q += nwarps) {
-    const int kind = slot_kind(q);
-    double acc = kind == 0 ? 0.0 : (kind == 1 ? -INFINITY : INFINITY);
-    for (int b = lane; b < dc.nblocks; b += 32) {
-      const double v = __ldcg(&dc.partials[(size_t)b * NPART + q]);
-      acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
-    }
-    acc = kind == 0 ? warp_sum(acc) : (kind == 1 ? warp_max(acc) : warp_min(acc));
-    if (lane == 0) red_smem[q] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) dc.hdr->counter = 0u;
-  return true;
-}
-
-// ---- the fused stage kernel ---------------------------------------------------------------
-// STAGE 1: Uout = Uin + dt L(Uin).  STAGE 2: Uout = (Un + Uin + dt L(Uin))/2 (Uout may be Un).
-constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
-template <class T>
-constexpr size_t stage_smem() { return sizeof(T) * (size_t)NF * (HX * HY + 3 * NFACE); }
-// shared memory of the surrogate phase, reusing the (then dead) stencil buffers:
-// activations, streamed weights, outputs, blob header, TMEM slot, mbarrier
-constexpr size_t SM_A = 0, SM_W = SM_A + mlp::ABYTES, SM_OUT = SM_W + 32768, SM_HDR = SM_OUT + 128 * 10 * 4,
-                 SM_TSLOT = SM_HDR + mlp::NFLOAT * 4, SM_MBAR = SM_TSLOT + 16, SM_RES = SM_MBAR + 16,
-                 SURR_SMEM = SM_RES + 288 * 10 * 4;
-constexpr size_t stage_smem_surr() { return stage_smem<float>() > SURR_SMEM ? stage_smem<float>() : SURR_SMEM; }
-
-// Surrogate cells of one tile (called by all threads, only when the tile has at least one):
-// compaction into 128-row tiles and the BF16 tensor-core network.  Each surrogate cell's
-// thread finds its 10 outputs (raw units, held to the training range of their targets) in
-// res[10 * threadIdx.x ...] afterwards.  x: the cell's 16 raw inputs (kind == 2 only).
-__device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ blob, int kind, const float* x, int& nbad,
-                                            unsigned char* smem) {
-  __shared__ int wcnt[NT / 32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float* ghdr = reinterpret_cast<const float*>(blob);
-  const unsigned mask = __ballot_sync(0xffffffffu, kind == 2);
-  if (lane == 0) wcnt[warp] = __popc(mask);
-  __syncthreads();
-  int off = 0, total = 0;
-  for (int w2 = 0; w2 < NT / 32; ++w2) {
-    off += w2 < warp ? wcnt[w2] : 0;
-    total += wcnt[w2];
-  }
-  const int row = off + __popc(mask & ((1u << lane) - 1u));
-  unsigned char* A = smem + SM_A;
-  unsigned char* W = smem + SM_W;
-  float* outs = reinterpret_cast<float*>(smem + SM_OUT);
-  float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
-  float* res = reinterpret_cast<float*>(smem + SM_RES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM_TSLOT);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SM_MBAR);
-  for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
-  if (warp == 0) {
-    tc::tmem_alloc(tc::smem_addr(tslot), 128);
-    tc::tmem_relinquish();
-  }
-  if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(mbar), 1);
-    tc::fence_mbar_init();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tslot;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int c0 = 0; c0 < total; c0 += 128) {
-    const bool mine = kind == 2 && row >= c0 && row < c0 + 128;
-    if (mine) {
-      float v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = (x[q] - hdr[mlp::F_XMEAN + q]) * hdr[mlp::F_XISD + q];
-      mlp::store_row16(A, row - c0, 0, 16, v);
-    }
-    float o[10];
-    ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(mbar), phase, o, blob + mlp::WOFF,
-                             total - c0) && ok;
-    if (tid < 128) {
-#pragma unroll
-      for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
-    }
-    __syncthreads();
-    if (mine) {
-#pragma unroll
-      for (int q = 0; q < 10; ++q)
-        res[tid * 10 + q] = fminf(fmaxf(outs[(row - c0) * 10 + q], hdr[mlp::F_YMIN + q]), hdr[mlp::F_YMAX + q]);
-    }
-    __syncthreads();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
-  if (!ok && tid == 0) nbad += 1;   // a tensor-core wait timed out: the step reports failure
-}
-
-// Source of the FP32 + surrogate path (called by all threads): active cells inside the
-// surrogate's training hull take their rates from the network, the others the plain source
-// (counted as fallbacks); both feed the plain path's tail, so conservation and the limiters
-// are exact.  Adds the source to acc.
-template <class T>
-__device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsigned char* __restrict__ blob, bool cell,
-                                                 const Prim<T>& w, const T* u14, T* acc, T dt, int& nactive,
-                                                 int& nfallback, int& nbad, T& lnJh, T& lnJt, unsigned char* smem) {
-  const float* ghdr = reinterpret_cast<const float*>(blob);
-  int kind = 0;   // 0 inactive, 1 plain source (outside the hull), 2 surrogate
-  Sat<T> st;
-  st.lnSl = st.lnSi = st.lnpv = 0.0;
-  st.pres_l = st.pres_s = st.active = false;
-  T Q[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) Q[f] = T(0);
-  double lnJ2[2] = {-INFINITY, -INFINITY};
-  float x[CT_MLP_IN];
-  if (cell && dc.sc.phase_change) {
-    bool pl, ps;
-    const bool pops = populations(w, pl, ps);
-    if (pops || !clearly_inactive(w)) {
-      st = saturation(w);
-      if (st.active) {
-        mlp_features<T>(w, st, dc.sc.rp2, x);
-        bool inside = true;
-#pragma unroll
-        for (int q = 0; q < CT_MLP_IN; ++q)
-          inside = inside && x[q] >= ghdr[mlp::F_HMIN + q] && x[q] <= ghdr[mlp::F_HMAX + q];
-        kind = inside ? 2 : 1;
-      }
-    }
-  }
-  if (kind == 1) {
-    const Rates<T> r = plain_rates<T>(w, st, dc.sc, lnJ2, nullptr, nullptr);
-    source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
-    nfallback = 1;
-  }
-  // the stencil buffers are dead from here on; tiles without a surrogate cell skip the rest
-  if (__syncthreads_or(kind == 2)) {
-    surrogate_tile(blob, kind, x, nbad, smem);
-    if (kind == 2) {
-      const float* y = reinterpret_cast<const float*>(smem + SM_RES) + 10 * threadIdx.x;
-      const bool nuc = st.lnSl > 0.0;
-      Rates<T> r;
-      r.Jeff = nuc ? T(__expf(y[0])) : T(0);
-      // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
-      r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
-                        (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
-                    : T(0);
-      r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
-      r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
-      r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
-      r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
-      if (nuc) {
-        lnJ2[0] = y[6];
-        if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
-      }
-      source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
-    }
-  }
-  if (cell) {
-    nactive = kind != 0 ? 1 : 0;
-    lnJh = T(lnJ2[0]);
-    lnJt = T(lnJ2[1]);
-#pragma unroll
-    for (int f = 4; f < 13; ++f) acc[f] += Q[f];
-  }
-}
-
-template <class T, int STAGE, bool SURR>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
-    k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T (*qs)[HY][HX] = reinterpret_cast<T (*)[HY][HX]>(smem_raw);                      // primitives
-  T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NF * HX * HY);   // face fluxes
-  T (*fL)[NFACE] = fb + NF;        // reconstructed left state of each face
-  T (*fR)[NFACE] = fb + 2 * NF;    // reconstructed right state of each face
-  __shared__ double red[NT / 32][NPART];
-  __shared__ double fin[NPART];
-
-  const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
-  const size_t N = (size_t)nx * nr;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int tid = threadIdx.x;
-  const double dtd = dc.hdr->dt_cur;
-  const T dt = T(dtd);
-  const Geo<T> g = geo_of(dc, T(0));
-
-  // phase A: halo primitives
-  for (int p = tid; p < HX * HY; p += NT) {
-    const int hi = p % HX, hj = p / HX;
-    const int i = i0 + hi - 2, j = j0 + hj - 2;
-    const bool xin = i >= 0 && i < nx, rin = j >= 0 && j < nr;
-    bool need = (xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1;
-    if (dc.geom == 0) need = need && j == 0;
-    if (!need) continue;
-    T u14[NF];
-    if (xin && rin) {
-      const size_t n = (size_t)j * nx + i;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-    } else {
-      load_ghost<T>(dc, Uin, N, i, j, u14);
-    }
-    Prim<T> w;
-    cons_to_prim<T>(u14, w);
-    qs[0][hj][hi] = w.rho;
-    qs[1][hj][hi] = w.u;
-    qs[2][hj][hi] = w.v;
-    qs[3][hj][hi] = w.p;
-    qs[4][hj][hi] = w.Yv;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      qs[5 + q][hj][hi] = w.ml[q];
-      qs[9 + q][hj][hi] = w.ms[q];
-    }
-    qs[13][hj][hi] = w.ns;
-  }
-  __syncthreads();
-
-  // phase B1: limited x slopes, once per cell, written as the states of its two faces
-  // (tile-local cell c in [-1, TX]; face f lies between cells f-1 and f)
-  for (int p = tid; p < (TX + 2) * TY; p += NT) {
-    const int c = p % (TX + 2) - 1, hj = p / (TX + 2);
-    const int i = i0 + c, j = j0 + hj;
-    if (i > nx || j >= nr) continue;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const T am = qs[f][hj + 2][c + 1], a0 = qs[f][hj + 2][c + 2], a1 = qs[f][hj + 2][c + 3];
-      const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
-      if (c < TX) fL[f][hj * (TX + 1) + c + 1] = a0 + hs;
-      if (c >= 0) fR[f][hj * (TX + 1) + c] = a0 - hs;
-    }
-  }
-  __syncthreads();
-
-  // phase B2: x-face Roe fluxes
-  for (int p = tid; p < (TX + 1) * TY; p += NT) {
-    const int fx = p % (TX + 1), hj = p / (TX + 1);
-    const int i = i0 + fx, j = j0 + hj;
-    if (i > nx || j >= nr) continue;
-    T qL[NF], qR[NF], F[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      qL[f] = fL[f][p];
-      qR[f] = fR[f][p];
-    }
-    roe_flux<T, 0>(qL, qR, F);
-#pragma unroll
-    for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
-  }
-  __syncthreads();
-
-  const int ci = tid % TX, cj = tid / TX;
-  const int i = i0 + ci, j = j0 + cj;
-  const bool cell = tid < NCELL && i < nx && j < nr;
-  T acc[NF];
-  T bm = T(0), bw = T(0), be = T(0);   // boundary inflow rates of this cell's faces
-  T area_w = T(0), area_e = T(0), vol = T(0);
-  if (cell) {
-    const int w = cj * (TX + 1) + ci, e = w + 1;
-    T cw, ce;
-    if (dc.geom == 0) {
-      const T xw = T(i) * g.dx, xe = T(i + 1) * g.dx, xc = (T(i) + T(0.5)) * g.dx;
-      const T sw = xw * g.ixt - T(1), se = xe * g.ixt - T(1), sc = xc * g.ixt - T(1);
-      area_w = T(1) + g.area_a * sw * sw;
-      area_e = T(1) + g.area_a * se * se;
-      const T Ac = T(1) + g.area_a * sc * sc;
-      const T iv = frcp(Ac * g.dx);
-      cw = area_w * iv;
-      ce = area_e * iv;
-      vol = Ac * g.dx;
-    } else {
-      cw = ce = g.idx;
-      area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
-      vol = area_w * g.dx;
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) acc[f] = cw * fb[f][w] - ce * fb[f][e];
-    if (i == 0) {
-      bm += area_w * fb[0][w];
-      bw += area_w * (fb[4][w] + T(k::YL3) * fb[8][w] + T(k::YS3) * fb[12][w]);
-      be += area_w * fb[3][w];
-    }
-    if (i == nx - 1) {
-      bm -= area_e * fb[0][e];
-      bw -= area_e * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
-      be -= area_e * fb[3][e];
-    }
-  }
-
-  if (dc.geom == 1) {
-    __syncthreads();
-    // phase D1: limited r slopes (tile-local row c in [-1, TY]) -> states of the r faces
-    for (int p = tid; p < TX * (TY + 2); p += NT) {
-      const int hi = p % TX, c = p / TX - 1;
-      const int ii = i0 + hi, jj = j0 + c;
-      if (ii >= nx || jj > nr) continue;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const T am = qs[f][c + 1][hi + 2], a0 = qs[f][c + 2][hi + 2], a1 = qs[f][c + 3][hi + 2];
-        const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
-        if (c < TY) fL[f][(c + 1) * TX + hi] = a0 + hs;
-        if (c >= 0) fR[f][c * TX + hi] = a0 - hs;
-      }
-    }
-    __syncthreads();
-    // phase D2: r-face Roe fluxes (face fy lies between tile rows fy-1 and fy)
-    for (int p = tid; p < TX * (TY + 1); p += NT) {
-      const int hi = p % TX, fy = p / TX;
-      const int ii = i0 + hi, jj = j0 + fy;
-      if (ii >= nx || jj > nr) continue;
-      T qL[NF], qR[NF], F[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        qL[f] = fL[f][p];
-        qR[f] = fR[f][p];
-      }
-      roe_flux<T, 1>(qL, qR, F);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
-    }
-    __syncthreads();
-  }
-
-  // phase E: residual, source, update, partial reductions
-  T pM = T(0), pW = T(0), pE = T(0);
-  T dtmin = T(INFINITY);
-  T rmax[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) rmax[f] = T(0);
-  T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
-  int nactive = 0, nbad = 0, nfallback = 0;
-  T u14[NF];
-  Prim<T> w;
-  if (cell) {
-    const size_t n = (size_t)j * nx + i;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-    cons_to_prim<T>(u14, w);
-    if (dc.geom == 1) {
-      const T ijh = frcp(T(j) + T(0.5));
-      const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
-      const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        T Fs = fb[f][cj * TX + ci], Fn = fb[f][(cj + 1) * TX + ci];
-        if (wall && j == dc.jw - 1) Fn = f == 2 ? w.p : T(0);
-        if (wall && j == dc.jw) Fs = f == 2 ? w.p : T(0);
-        acc[f] += cs * Fs - cn * Fn;
-      }
-      acc[2] += w.p * ijh * g.idr;
-      if (j == nr - 1) {
-        const T An = T(nr) * g.dr * g.dx;
-        const int e = (cj + 1) * TX + ci;
-        bm -= An * fb[0][e];
-        bw -= An * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
-        be -= An * fb[3][e];
-      }
-    } else {
-      acc[1] += w.p * fdiv(area_e - area_w, vol);
-    }
-    // phase-change source limited on the flux-updated state
-    T Q[NF];
-    double lnJ2[2];
-    if (!SURR) {
-      const bool act = phase_source<T>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
-      nactive = act ? 1 : 0;
-      lnJh = T(lnJ2[0]);
-      lnJt = T(lnJ2[1]);
-#pragma unroll
-      for (int f = 4; f < 13; ++f) acc[f] += Q[f];
-    }
-  }
-  if (SURR) surrogate_source<T>(dc, blob, cell, w, u14, acc, dt, nactive, nfallback, nbad, lnJh, lnJt, smem_raw);
-  if (cell) {
-    const size_t n = (size_t)j * nx + i;
-    // RK combine
-    T out[NF];
-    if (STAGE == 1) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) out[f] = u14[f] + dt * acc[f];
-    } else {
-      const T idt = frcp(dt);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const T un = Un[f * N + n];
-        out[f] = T(0.5) * un + T(0.5) * (u14[f] + dt * acc[f]);
-        rmax[f] = m_fabs(out[f] - un) * idt;
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      Uout[f * N + n] = out[f];
-      nbad += isfinite(out[f]) ? 0 : 1;
-    }
-    if (STAGE == 2) {
-      Prim<T> wn;
-      cons_to_prim<T>(out, wn);
-      const T c = m_sqrt(wn.c2);
-      T rate = (m_fabs(wn.u) + c) * g.idx;
-      if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
-      dtmin = T(1) / rate;   // times cfl at the end
-      pM = vol * out[0];
-      pW = vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]);
-      pE = vol * out[3];
-    }
-  }
-
-  // block partials: warp shuffles in the state precision, FP64 from the warp level on
-  const int warp = tid >> 5, lane = tid & 31;
-  {
-    T v;
-    v = warp_min(dtmin); if (lane == 0) red[warp][0] = double(v);
-    v = warp_sum(pM); if (lane == 0) red[warp][1] = double(v);
-    v = warp_sum(pW); if (lane == 0) red[warp][2] = double(v);
-    v = warp_sum(pE); if (lane == 0) red[warp][3] = double(v);
-    v = warp_sum(bm); if (lane == 0) red[warp][4] = double(v);
-    v = warp_sum(bw); if (lane == 0) red[warp][5] = double(v);
-    v = warp_sum(be); if (lane == 0) red[warp][6] = double(v);
-    int a = warp_sum(nactive); if (lane == 0) red[warp][7] = a;
-    a = warp_sum(nbad); if (lane == 0) red[warp][8] = a;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      v = warp_max(rmax[f]);
-      if (lane == 0) red[warp][9 + f] = double(v);
-    }
-    v = warp_max(lnJh); if (lane == 0) red[warp][23] = double(v);
-    v = warp_max(lnJt); if (lane == 0) red[warp][24] = double(v);
-    a = warp_sum(nfallback); if (lane == 0) red[warp][25] = a;
-  }
-  __syncthreads();
-  if (tid < NPART) {
-    const int kind = slot_kind(tid);
-    double acc2 = red[0][tid];
-    for (int w2 = 1; w2 < NT / 32; ++w2) {
-      const double v = red[w2][tid];
-      acc2 = kind == 0 ? acc2 + v : (kind == 1 ? fmax(acc2, v) : fmin(acc2, v));
-    }
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    dc.partials[(size_t)b * NPART + tid] = acc2;
-  }
-  if (!last_block_reduce(dc, fin)) return;
-  if (tid == 0) {
-    WsHeader* h = dc.hdr;
-    if (STAGE == 1) {
-      h->b1[0] = fin[4];
-      h->b1[1] = fin[5];
-      h->b1[2] = fin[6];
-    } else {
-      double* d = h->diag;
-      d[0] = dtd;
-      d[1] = fin[1];
-      d[2] = fin[2];
-      d[3] = fin[3];
-      d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
-      d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
-      d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
-      d[7] = fin[7];
-      d[8] = fin[8];
-      for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
-      d[23] = fin[23] * (1.0 / 2.302585092994045684);
-      d[24] = fin[24] * (1.0 / 2.302585092994045684);
-      const double dtn = dc.cfl * fin[0];
-      d[25] = dtn;
-      d[26] = fin[25];
-      h->steps += 1.0;
-      d[27] = h->steps;
-      h->dt_cur = dtn;
-    }
-  }
-}
 
 // ---- time step of a given state (initial step / after a load) --------------------------
 template <class T>
-__global__ void __launch_bounds__(NT) k_dt(DevCase dc, const T* __restrict__ U) {
+__global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__ U) {
+  constexpr int NT = NT_AUX;
   __shared__ double red[NT / 32][NPART];
   __shared__ double fin[NPART];
   const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
@@ -887,9 +257,55 @@ static ct_status cuda_check(const char* where) {
 }
 
 static int case_nr(const ct_case* c) { return c->geom == 1 ? c->nr : 1; }
-static int tiles_x(const ct_case* c) { return (c->nx + TX - 1) / TX; }
-static int tiles_y(const ct_case* c) { return (case_nr(c) + TY - 1) / TY; }
-static int num_blocks(const ct_case* c) { return tiles_x(c) * tiles_y(c); }
+
+// ---- tile shapes ------------------------------------------------------------------------
+namespace ct {
+const StageSet* stage_set_32x8();
+const StageSet* stage_set_16x16();
+const StageSet* stage_set_32x16();
+const StageSet* stage_set_64x8();
+const StageSet* stage_set(int shape) {
+  switch (shape) {
+    case 1: return stage_set_16x16();
+    case 2: return stage_set_32x16();
+    case 3: return stage_set_64x8();
+    default: return stage_set_32x8();
+  }
+}
+}  // namespace ct
+
+static int prec_index(int precision) { return precision == CT_FP64 ? 0 : (precision == CT_FP32 ? 1 : 2); }
+static int tiles_x(const ct_case* c, int shape) {
+  const int tx = stage_set(shape)->tx;
+  return (c->nx + tx - 1) / tx;
+}
+static int tiles_y(const ct_case* c, int shape) {
+  const int ty = stage_set(shape)->ty;
+  return (case_nr(c) + ty - 1) / ty;
+}
+static int num_blocks(const ct_case* c, int shape) { return tiles_x(c, shape) * tiles_y(c, shape); }
+// partial records the workspace holds: enough for every shape
+static int max_blocks(const ct_case* c) {
+  int m = 0;
+  for (int s = 0; s < NSHAPES; ++s) m = std::max(m, num_blocks(c, s));
+  return m;
+}
+
+// Shape chosen per (geometry, grid, precision): set by the autotuner or by the caller,
+// else shape 0.  The state does not depend on the choice; only the speed does.
+static std::mutex g_shape_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_shape;
+static std::tuple<int, int, int, int> shape_key(const ct_case* c, int precision) {
+  return std::make_tuple(c->geom, c->nx, case_nr(c), prec_index(precision));
+}
+static int shape_for(const ct_case* c, int precision) {
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  auto it = g_shape.find(shape_key(c, precision));
+  return it == g_shape.end() ? 0 : it->second;
+}
+static bool shape_usable(int shape, int precision) {
+  return shape >= 0 && shape < NSHAPES && stage_set(shape)->stage[prec_index(precision)][0] != nullptr;
+}
 
 static ct_status validate(const ct_case* c, int precision) {
   if (!c) return fail(CT_ERR_ARG, "null case");
@@ -915,11 +331,11 @@ static size_t ws_bytes(const ct_case* c) {
   size_t b = HDR_BYTES;
   b += align256(nr * NF * sizeof(double));
   b += align256(NF * sizeof(double));
-  b += align256((size_t)num_blocks(c) * NPART * sizeof(double));
+  b += align256((size_t)max_blocks(c) * NPART * sizeof(double));
   return b;
 }
 
-static DevCase make_dev(const ct_case* c, void* work) {
+static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   DevCase d;
   memset(&d, 0, sizeof(d));
   d.geom = c->geom;
@@ -961,8 +377,27 @@ static DevCase make_dev(const ct_case* c, void* work) {
   d.amb = (const double*)(base + off);
   off += align256(NF * sizeof(double));
   d.partials = (double*)(base + off);
-  d.nblocks = num_blocks(c);
+  d.nblocks = num_blocks(c, shape);
   return d;
+}
+
+// Time `reps` launches of one stage with CUDA events on the stream; returns ms per launch.
+template <class F>
+static ct_status time_launches(F&& launch, int reps, cudaStream_t st, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_check("event");
+  launch();   // warm-up (instruction cache, first-touch of the kernel)
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps; ++r) launch();
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
+  *ms = t / (float)reps;
+  return cuda_check("autotune");
 }
 
 extern "C" {
@@ -1016,10 +451,10 @@ static ct_status launch_dt(const ct_case* c, int precision, void* work, const vo
   DevCase d = make_dev(c, work);
   d.cfl = cfl;
   const size_t N = (size_t)c->nx * case_nr(c);
-  int grid = (int)std::min<size_t>((N + NT - 1) / NT, (size_t)d.nblocks);
+  int grid = (int)std::min<size_t>((N + NT_AUX - 1) / NT_AUX, (size_t)d.nblocks);
   d.nblocks = grid;
-  if (precision == CT_FP64) k_dt<double><<<grid, NT, 0, st>>>(d, (const double*)U);
-  else k_dt<float><<<grid, NT, 0, st>>>(d, (const float*)U);
+  if (precision == CT_FP64) k_dt<double><<<grid, NT_AUX, 0, st>>>(d, (const double*)U);
+  else k_dt<float><<<grid, NT_AUX, 0, st>>>(d, (const float*)U);
   return cuda_check("k_dt");
 }
 
@@ -1053,58 +488,53 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   return launch_dt(c, precision, work, U, cfl, st);
 }
 
-static bool g_attr_done[3] = {false, false, false};
+static std::mutex g_attr_mu;
+static bool g_attr_done[NSHAPES][3];
 
-static ct_status set_stage_attrs(int precision) {
-  const int p = precision == CT_FP64 ? 0 : (precision == CT_FP32 ? 1 : 2);
-  if (g_attr_done[p]) return CT_OK;
-  cudaError_t e;
-  if (p == 0) {
-    e = cudaFuncSetAttribute(k_stage<double, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)stage_smem<double>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<double, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stage_smem<double>());
-  } else if (p == 1) {
-    e = cudaFuncSetAttribute(k_stage<float, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)stage_smem<float>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<float, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stage_smem<float>());
-  } else {
-    e = cudaFuncSetAttribute(k_stage<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)stage_smem_surr());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stage_smem_surr());
+// Opt the kernels of one (shape, precision) into their dynamic shared memory, once.
+static ct_status set_stage_attrs(int shape, int precision) {
+  const int p = prec_index(precision);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done[shape][p]) return CT_OK;
+  const StageSet* ss = stage_set(shape);
+  cudaError_t e = cudaSuccess;
+  for (int st = 0; st < 2 && e == cudaSuccess; ++st) {
+    if (ss->stage[p][st])
+      e = cudaFuncSetAttribute(ss->stage[p][st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
+    if (e == cudaSuccess && ss->batch[p][st])
+      e = cudaFuncSetAttribute(ss->batch[p][st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
-  g_attr_done[p] = true;
+  g_attr_done[shape][p] = true;
   return CT_OK;
 }
 
+// One stage launch of one case (stage 1: U -> U1; stage 2: U1, U -> U).
+static void launch_stage(const StageSet* ss, int p, int stage, const DevCase& d, dim3 grid, const void* Uin,
+                         const void* Un, void* Uout, const void* blob, cudaStream_t st) {
+  DevCase dc = d;
+  const void* a1 = Uin;
+  const void* a2 = Un;
+  void* a3 = Uout;
+  const void* a4 = blob;
+  void* args[] = {&dc, &a1, &a2, &a3, &a4};
+  cudaLaunchKernel(ss->stage[p][stage - 1], grid, dim3(ss->nt), args, ss->smem[p], st);
+}
+
 static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
-                               cudaStream_t st, const void* blob = nullptr) {
-  ct_status s = set_stage_attrs(precision);
+                               cudaStream_t st, const void* blob = nullptr, int shape = -1) {
+  if (shape < 0) shape = shape_for(c, precision);
+  if (!shape_usable(shape, precision)) shape = 0;
+  ct_status s = set_stage_attrs(shape, precision);
   if (s != CT_OK) return s;
-  DevCase d = make_dev(c, work);
+  const StageSet* ss = stage_set(shape);
+  const int p = prec_index(precision);
+  DevCase d = make_dev(c, work, shape);
   d.cfl = cfl;
-  dim3 grid(tiles_x(c), tiles_y(c));
-  const unsigned char* b = (const unsigned char*)blob;
+  dim3 grid(tiles_x(c, shape), tiles_y(c, shape));
   for (int k2 = 0; k2 < nsteps; ++k2) {
-    if (precision == CT_FP64) {
-      const size_t sm = stage_smem<double>();
-      k_stage<double, 1, false><<<grid, NT, sm, st>>>(d, (const double*)U, nullptr, (double*)U1, nullptr);
-      k_stage<double, 2, false><<<grid, NT, sm, st>>>(d, (const double*)U1, (const double*)U, (double*)U, nullptr);
-    } else if (precision == CT_FP32) {
-      const size_t sm = stage_smem<float>();
-      k_stage<float, 1, false><<<grid, NT, sm, st>>>(d, (const float*)U, nullptr, (float*)U1, nullptr);
-      k_stage<float, 2, false><<<grid, NT, sm, st>>>(d, (const float*)U1, (const float*)U, (float*)U, nullptr);
-    } else {
-      const size_t sm = stage_smem_surr();
-      k_stage<float, 1, true><<<grid, NT, sm, st>>>(d, (const float*)U, nullptr, (float*)U1, b);
-      k_stage<float, 2, true><<<grid, NT, sm, st>>>(d, (const float*)U1, (const float*)U, (float*)U, b);
-    }
+    launch_stage(ss, p, 1, d, grid, U, nullptr, U1, blob, st);
+    launch_stage(ss, p, 2, d, grid, U1, U, U, blob, st);
   }
   return cuda_check("k_stage");
 }
@@ -1160,6 +590,7 @@ ct_status ct_diagnostics(const void* work, double* host_out, int nout, void* str
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("diag sync");
   memcpy(host_out, tmp, sizeof(double) * nout);
   if (tmp[8] != 0.0) return fail(CT_ERR_NONFINITE, "the last step produced non-finite values");
+  if (tmp[28] != 0.0) return fail(CT_ERR_TIMEOUT, "a tensor-core wait of the last step gave up");
   return CT_OK;
 }
 
@@ -1249,7 +680,8 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
     snprintf(g_err, sizeof(g_err),
              "case needs %zu bytes of scratch but the static scratch holds %zu (about %d tiles of %dx%d cells); "
              "use ct_step with a caller workspace",
-             need, STATIC_SCRATCH_BYTES, (int)((STATIC_SCRATCH_BYTES - HDR_BYTES) / (NPART * sizeof(double))), TX, TY);
+             need, STATIC_SCRATCH_BYTES, (int)((STATIC_SCRATCH_BYTES - HDR_BYTES) / (NPART * sizeof(double))),
+             stage_set(0)->tx, stage_set(0)->ty);
     return CT_ERR_SIZE;
   }
   void* work = nullptr;
@@ -1261,6 +693,351 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   if ((s = cuda_check("ct_step_static setup")) != CT_OK) return s;
   if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
   return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st);
+}
+
+// ---- tile shapes and the autotuner ------------------------------------------------------
+int ct_tile_shape_count(void) { return NSHAPES; }
+
+ct_status ct_tile_shape(int shape, int* tx, int* ty) {
+  if (shape < 0 || shape >= NSHAPES || !tx || !ty) return fail(CT_ERR_ARG, "ct_tile_shape: bad argument");
+  *tx = stage_set(shape)->tx;
+  *ty = stage_set(shape)->ty;
+  return CT_OK;
+}
+
+ct_status ct_set_tile_shape(const ct_case* c, int precision, int shape) {
+  ct_status s = validate(c, precision);
+  if (s != CT_OK) return s;
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  if (shape < 0) {
+    g_shape.erase(shape_key(c, precision));
+    return CT_OK;
+  }
+  if (!shape_usable(shape, precision)) return fail(CT_ERR_ARG, "tile shape not available for this precision");
+  g_shape[shape_key(c, precision)] = shape;
+  return CT_OK;
+}
+
+ct_status ct_autotune(const ct_case* c, int precision, const void* U, void* U1, void* work, const void* blob, int reps,
+                      void* stream, int* shape_out, float* ms_out) {
+  ct_status s = validate(c, precision);
+  if (s != CT_OK) return s;
+  if (!U || !U1 || !work || U == U1) return fail(CT_ERR_ARG, "ct_autotune: bad buffers");
+  if (precision == CT_FP32_MLP && (!blob || ((uintptr_t)blob & 15) != 0)) return fail(CT_ERR_ARG, "ct_autotune: blob");
+  if (reps < 1) return fail(CT_ERR_ARG, "ct_autotune: reps < 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int p = prec_index(precision);
+  int best = -1;
+  float best_ms = 0.0f;
+  for (int sh = 0; sh < NSHAPES; ++sh) {
+    float ms = -1.0f;
+    if (shape_usable(sh, precision)) {
+      if ((s = set_stage_attrs(sh, precision)) != CT_OK) return s;
+      const StageSet* ss = stage_set(sh);
+      DevCase d = make_dev(c, work, sh);
+      const dim3 grid(tiles_x(c, sh), tiles_y(c, sh));
+      // stage 1 only: it reads U and writes the scratch state U1, so U is left as it was
+      auto launch = [&]() { launch_stage(ss, p, 1, d, grid, U, nullptr, U1, blob, st); };
+      if ((s = time_launches(launch, reps, st, &ms)) != CT_OK) return s;
+      if (best < 0 || ms < best_ms) {
+        best = sh;
+        best_ms = ms;
+      }
+    }
+    if (ms_out) ms_out[sh] = ms;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[shape_key(c, precision)] = best;
+  }
+  if (shape_out) *shape_out = best;
+  return CT_OK;
+}
+
+// ---- batched persistent step ---------------------------------------------------------------
+}  // extern "C"
+
+struct ct_batch {
+  std::vector<ct_case> cases;
+  int precision = CT_FP32;
+  int shape = 0;
+  cudaStream_t stream = nullptr;   // the caller's
+  cudaStream_t cap = nullptr;      // private stream the step graphs are captured on
+  char* work = nullptr;            // device workspace (caller-owned)
+  BatchDev* bd = nullptr;          // its head
+  double* diag = nullptr;          // ncases x CT_NDIAG gather area
+  std::vector<size_t> case_off;    // byte offset of each case's workspace
+  std::vector<long long> state_off;
+  int grid = 0;                    // persistent CTAs
+  // the captured graph of the last ct_batch_step call and what it was captured for
+  cudaGraphExec_t exec = nullptr;
+  const void *g_U = nullptr, *g_U1 = nullptr, *g_blob = nullptr;
+  int g_steps = -1, g_shape = -1;
+  double g_cfl = 0.0;
+};
+
+static size_t batch_head_bytes(int ncases) {
+  return align256(sizeof(BatchDev)) + align256((size_t)ncases * CT_NDIAG * sizeof(double));
+}
+
+static ct_status batch_validate(const ct_case* cases, int ncases, int precision) {
+  if (!cases || ncases < 1 || ncases > MAX_BATCH) return fail(CT_ERR_ARG, "ncases out of range [1, 256]");
+  if (precision != CT_FP32 && precision != CT_FP32_MLP) return fail(CT_ERR_ARG, "batched steps are FP32 or FP32_MLP");
+  for (int k = 0; k < ncases; ++k) {
+    ct_status s = validate(&cases[k], precision);
+    if (s != CT_OK) return s;
+    if (cases[k].geom != 1) return fail(CT_ERR_ARG, "batched cases must be axisymmetric plumes (geom 1)");
+  }
+  return CT_OK;
+}
+
+// Upload the work list and case table for the batch's current tile shape.
+static ct_status batch_upload(ct_batch* b) {
+  const int n = (int)b->cases.size();
+  std::vector<BatchDev> hv(1);
+  BatchDev& h = hv[0];
+  memset(&h, 0, sizeof(h));
+  h.ncases = n;
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  // largest cases first, so the last tiles handed out are from the small cases
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c2) {
+    return num_blocks(&b->cases[a], b->shape) > num_blocks(&b->cases[c2], b->shape);
+  });
+  int t = 0;
+  for (int q = 0; q < n; ++q) {
+    const int k = order[q];
+    h.tile_start[q] = t;
+    h.case_of[q] = k;
+    t += num_blocks(&b->cases[k], b->shape);
+  }
+  h.tile_start[n] = t;
+  h.total_tiles = t;
+  for (int k = 0; k < n; ++k) {
+    h.tiles_x[k] = tiles_x(&b->cases[k], b->shape);
+    h.state_off[k] = b->state_off[k];
+    h.cases[k] = make_dev(&b->cases[k], b->work + b->case_off[k], b->shape);
+  }
+  if (cudaMemcpyAsync(b->bd, &h, sizeof(BatchDev), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return cuda_check("batch table copy");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return cuda_check("batch table sync");
+  // persistent grid: every SM full, never more CTAs than tiles
+  ct_status s = set_stage_attrs(b->shape, b->precision);
+  if (s != CT_OK) return s;
+  const StageSet* ss = stage_set(b->shape);
+  const int p = prec_index(b->precision);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // The runtime's occupancy calculator assumes one CTA per SM for kernels that use TMEM;
+  // every CTA here gives up its allocation permit at once, so take the register and
+  // shared-memory limit of the plain FP32 kernel (same registers) at this shared memory.
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ss->batch[1][0], ss->nt, ss->smem[p]) != cudaSuccess)
+    return cuda_check("occupancy");
+  per_sm = std::max(1, per_sm);
+  b->grid = std::min(t, nsm * per_sm);
+  return CT_OK;
+}
+
+static void batch_launch(ct_batch* b, int stage, const void* Uin, const void* Un, void* Uout, const void* blob,
+                         double cfl, cudaStream_t st) {
+  const StageSet* ss = stage_set(b->shape);
+  const int p = prec_index(b->precision);
+  BatchDev* bd = b->bd;
+  const void* a1 = Uin;
+  const void* a2 = Un;
+  void* a3 = Uout;
+  const void* a4 = blob;
+  double a5 = cfl;
+  void* args[] = {&bd, &a1, &a2, &a3, &a4, &a5};
+  cudaLaunchKernel(ss->batch[p][stage - 1], dim3(b->grid), dim3(ss->nt), args, ss->smem[p], st);
+}
+
+__global__ void k_batch_diag(const BatchDev* __restrict__ bd, double* __restrict__ out) {
+  const int k = blockIdx.x, q = threadIdx.x;
+  if (k < bd->ncases && q < CT_NDIAG) out[(size_t)k * CT_NDIAG + q] = bd->cases[k].hdr->diag[q];
+}
+
+extern "C" {
+
+size_t ct_batch_workspace_bytes(const ct_case* cases, int ncases) {
+  if (batch_validate(cases, ncases, CT_FP32) != CT_OK) return 0;
+  size_t b = batch_head_bytes(ncases);
+  for (int k = 0; k < ncases; ++k) b += align256(ws_bytes(&cases[k]));
+  return b;
+}
+
+size_t ct_batch_state_elems(const ct_case* cases, int ncases) {
+  if (batch_validate(cases, ncases, CT_FP32) != CT_OK) return 0;
+  size_t n = 0;
+  for (int k = 0; k < ncases; ++k) n += (size_t)NF * cases[k].nx * case_nr(&cases[k]);
+  return n;
+}
+
+ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const double* ufac_rows_host, void* work,
+                          size_t work_bytes, void* stream, ct_batch** out) {
+  ct_status s = batch_validate(cases, ncases, precision);
+  if (s != CT_OK) return s;
+  if (!work || !out) return fail(CT_ERR_ARG, "null workspace or handle");
+  if (((uintptr_t)work & 255) != 0) return fail(CT_ERR_ARG, "workspace must be 256-byte aligned");
+  if (work_bytes < ct_batch_workspace_bytes(cases, ncases)) return fail(CT_ERR_SIZE, "workspace too small");
+  ct_batch* b = new ct_batch();
+  b->cases.assign(cases, cases + ncases);
+  b->precision = precision;
+  b->stream = (cudaStream_t)stream;
+  b->work = (char*)work;
+  b->bd = (BatchDev*)work;
+  b->diag = (double*)((char*)work + align256(sizeof(BatchDev)));
+  size_t off = batch_head_bytes(ncases);
+  long long so = 0;
+  size_t row = 0;
+  for (int k = 0; k < ncases; ++k) {
+    b->case_off.push_back(off);
+    b->state_off.push_back(so);
+    off += align256(ws_bytes(&cases[k]));
+    so += (long long)NF * cases[k].nx * case_nr(&cases[k]);
+  }
+  // per-case workspace: header, inflow profile and ambient state
+  for (int k = 0; k < ncases && s == CT_OK; ++k) {
+    const ct_case* c = &cases[k];
+    s = ct_setup(c, precision, ufac_rows_host ? ufac_rows_host + row : nullptr, b->work + b->case_off[k],
+                 ws_bytes(c), stream);
+    row += (size_t)case_nr(c);
+  }
+  if (s == CT_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    s = cuda_check("capture stream");
+  if (s == CT_OK) s = batch_upload(b);
+  if (s != CT_OK) {
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return CT_OK;
+}
+
+void ct_batch_destroy(ct_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+ct_status ct_batch_init_state(ct_batch* b, void* U, double cfl) {
+  if (!b || !U) return fail(CT_ERR_ARG, "null batch or state");
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    ct_status s = ct_init_state(&b->cases[k], b->precision, b->work + b->case_off[k], (float*)U + b->state_off[k], cfl,
+                                b->stream);
+    if (s != CT_OK) return s;
+  }
+  return CT_OK;
+}
+
+ct_status ct_batch_load_state(ct_batch* b, const void* U_src, void* U, double cfl) {
+  if (!b || !U || !U_src) return fail(CT_ERR_ARG, "null batch or state");
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    ct_status s = ct_load_state(&b->cases[k], b->precision, b->work + b->case_off[k],
+                                (const float*)U_src + b->state_off[k], (float*)U + b->state_off[k], cfl, b->stream);
+    if (s != CT_OK) return s;
+  }
+  return CT_OK;
+}
+
+ct_status ct_batch_set_tile_shape(ct_batch* b, int shape) {
+  if (!b) return fail(CT_ERR_ARG, "null batch");
+  if (shape < 0 || shape >= NSHAPES || !stage_set(shape)->batch[prec_index(b->precision)][0])
+    return fail(CT_ERR_ARG, "tile shape not available");
+  if (shape == b->shape) return CT_OK;
+  const int old = b->shape;
+  b->shape = shape;
+  ct_status s = batch_upload(b);
+  if (s != CT_OK) b->shape = old;
+  return s;
+}
+
+int ct_batch_tile_shape(const ct_batch* b) { return b ? b->shape : -1; }
+
+ct_status ct_batch_autotune(ct_batch* b, const void* U, void* U1, const void* blob, int reps, int* shape_out,
+                            float* ms_out) {
+  if (!b || !U || !U1 || U == U1) return fail(CT_ERR_ARG, "ct_batch_autotune: bad buffers");
+  if (b->precision == CT_FP32_MLP && (!blob || ((uintptr_t)blob & 15) != 0))
+    return fail(CT_ERR_ARG, "ct_batch_autotune: blob");
+  if (reps < 1) return fail(CT_ERR_ARG, "ct_batch_autotune: reps < 1");
+  int best = -1;
+  float best_ms = 0.0f;
+  ct_status s = CT_OK;
+  for (int sh = 0; sh < NSHAPES; ++sh) {
+    float ms = -1.0f;
+    if (stage_set(sh)->batch[prec_index(b->precision)][0]) {
+      if ((s = ct_batch_set_tile_shape(b, sh)) != CT_OK) return s;
+      // stage 1 only: it reads U and writes the scratch state U1
+      auto launch = [&]() { batch_launch(b, 1, U, nullptr, U1, blob, 0.5, b->stream); };
+      if ((s = time_launches(launch, reps, b->stream, &ms)) != CT_OK) return s;
+      if (best < 0 || ms < best_ms) {
+        best = sh;
+        best_ms = ms;
+      }
+    }
+    if (ms_out) ms_out[sh] = ms;
+  }
+  if ((s = ct_batch_set_tile_shape(b, best)) != CT_OK) return s;
+  if (shape_out) *shape_out = best;
+  return CT_OK;
+}
+
+ct_status ct_batch_step(ct_batch* b, void* U, void* U1, const void* blob, int nsteps, double cfl) {
+  if (!b || !U || !U1 || U == U1) return fail(CT_ERR_ARG, "ct_batch_step: bad buffers");
+  if (b->precision == CT_FP32_MLP && (!blob || ((uintptr_t)blob & 15) != 0))
+    return fail(CT_ERR_ARG, "ct_batch_step: FP32_MLP needs a 16-byte aligned surrogate blob");
+  if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
+  if (nsteps == 0) return CT_OK;
+  const bool same = b->exec && b->g_U == U && b->g_U1 == U1 && b->g_blob == blob && b->g_steps == nsteps &&
+                    b->g_cfl == cfl && b->g_shape == b->shape;
+  if (!same) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    // capture the 2 * nsteps launches once; later calls with the same arguments replay it
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_check("capture");
+    for (int k = 0; k < nsteps; ++k) {
+      batch_launch(b, 1, U, nullptr, U1, blob, cfl, b->cap);
+      batch_launch(b, 2, U1, U, U, blob, cfl, b->cap);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0ULL);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return fail(CT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    b->g_U = U;
+    b->g_U1 = U1;
+    b->g_blob = blob;
+    b->g_steps = nsteps;
+    b->g_cfl = cfl;
+    b->g_shape = b->shape;
+  }
+  if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return cuda_check("graph launch");
+  return CT_OK;
+}
+
+ct_status ct_batch_diagnostics(ct_batch* b, double* host_out) {
+  if (!b || !host_out) return fail(CT_ERR_ARG, "null batch or output");
+  const int n = (int)b->cases.size();
+  k_batch_diag<<<n, 32, 0, b->stream>>>(b->bd, b->diag);
+  if (cudaMemcpyAsync(host_out, b->diag, (size_t)n * CT_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, b->stream) !=
+      cudaSuccess)
+    return cuda_check("batch diag copy");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return cuda_check("batch diag sync");
+  for (int k = 0; k < n; ++k)
+    if (host_out[(size_t)k * CT_NDIAG + 8] != 0.0) return fail(CT_ERR_NONFINITE, "a case produced non-finite values");
+  for (int k = 0; k < n; ++k)
+    if (host_out[(size_t)k * CT_NDIAG + 28] != 0.0)
+      return fail(CT_ERR_TIMEOUT, "a tensor-core wait of the last step gave up");
+  return CT_OK;
 }
 
 ct_status ct_mlp_dataset(const ct_case* c, const double* U, int n, float* X, float* Y, float* M, void* stream) {

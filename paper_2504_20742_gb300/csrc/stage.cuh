@@ -1,0 +1,854 @@
+// stage.cuh -- the fused finite-volume stage (one SSP-RK2 stage of Sec. 3.2 of Tegethoff &
+// Wheeler, arXiv 2504.20742), templated on the tile shape, and its two launch forms: one CTA
+// per tile of one case (k_stage), and persistent CTAs over a work list of the tiles of many
+// cases (k_batch_stage).
+//
+// Each CTA owns a TX x TY tile of cells and, in shared memory, the primitive variables of
+// the tile plus a two-cell halo (boundary ghosts are built on the fly).  It computes the
+// x-face and r-face Roe fluxes once per face, the flux divergence with the axisymmetric /
+// area geometric sources, the per-cell phase-change source (limited on the flux-updated
+// state), the RK combine, and block partials of the CFL time step and of the conservation
+// diagnostics.  The last CTA of a case to finish reduces the partials in a fixed order
+// (deterministic) and publishes the next time step to the workspace, so that N steps run
+// without any host round trip.  Per-cell results do not depend on the tile shape.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "../../include/contrail.h"
+#include "flux.cuh"
+#include "mlp_tc.cuh"
+#include "physics.cuh"
+
+namespace ct {
+
+
+// ---- workspace layout ------------------------------------------------------------------
+constexpr int NPART = 27;   // per-block partial record
+// partial slots: 0 dt min, 1 M, 2 W, 3 E, 4..6 boundary inflow rate (mass, water, energy),
+// 7 active, 8 non-finite, 9..22 max |dU/dt| per field, 23 max ln J_hom, 24 max ln J_het,
+// 25 surrogate fallback count, 26 tensor-core wait timeouts.  Stage 1 fills only 4..6 and
+// 26 (the others are written as zero).
+struct WsHeader {
+  double dt_cur;          // time step of the next step
+  double cfl;
+  double b1[4];           // stage-1 boundary inflow rates (0..2) and timeouts (3)
+  double diag[CT_NDIAG];  // last completed step
+  double steps;
+  unsigned int counter;   // last-block-done ticket
+  unsigned int setup_magic;
+  int nblocks;
+  int pad;
+};
+constexpr unsigned int SETUP_MAGIC = 0x43544231u;
+constexpr size_t HDR_BYTES = 1024;
+static_assert(sizeof(WsHeader) <= HDR_BYTES, "header");
+
+struct DevCase {
+  int geom, nx, nr, bc_xlo, bc_xhi, bc_rhi, jw, nblocks;
+  double dx, dr, idx, idr, cfl;
+  double area_a, x_throat, wall_len;
+  double p0, T0, Yv0, cp0, gam0;       // nozzle inlet mixture
+  float fdx, fidx, fdr, fidr, fwall_len, farea_a, fixt;   // FP32 copies of the geometry
+  SrcCase sc;
+  const double* inflow;   // nr x NF (plume)
+  const double* amb;      // NF
+  WsHeader* hdr;
+  double* partials;       // nblocks x NPART
+};
+
+// Tile of TX x TY cells per CTA with a two-cell halo (HX x HY).  NT threads: the larger of
+// the x-face ((TX+1) x TY) and r-face (TX x (TY+1)) counts rounded up to whole warps, so that
+// each face pass takes a single round of the CTA.  MINB: CTAs per SM the register budget is
+// set for (two for the FP32 kernels of tiles up to 320 threads).
+template <int TX_, int TY_>
+struct Tile {
+  static constexpr int TX = TX_, TY = TY_, HX = TX + 4, HY = TY + 4, NCELL = TX * TY;
+  static constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
+  static constexpr int NT = (NFACE + 31) / 32 * 32;
+  template <class T>
+  static constexpr int minb() { return sizeof(T) == 4 && NT <= 320 ? 2 : 1; }
+  template <class T>
+  static constexpr size_t smem() { return sizeof(T) * (size_t)NF * (HX * HY + 3 * NFACE); }
+};
+// thread count of the auxiliary kernels (time step of a given state)
+constexpr int NT_AUX = 288;
+
+// Geometry in the state precision (no double->float conversions inside FP32 kernels).
+template <class T>
+struct Geo {
+  T dx, idx, dr, idr, wall_len, area_a, ixt;
+};
+__device__ __forceinline__ Geo<float> geo_of(const DevCase& d, float) {
+  return {d.fdx, d.fidx, d.fdr, d.fidr, d.fwall_len, d.farea_a, d.fixt};
+}
+__device__ __forceinline__ Geo<double> geo_of(const DevCase& d, double) {
+  return {d.dx, d.idx, d.dr, d.idr, d.wall_len, d.area_a, 1.0 / d.x_throat};
+}
+
+// ---- boundary ghost cells (Sec. 4.1; reading A1) ---------------------------------------
+// Conserved state at (i, j), i in [-2, nx+1], j in [-2, nr+1], not both outside.
+// Out of line on purpose: keeps the nozzle inlet's FP64 arithmetic from being hoisted into
+// the interior path of the FP32 kernels.
+template <class T>
+__device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__ U, size_t N, int i, int j,
+                                        T* u14) {
+  const int nx = dc.nx, nr = dc.nr;
+  if (i < 0) {
+    if (dc.bc_xlo == 1) {   // wall: mirror
+      const size_t n = (size_t)j * nx + (-i - 1);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+      u14[1] = -u14[1];
+    } else if (dc.geom == 0) {   // total-condition subsonic inlet, interior velocity
+      const size_t n = (size_t)j * nx;
+      double u = double(U[N + n]) / double(U[n]);
+      u = u < 0.0 ? 0.0 : u;
+      const double Tg = dc.T0 - u * u / (2.0 * dc.cp0);
+      const double p = dc.p0 * pow(Tg / dc.T0, dc.gam0 / (dc.gam0 - 1.0));
+      const double z[4] = {0, 0, 0, 0};
+      prim_to_cons<T>(p, Tg, u, 0.0, dc.Yv0, z, z, 0.0, u14);
+    } else {   // plume inflow profile
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = T(dc.inflow[j * NF + f]);
+    }
+    return;
+  }
+  if (i >= nx) {
+    const int ii = dc.bc_xhi == 1 ? 2 * nx - 1 - i : nx - 1;
+    const size_t n = (size_t)j * nx + ii;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    if (dc.bc_xhi == 1) u14[1] = -u14[1];
+    return;
+  }
+  if (j < 0) {   // axis: mirror with rho*v negated
+    const size_t n = (size_t)(-j - 1) * nx + i;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    u14[2] = -u14[2];
+    return;
+  }
+  if (j >= nr) {
+    if (dc.bc_rhi == 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = T(dc.amb[f]);
+    } else {
+      const int jj = dc.bc_rhi == 1 ? 2 * nr - 1 - j : nr - 1;
+      const size_t n = (size_t)jj * nx + i;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+      if (dc.bc_rhi == 1) u14[2] = -u14[2];
+    }
+    return;
+  }
+  const size_t n = (size_t)j * nx + i;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+}
+
+__device__ __forceinline__ double area_q1d(const DevCase& dc, double x) {
+  const double s = x / dc.x_throat - 1.0;
+  return 1.0 + dc.area_a * s * s;
+}
+
+// ---- reductions -------------------------------------------------------------------------
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class V>
+__device__ __forceinline__ V warp_max(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    V w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+template <class V>
+__device__ __forceinline__ V warp_min(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    V w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+// kind: 0 sum, 1 max, 2 min
+__device__ __forceinline__ int slot_kind(int q) { return q == 0 ? 2 : ((q >= 9 && q <= 24) ? 1 : 0); }
+
+// Last CTA: reduce the partial records of all CTAs in a fixed order; returns true in the
+// CTA that did it (red[] then holds the totals).
+__device__ inline bool last_block_reduce(const DevCase& dc, double* red_smem) {
+  __shared__ unsigned int ticket;
+  __threadfence();   // every thread that wrote partials makes them visible device-wide
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&dc.hdr->counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(dc.nblocks - 1)) return false;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  for (int q = warp; q < NPART; q += nwarps) {
+    const int kind = slot_kind(q);
+    double acc = kind == 0 ? 0.0 : (kind == 1 ? -INFINITY : INFINITY);
+    for (int b = lane; b < dc.nblocks; b += 32) {
+      const double v = __ldcg(&dc.partials[(size_t)b * NPART + q]);
+      acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
+    }
+    acc = kind == 0 ? warp_sum(acc) : (kind == 1 ? warp_max(acc) : warp_min(acc));
+    if (lane == 0) red_smem[q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) dc.hdr->counter = 0u;
+  return true;
+}
+
+// ---- the fused stage kernel ---------------------------------------------------------------
+// shared memory of the surrogate phase, reusing the (then dead) stencil buffers:
+// activations, streamed weights, outputs, blob header, per-thread results
+constexpr size_t SM_A = 0, SM_W = SM_A + mlp::ABYTES, SM_OUT = SM_W + 32768, SM_HDR = SM_OUT + 128 * 10 * 4,
+                 SM_RES = SM_HDR + mlp::NFLOAT * 4;
+template <class TL>
+constexpr size_t stage_smem_surr() {
+  return TL::template smem<float>() > SM_RES + (size_t)TL::NT * 40 ? TL::template smem<float>()
+                                                                     : SM_RES + (size_t)TL::NT * 40;
+}
+
+// Tensor-core resources of a CTA: 128 TMEM columns and the MMA-completion mbarrier (outside
+// the overlaid stencil buffers).  The stage kernels take them once at the start
+// (ready = true); the surrogate routine can also take and free them around a single call
+// (ready = false), since a CTA that has relinquished its allocation permit may not
+// allocate again.
+static __shared__ uint64_t s_tc_mbar;
+static __shared__ uint32_t s_tc_slot;
+struct TcCtx {
+  uint32_t tmem, phase;
+  bool ready;
+};
+__device__ __forceinline__ uint32_t tc_acquire() {
+  if ((threadIdx.x >> 5) == 0) {
+    tc::tmem_alloc(tc::smem_addr(&s_tc_slot), 128);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_addr(&s_tc_mbar), 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  return s_tc_slot;
+}
+__device__ __forceinline__ void tc_release(uint32_t tmem) {
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// Surrogate cells of one tile (called by all threads, only when the tile has at least one):
+// compaction into 128-row tiles and the BF16 tensor-core network.  Each surrogate cell's
+// thread finds its 10 outputs (raw units, held to the training range of their targets) in
+// res[10 * threadIdx.x ...] afterwards.  x: the cell's 16 raw inputs (kind == 2 only).
+template <class TL>
+__device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ blob, int kind, const float* x,
+                                            int& ntimeout, unsigned char* smem, TcCtx* tcx) {
+  constexpr int NT = TL::NT;
+  __shared__ int wcnt[NT / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* ghdr = reinterpret_cast<const float*>(blob);
+  const unsigned mask = __ballot_sync(0xffffffffu, kind == 2);
+  if (lane == 0) wcnt[warp] = __popc(mask);
+  unsigned char* A = smem + SM_A;
+  unsigned char* W = smem + SM_W;
+  float* outs = reinterpret_cast<float*>(smem + SM_OUT);
+  float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
+  float* res = reinterpret_cast<float*>(smem + SM_RES);
+  for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
+  uint32_t tmem, phase = 0;
+  if (tcx->ready) {
+    tmem = tcx->tmem;
+    phase = tcx->phase;
+    __syncthreads();
+  } else {
+    tmem = tc_acquire();   // includes the barrier
+  }
+  int off = 0, total = 0;
+  for (int w2 = 0; w2 < NT / 32; ++w2) {
+    off += w2 < warp ? wcnt[w2] : 0;
+    total += wcnt[w2];
+  }
+  const int row = off + __popc(mask & ((1u << lane) - 1u));
+  bool ok = true;
+  for (int c0 = 0; c0 < total; c0 += 128) {
+    const bool mine = kind == 2 && row >= c0 && row < c0 + 128;
+    if (mine) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = (x[q] - hdr[mlp::F_XMEAN + q]) * hdr[mlp::F_XISD + q];
+      mlp::store_row16(A, row - c0, 0, 16, v);
+    }
+    float o[10];
+    ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(&s_tc_mbar), phase, o, blob + mlp::WOFF,
+                             total - c0) && ok;
+    if (tid < 128) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
+    }
+    __syncthreads();
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q)
+        res[tid * 10 + q] = fminf(fmaxf(outs[(row - c0) * 10 + q], hdr[mlp::F_YMIN + q]), hdr[mlp::F_YMAX + q]);
+    }
+    __syncthreads();
+  }
+  if (tcx->ready) tcx->phase = phase;
+  else tc_release(tmem);
+  if (!ok && tid == 0) ntimeout += 1;   // a tensor-core wait gave up: the step reports it
+}
+
+// Source of the FP32 + surrogate path (called by all threads): active cells inside the
+// surrogate's training hull take their rates from the network, the others the plain source
+// (counted as fallbacks); both feed the plain path's tail, so conservation and the limiters
+// are exact.  Adds the source to acc.
+template <class TL, class T>
+__device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsigned char* __restrict__ blob, bool cell,
+                                                 const Prim<T>& w, const T* u14, T* acc, T dt, int& nactive,
+                                                 int& nfallback, int& ntimeout, T& lnJh, T& lnJt,
+                                                 unsigned char* smem, TcCtx* tcx) {
+  const float* ghdr = reinterpret_cast<const float*>(blob);
+  int kind = 0;   // 0 inactive, 1 plain source (outside the hull), 2 surrogate
+  Sat<T> st;
+  st.lnSl = st.lnSi = st.lnpv = 0.0;
+  st.pres_l = st.pres_s = st.active = false;
+  T Q[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Q[f] = T(0);
+  double lnJ2[2] = {-INFINITY, -INFINITY};
+  float x[CT_MLP_IN];
+  if (cell && dc.sc.phase_change) {
+    bool pl, ps;
+    const bool pops = populations(w, pl, ps);
+    if (pops || !clearly_inactive(w)) {
+      st = saturation(w);
+      if (st.active) {
+        mlp_features<T>(w, st, dc.sc.rp2, x);
+        bool inside = true;
+#pragma unroll
+        for (int q = 0; q < CT_MLP_IN; ++q)
+          inside = inside && x[q] >= ghdr[mlp::F_HMIN + q] && x[q] <= ghdr[mlp::F_HMAX + q];
+        kind = inside ? 2 : 1;
+      }
+    }
+  }
+  if (kind == 1) {
+    const Rates<T> r = plain_rates<T>(w, st, dc.sc, lnJ2, nullptr, nullptr);
+    source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
+    nfallback = 1;
+  }
+  // the stencil buffers are dead from here on; tiles without a surrogate cell skip the rest
+  if (__syncthreads_or(kind == 2)) {
+    surrogate_tile<TL>(blob, kind, x, ntimeout, smem, tcx);
+    if (kind == 2) {
+      const float* y = reinterpret_cast<const float*>(smem + SM_RES) + 10 * threadIdx.x;
+      const bool nuc = st.lnSl > 0.0;
+      Rates<T> r;
+      r.Jeff = nuc ? T(__expf(y[0])) : T(0);
+      // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
+      r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
+                        (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
+                    : T(0);
+      r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
+      r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
+      r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
+      r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
+      if (nuc) {
+        lnJ2[0] = y[6];
+        if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
+      }
+      source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
+    }
+  }
+  if (cell) {
+    nactive = kind != 0 ? 1 : 0;
+    lnJh = T(lnJ2[0]);
+    lnJt = T(lnJ2[1]);
+#pragma unroll
+    for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+  }
+}
+
+
+// One stage on tile (bx, by) of a case; `tile` = by * tiles_x + bx indexes the partial
+// records.  All threads of the CTA call this.  STAGE 1: Uout = Uin + dt L(Uin).
+// STAGE 2: Uout = (Un + Uin + dt L(Uin))/2 (Uout may be Un); the last tile of the case to
+// finish reduces the partials and publishes cfl * (stable step) as the next time step.
+template <class TL, class T, int STAGE, bool SURR>
+__device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, int tile, const T* __restrict__ Uin,
+                                           const T* Un, T* Uout, const unsigned char* __restrict__ blob,
+                                           unsigned char* smem_raw, double cfl, TcCtx* tcx) {
+  constexpr int TX = TL::TX, TY = TL::TY, HX = TL::HX, HY = TL::HY, NT = TL::NT, NCELL = TL::NCELL;
+  constexpr int NFACE = TL::NFACE;
+  T (*qs)[HY][HX] = reinterpret_cast<T (*)[HY][HX]>(smem_raw);                      // primitives
+  T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NF * HX * HY);   // face fluxes
+  T (*fL)[NFACE] = fb + NF;        // reconstructed left state of each face
+  T (*fR)[NFACE] = fb + 2 * NF;    // reconstructed right state of each face
+  __shared__ double red[NT / 32][NPART];
+  __shared__ double fin[NPART];
+
+  const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
+  const size_t N = (size_t)nx * nr;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int tid = threadIdx.x;
+  const double dtd = dc.hdr->dt_cur;
+  const T dt = T(dtd);
+  const Geo<T> g = geo_of(dc, T(0));
+
+  // phase A: halo primitives
+  for (int p = tid; p < HX * HY; p += NT) {
+    const int hi = p % HX, hj = p / HX;
+    const int i = i0 + hi - 2, j = j0 + hj - 2;
+    const bool xin = i >= 0 && i < nx, rin = j >= 0 && j < nr;
+    bool need = (xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1;
+    if (dc.geom == 0) need = need && j == 0;
+    if (!need) continue;
+    T u14[NF];
+    if (xin && rin) {
+      const size_t n = (size_t)j * nx + i;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+    } else {
+      load_ghost<T>(dc, Uin, N, i, j, u14);
+    }
+    Prim<T> w;
+    cons_to_prim<T>(u14, w);
+    qs[0][hj][hi] = w.rho;
+    qs[1][hj][hi] = w.u;
+    qs[2][hj][hi] = w.v;
+    qs[3][hj][hi] = w.p;
+    qs[4][hj][hi] = w.Yv;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      qs[5 + q][hj][hi] = w.ml[q];
+      qs[9 + q][hj][hi] = w.ms[q];
+    }
+    qs[13][hj][hi] = w.ns;
+  }
+  __syncthreads();
+
+  // phase B1: limited x slopes, once per cell, written as the states of its two faces
+  // (tile-local cell c in [-1, TX]; face f lies between cells f-1 and f)
+  for (int p = tid; p < (TX + 2) * TY; p += NT) {
+    const int c = p % (TX + 2) - 1, hj = p / (TX + 2);
+    const int i = i0 + c, j = j0 + hj;
+    if (i > nx || j >= nr) continue;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T am = qs[f][hj + 2][c + 1], a0 = qs[f][hj + 2][c + 2], a1 = qs[f][hj + 2][c + 3];
+      const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
+      if (c < TX) fL[f][hj * (TX + 1) + c + 1] = a0 + hs;
+      if (c >= 0) fR[f][hj * (TX + 1) + c] = a0 - hs;
+    }
+  }
+  __syncthreads();
+
+  // phase B2: x-face Roe fluxes
+  for (int p = tid; p < (TX + 1) * TY; p += NT) {
+    const int fx = p % (TX + 1), hj = p / (TX + 1);
+    const int i = i0 + fx, j = j0 + hj;
+    if (i > nx || j >= nr) continue;
+    T qL[NF], qR[NF], F[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      qL[f] = fL[f][p];
+      qR[f] = fR[f][p];
+    }
+    roe_flux<T, 0>(qL, qR, F);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
+  }
+  __syncthreads();
+
+  const int ci = tid % TX, cj = tid / TX;
+  const int i = i0 + ci, j = j0 + cj;
+  const bool cell = tid < NCELL && i < nx && j < nr;
+  T acc[NF];
+  T bm = T(0), bw = T(0), be = T(0);   // boundary inflow rates of this cell's faces
+  T area_w = T(0), area_e = T(0), vol = T(0);
+  if (cell) {
+    const int w = cj * (TX + 1) + ci, e = w + 1;
+    T cw, ce;
+    if (dc.geom == 0) {
+      const T xw = T(i) * g.dx, xe = T(i + 1) * g.dx, xc = (T(i) + T(0.5)) * g.dx;
+      const T sw = xw * g.ixt - T(1), se = xe * g.ixt - T(1), sc = xc * g.ixt - T(1);
+      area_w = T(1) + g.area_a * sw * sw;
+      area_e = T(1) + g.area_a * se * se;
+      const T Ac = T(1) + g.area_a * sc * sc;
+      const T iv = frcp(Ac * g.dx);
+      cw = area_w * iv;
+      ce = area_e * iv;
+      vol = Ac * g.dx;
+    } else {
+      cw = ce = g.idx;
+      area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
+      vol = area_w * g.dx;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f] = cw * fb[f][w] - ce * fb[f][e];
+    if (i == 0) {
+      bm += area_w * fb[0][w];
+      bw += area_w * (fb[4][w] + T(k::YL3) * fb[8][w] + T(k::YS3) * fb[12][w]);
+      be += area_w * fb[3][w];
+    }
+    if (i == nx - 1) {
+      bm -= area_e * fb[0][e];
+      bw -= area_e * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
+      be -= area_e * fb[3][e];
+    }
+  }
+
+  if (dc.geom == 1) {
+    __syncthreads();
+    // phase D1: limited r slopes (tile-local row c in [-1, TY]) -> states of the r faces
+    for (int p = tid; p < TX * (TY + 2); p += NT) {
+      const int hi = p % TX, c = p / TX - 1;
+      const int ii = i0 + hi, jj = j0 + c;
+      if (ii >= nx || jj > nr) continue;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T am = qs[f][c + 1][hi + 2], a0 = qs[f][c + 2][hi + 2], a1 = qs[f][c + 3][hi + 2];
+        const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
+        if (c < TY) fL[f][(c + 1) * TX + hi] = a0 + hs;
+        if (c >= 0) fR[f][c * TX + hi] = a0 - hs;
+      }
+    }
+    __syncthreads();
+    // phase D2: r-face Roe fluxes (face fy lies between tile rows fy-1 and fy)
+    for (int p = tid; p < TX * (TY + 1); p += NT) {
+      const int hi = p % TX, fy = p / TX;
+      const int ii = i0 + hi, jj = j0 + fy;
+      if (ii >= nx || jj > nr) continue;
+      T qL[NF], qR[NF], F[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        qL[f] = fL[f][p];
+        qR[f] = fR[f][p];
+      }
+      roe_flux<T, 1>(qL, qR, F);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
+    }
+    __syncthreads();
+  }
+
+  // phase E: residual, source, update, partial reductions
+  T pM = T(0), pW = T(0), pE = T(0);
+  T dtmin = T(INFINITY);
+  T rmax[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) rmax[f] = T(0);
+  T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
+  int nactive = 0, nbad = 0, nfallback = 0, ntimeout = 0;
+  T u14[NF];
+  Prim<T> w;
+  if (cell) {
+    const size_t n = (size_t)j * nx + i;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+    cons_to_prim<T>(u14, w);
+    if (dc.geom == 1) {
+      const T ijh = frcp(T(j) + T(0.5));
+      const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
+      const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        T Fs = fb[f][cj * TX + ci], Fn = fb[f][(cj + 1) * TX + ci];
+        if (wall && j == dc.jw - 1) Fn = f == 2 ? w.p : T(0);
+        if (wall && j == dc.jw) Fs = f == 2 ? w.p : T(0);
+        acc[f] += cs * Fs - cn * Fn;
+      }
+      acc[2] += w.p * ijh * g.idr;
+      if (j == nr - 1) {
+        const T An = T(nr) * g.dr * g.dx;
+        const int e = (cj + 1) * TX + ci;
+        bm -= An * fb[0][e];
+        bw -= An * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
+        be -= An * fb[3][e];
+      }
+    } else {
+      acc[1] += w.p * fdiv(area_e - area_w, vol);
+    }
+    // phase-change source limited on the flux-updated state
+    T Q[NF];
+    double lnJ2[2];
+    if (!SURR) {
+      const bool act = phase_source<T>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
+      nactive = act ? 1 : 0;
+      lnJh = T(lnJ2[0]);
+      lnJt = T(lnJ2[1]);
+#pragma unroll
+      for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+    }
+  }
+  if (SURR)
+    surrogate_source<TL, T>(dc, blob, cell, w, u14, acc, dt, nactive, nfallback, ntimeout, lnJh, lnJt, smem_raw,
+                            tcx);
+  if (cell) {
+    const size_t n = (size_t)j * nx + i;
+    // RK combine
+    T out[NF];
+    if (STAGE == 1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) out[f] = u14[f] + dt * acc[f];
+    } else {
+      const T idt = frcp(dt);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T un = Un[f * N + n];
+        out[f] = T(0.5) * un + T(0.5) * (u14[f] + dt * acc[f]);
+        rmax[f] = m_fabs(out[f] - un) * idt;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Uout[f * N + n] = out[f];
+      nbad += isfinite(out[f]) ? 0 : 1;
+    }
+    if (STAGE == 2) {
+      Prim<T> wn;
+      cons_to_prim<T>(out, wn);
+      const T c = m_sqrt(wn.c2);
+      T rate = (m_fabs(wn.u) + c) * g.idx;
+      if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
+      dtmin = T(1) / rate;   // times cfl at the end
+      pM = vol * out[0];
+      pW = vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]);
+      pE = vol * out[3];
+    }
+  }
+
+  // block partials: warp shuffles in the state precision, FP64 from the warp level on
+  const int warp = tid >> 5, lane = tid & 31;
+  {
+    T v;
+    int a;
+    v = warp_sum(bm); if (lane == 0) red[warp][4] = double(v);
+    v = warp_sum(bw); if (lane == 0) red[warp][5] = double(v);
+    v = warp_sum(be); if (lane == 0) red[warp][6] = double(v);
+    if (SURR) {
+      a = warp_sum(ntimeout);
+      if (lane == 0) red[warp][26] = a;
+    } else if (lane == 0) {
+      red[warp][26] = 0.0;
+    }
+    if (STAGE == 2) {
+      v = warp_min(dtmin); if (lane == 0) red[warp][0] = double(v);
+      v = warp_sum(pM); if (lane == 0) red[warp][1] = double(v);
+      v = warp_sum(pW); if (lane == 0) red[warp][2] = double(v);
+      v = warp_sum(pE); if (lane == 0) red[warp][3] = double(v);
+      a = warp_sum(nactive); if (lane == 0) red[warp][7] = a;
+      a = warp_sum(nbad); if (lane == 0) red[warp][8] = a;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        v = warp_max(rmax[f]);
+        if (lane == 0) red[warp][9 + f] = double(v);
+      }
+      v = warp_max(lnJh); if (lane == 0) red[warp][23] = double(v);
+      v = warp_max(lnJt); if (lane == 0) red[warp][24] = double(v);
+      a = warp_sum(nfallback); if (lane == 0) red[warp][25] = a;
+    } else if (lane == 0) {
+      // stage 1 needs the boundary inflow and the timeouts only
+      for (int q = 0; q < NPART; ++q)
+        if (q < 4 || q > 6) red[warp][q] = q == 26 ? red[warp][q] : 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid < NPART) {
+    const int kind = slot_kind(tid);
+    double acc2 = red[0][tid];
+    for (int w2 = 1; w2 < NT / 32; ++w2) {
+      const double v = red[w2][tid];
+      acc2 = kind == 0 ? acc2 + v : (kind == 1 ? fmax(acc2, v) : fmin(acc2, v));
+    }
+    dc.partials[(size_t)tile * NPART + tid] = acc2;
+  }
+  if (!last_block_reduce(dc, fin)) return;
+  if (tid == 0) {
+    WsHeader* h = dc.hdr;
+    if (STAGE == 1) {
+      h->b1[0] = fin[4];
+      h->b1[1] = fin[5];
+      h->b1[2] = fin[6];
+      h->b1[3] = fin[26];
+    } else {
+      double* d = h->diag;
+      d[0] = dtd;
+      d[1] = fin[1];
+      d[2] = fin[2];
+      d[3] = fin[3];
+      d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
+      d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
+      d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
+      d[7] = fin[7];
+      d[8] = fin[8];
+      for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
+      d[23] = fin[23] * (1.0 / 2.302585092994045684);
+      d[24] = fin[24] * (1.0 / 2.302585092994045684);
+      const double dtn = cfl * fin[0];
+      d[25] = dtn;
+      d[26] = fin[25];
+      h->steps += 1.0;
+      d[27] = h->steps;
+      d[28] = h->b1[3] + fin[26];
+      h->dt_cur = dtn;
+    }
+  }
+}
+
+template <class TL, class T, int STAGE, bool SURR>
+__global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
+    k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcCtx tcx;
+  tcx.ready = false;
+  if (SURR) {
+    // Take the tensor-core resources up front, also in tiles that will not need them: the
+    // SM does not start a second CTA of a kernel that uses TMEM until the first has given
+    // up its allocation permit, so a lazy allocation would halve the CTAs per SM.
+    tcx.tmem = tc_acquire();
+    tcx.phase = 0;
+    tcx.ready = true;
+  }
+  stage_tile<TL, T, STAGE, SURR>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
+                                 smem_raw, dc.cfl, &tcx);
+  if (SURR) tc_release(tcx.tmem);
+}
+
+// ---- batched persistent stage ----------------------------------------------------------------
+// Many independent cases of uneven size in one launch.  The work list is the concatenation
+// of the cases' tiles (largest cases first); persistent CTAs take tiles from an atomic
+// counter, so a CTA that drew a cheap tile takes the next one at once.  Each case keeps its
+// own workspace (time step, partials, diagnostics): its last tile reduces it as in the
+// single-case kernel.  The last CTA to leave resets the counter for the next launch.
+constexpr int MAX_BATCH = 256;
+struct BatchDev {
+  unsigned int next_tile;
+  unsigned int exited;
+  int ncases, total_tiles;
+  int tile_start[MAX_BATCH + 1];   // first work-list tile of each slot
+  int case_of[MAX_BATCH];          // case index of each work-list slot
+  int tiles_x[MAX_BATCH];          // per case
+  long long state_off[MAX_BATCH];  // element offset of the case's first plane
+  DevCase cases[MAX_BATCH];
+};
+
+template <class TL, class T, int STAGE, bool SURR>
+__global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
+    k_batch_stage(BatchDev* __restrict__ bd, const T* __restrict__ Uin, const T* Un, T* Uout,
+                  const unsigned char* __restrict__ blob, double cfl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) DevCase s_dc;
+  __shared__ int s_t, s_slot;
+  __shared__ int s_start[MAX_BATCH + 1];
+  const int tid = threadIdx.x;
+  const int ncases = bd->ncases, total = bd->total_tiles;
+  for (int q = tid; q <= ncases; q += TL::NT) s_start[q] = bd->tile_start[q];
+  TcCtx tcx;
+  tcx.ready = false;
+  if (SURR) {
+    tcx.tmem = tc_acquire();   // includes the barrier
+    tcx.phase = 0;
+    tcx.ready = true;
+  }
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) {
+      const int t = (int)atomicAdd(&bd->next_tile, 1u);
+      int lo = 0, hi = ncases;   // slot with s_start[slot] <= t < s_start[slot + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_start[mid] <= t) lo = mid; else hi = mid;
+      }
+      s_t = t;
+      s_slot = lo;
+    }
+    __syncthreads();
+    const int t = s_t, slot = s_slot;
+    if (t >= total) break;
+    const int k = bd->case_of[slot];
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&bd->cases[k]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_dc);
+      for (int q = tid; q < (int)(sizeof(DevCase) / 4); q += TL::NT) dst[q] = src[q];
+    }
+    __syncthreads();
+    const int lt = t - s_start[slot], tx = bd->tiles_x[k];
+    const long long off = bd->state_off[k];
+    stage_tile<TL, T, STAGE, SURR>(s_dc, lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off, blob,
+                                   smem_raw, cfl, &tcx);
+    __syncthreads();
+  }
+  if (SURR) tc_release(tcx.tmem);
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&bd->exited, 1u) == gridDim.x - 1) {   // every CTA has left the loop
+      bd->next_tile = 0u;
+      bd->exited = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---- kernels of one tile shape, as seen by the host ---------------------------------------
+// Precision index p: 0 FP64, 1 FP32, 2 FP32 + surrogate.  A null entry: that combination
+// does not fit the shared memory of an SM.
+struct StageSet {
+  int tx, ty, nt;
+  size_t smem[3];
+  int minb[3];
+  const void* stage[3][2];   // k_stage, stages 1 and 2
+  const void* batch[3][2];   // k_batch_stage (FP32 and FP32 + surrogate only)
+};
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
+
+template <class TL>
+StageSet make_stage_set() {
+  StageSet s;
+  memset(&s, 0, sizeof(s));
+  s.tx = TL::TX;
+  s.ty = TL::TY;
+  s.nt = TL::NT;
+  s.smem[0] = TL::template smem<double>();
+  s.smem[1] = TL::template smem<float>();
+  s.smem[2] = stage_smem_surr<TL>();
+  s.minb[0] = TL::template minb<double>();
+  s.minb[1] = s.minb[2] = TL::template minb<float>();
+  if constexpr (TL::template smem<double>() <= SMEM_LIMIT) {
+    s.stage[0][0] = (const void*)k_stage<TL, double, 1, false>;
+    s.stage[0][1] = (const void*)k_stage<TL, double, 2, false>;
+  }
+  s.stage[1][0] = (const void*)k_stage<TL, float, 1, false>;
+  s.stage[1][1] = (const void*)k_stage<TL, float, 2, false>;
+  s.stage[2][0] = (const void*)k_stage<TL, float, 1, true>;
+  s.stage[2][1] = (const void*)k_stage<TL, float, 2, true>;
+  s.batch[1][0] = (const void*)k_batch_stage<TL, float, 1, false>;
+  s.batch[1][1] = (const void*)k_batch_stage<TL, float, 2, false>;
+  s.batch[2][0] = (const void*)k_batch_stage<TL, float, 1, true>;
+  s.batch[2][1] = (const void*)k_batch_stage<TL, float, 2, true>;
+  return s;
+}
+
+// the tile shapes the library is built with (one translation unit each)
+constexpr int NSHAPES = 4;
+const StageSet* stage_set(int shape);   // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8
+
+}  // namespace ct

@@ -49,6 +49,11 @@ class Solver:
     def diagnostics(self) -> np.ndarray:
         return L.ct_diagnostics(self.work, self.stream)
 
+    def autotune(self, reps: int = 5):
+        """Pick the fastest tile shape for this grid (state unchanged); returns (shape, ms)."""
+        return L.ct_autotune(self.case, self.precision, self.U, self.U1, self.work, getattr(self, "blob", None),
+                             reps, self.stream)
+
     def derived(self, which: int, dt: float = 1e-6) -> torch.Tensor:
         out = torch.empty((self.nr, self.nx), dtype=torch.float64, device=self.device)
         L.ct_derived(self.case, self.precision, self.U, which, dt, out, self.stream)
@@ -57,3 +62,61 @@ class Solver:
     def state64(self) -> np.ndarray:
         self.stream.synchronize()
         return self.U.detach().to(torch.float64).cpu().numpy()
+
+
+class Batch:
+    """Many axisymmetric cases stepped together by the persistent, graph-captured kernel.
+    The batch state is one float32 tensor; `state(k)` views case k as (14, nr, nx)."""
+
+    def __init__(self, cases: list, ufac_rows: list | None = None, precision: int = L.CT_FP32_MLP,
+                 device="cuda:0", stream: torch.cuda.Stream | None = None, blob: torch.Tensor | None = None):
+        self.cases = [dict(c) for c in cases]
+        self.precision = precision
+        self.device = torch.device(device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.blob = blob
+        n = L.ct_batch_state_elems(self.cases)
+        if n == 0:
+            raise L.ContrailError(1, "invalid batch: " + L.ct_last_error())
+        self.U = torch.zeros(n, dtype=torch.float32, device=self.device)
+        self.U1 = torch.zeros_like(self.U)
+        nbytes = L.ct_batch_workspace_bytes(self.cases)
+        self.work = torch.zeros(nbytes // 8 + 64, dtype=torch.float64, device=self.device)
+        rows = None
+        if ufac_rows is not None:
+            rows = np.concatenate([np.asarray(r, dtype=np.float64) for r in ufac_rows])
+        self.handle = L.ct_batch_create(self.cases, precision, rows, self.work, nbytes, self.stream)
+        self.offsets = []
+        off = 0
+        for c in self.cases:
+            self.offsets.append(off)
+            off += L.NF * int(c["nx"]) * int(c["nr"])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            L.ct_batch_destroy(h)
+            self.handle = None
+
+    def state(self, k: int) -> torch.Tensor:
+        c = self.cases[k]
+        nx, nr = int(c["nx"]), int(c["nr"])
+        return self.U[self.offsets[k]:self.offsets[k] + L.NF * nx * nr].view(L.NF, nr, nx)
+
+    def init_state(self, cfl: float = 0.5):
+        L.ct_batch_init_state(self.handle, self.U, cfl)
+
+    def load_state(self, U_src: torch.Tensor, cfl: float = 0.5):
+        L.ct_batch_load_state(self.handle, U_src, self.U, cfl)
+
+    def autotune(self, reps: int = 3):
+        return L.ct_batch_autotune(self.handle, self.U, self.U1, self.blob, reps)
+
+    def set_tile_shape(self, shape: int):
+        L.ct_batch_set_tile_shape(self.handle, shape)
+
+    def step(self, nsteps: int, cfl: float = 0.5):
+        L.ct_batch_step(self.handle, self.U, self.U1, self.blob, nsteps, cfl)
+
+    def diagnostics(self) -> np.ndarray:
+        return L.ct_batch_diagnostics(self.handle, len(self.cases))

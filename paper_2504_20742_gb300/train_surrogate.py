@@ -100,7 +100,7 @@ def main(argv=None):
                                           "p99_abs": float(torch.quantile(e10, 0.99)), "max_abs": float(e10.max())}
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     sur.save(args.out)
-    rep["out"] = args.out
+    rep["out"] = os.path.relpath(args.out, ROOT)
     print(json.dumps(rep))
     return sur, rep
 

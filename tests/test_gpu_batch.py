@@ -1,0 +1,150 @@
+"""Tile shapes, the autotuner and the batched persistent step.
+
+The per-cell arithmetic of a step does not depend on how cells are grouped into tiles, so
+every tile shape, and the batched kernel that steps many cases together, must reproduce the
+single-case step bit for bit (the single-case paths are held to the oracle elsewhere).
+The batch is the sweep of plume cases with uneven grids and conditions of the paper's
+parameter study, at reduced and at full size."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from synth import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2504_20742_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def blob(P):
+    from paper_2504_20742_gb300 import surrogate as S
+    return S.Surrogate.load(S.default_path()).blob()
+
+
+def _small_batch(n=6):
+    """n cases of the sweep with their grids cut by 4 in each direction, plus a ragged one
+    (grids not multiples of any tile shape)."""
+    out = []
+    for c, uf in cases.batch_cases(n=n):
+        c = dict(c, nx=c["nx"] // 4, nr=c["nr"] // 4)
+        out.append((c, np.ones(c["nr"])))
+    c, _ = out[0]
+    c = dict(c, nx=72, nr=20)
+    out.append((c, 1.0 + 0.01 * np.sin(np.arange(20.0))))
+    return out
+
+
+def _single(P, c, uf, prec, nsteps, blob=None, shape=-1):
+    P.ct_set_tile_shape(c, prec, shape)
+    s = P.Solver(c, uf, precision=prec)
+    s.init_state(0.5)
+    if prec == P.CT_FP32_MLP:
+        s.attach_surrogate(blob)
+    s.step(nsteps, 0.5)
+    d = s.diagnostics()
+    P.ct_set_tile_shape(c, prec, -1)
+    return s.U.clone(), d
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_every_tile_shape_gives_the_same_state(P, blob, prec):
+    c, uf = cases.mixing_layer_case(nx=100, nr=44)
+    ref, d0 = _single(P, c, uf, prec, 12, blob, 0)
+    assert d0[8] == 0 and d0[7] > 0
+    for shape in range(1, P.ct_tile_shape_count()):
+        try:
+            P.ct_set_tile_shape(c, prec, shape)
+        except P.ContrailError:
+            continue          # shape not built for this precision
+        U, d = _single(P, c, uf, prec, 12, blob, shape)
+        assert torch.equal(U, ref), (prec, P.ct_tile_shape(shape))
+        assert d[0] == d0[0] and d[7] == d0[7] and d[26] == d0[26]
+        # the totals are sums in another order: warp sums in the state precision, FP64 above
+        tol = 1e-12 if prec == 0 else 1e-6
+        for k in (1, 2, 3):
+            assert abs(d[k] - d0[k]) <= tol * abs(d0[k])
+
+
+def test_autotune_leaves_the_state_and_registers_a_shape(P):
+    c, uf = cases.mixing_layer_case(nx=256, nr=64)
+    s = P.Solver(c, uf, precision=P.CT_FP32)
+    s.init_state(0.5)
+    s.step(2, 0.5)
+    before = s.U.clone()
+    shape, ms = s.autotune(reps=3)
+    torch.cuda.synchronize()
+    assert torch.equal(s.U, before)
+    assert 0 <= shape < P.ct_tile_shape_count() and ms[shape] > 0
+    assert ms[shape] == min(m for m in ms if m > 0)
+    print("tile shapes", [P.ct_tile_shape(k) for k in range(len(ms))], "ms per stage launch", ms)
+    s.step(3, 0.5)
+    P.ct_set_tile_shape(c, P.CT_FP32, -1)
+    ref, _ = _single(P, c, uf, P.CT_FP32, 5, None, 0)
+    assert torch.equal(s.U, ref)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_matches_single_case_steps(P, blob, prec):
+    bc = _small_batch()
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=prec, blob=blob if prec == 2 else None)
+    b.init_state(0.5)
+    b.step(4, 0.5)
+    b.step(4, 0.5)          # replays the captured graph
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0)
+    dts = db[:, 0]
+    assert len(set(dts.tolist())) > 1          # every case keeps its own time step
+    for k, (c, uf) in enumerate(bc):
+        ref, d = _single(P, c, uf, prec, 8, blob)
+        assert torch.equal(b.state(k), ref), k
+        assert db[k, 0] == d[0] and db[k, 7] == d[7] and db[k, 27] == d[27]
+        for q in (1, 2, 3):
+            assert abs(db[k, q] - d[q]) <= 1e-12 * abs(d[q])
+
+
+def test_batch_shapes_autotune_and_recapture(P, blob):
+    bc = _small_batch(4)
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32_MLP, blob=blob)
+    b.init_state(0.5)
+    b.step(2, 0.5)
+    before = b.U.clone()
+    shape, ms = b.autotune(reps=2)
+    torch.cuda.synchronize()
+    assert torch.equal(b.U, before)
+    assert ms[shape] == min(m for m in ms if m > 0)
+    b.step(3, 0.5)                      # new shape: a new graph
+    after_tuned = b.U.clone()
+    b.load_state(before, 0.5)
+    b.set_tile_shape(0)
+    b.step(1, 0.5)                      # another step count: another graph
+    b.step(2, 0.5)
+    assert torch.equal(b.U, after_tuned)
+
+
+def test_full_size_sweep_samples(P, blob):
+    """The 64-case sweep at full size (grids 256x64 .. 2048x512, about 2.5 GB of FP32 state
+    in two copies) in the launch form of the benchmark; the two smallest cases are
+    re-run alone and must agree bit for bit."""
+    bc = cases.batch_cases(n=64)
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32_MLP, blob=blob)
+    b.init_state(0.5)
+    b.autotune(reps=1)
+    b.step(3, 0.5)
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0) and np.all(db[:, 27] == 3)
+    sizes = [c["nx"] * c["nr"] for c, _ in bc]
+    for k in np.argsort(sizes, kind="stable")[:2]:
+        c, uf = bc[k]
+        ref, d = _single(P, c, uf, P.CT_FP32_MLP, 3, blob)
+        assert torch.equal(b.state(int(k)), ref), k
+        assert db[k, 0] == d[0]
+    print("active cells per case (min, max):", db[:, 7].min(), db[:, 7].max(),
+          "fallbacks:", db[:, 26].sum())

@@ -78,7 +78,7 @@ def test_surrogate_rates_on_visited_states(P, sur):
 
 
 def test_surrogate_trajectory_vs_oracle_on_nozzle(P, sur):
-    """Condensing nozzle (configs[0] geometry), 300 steps: the FP32 + surrogate state against
+    """The 400-cell condensing nozzle, 300 steps: the FP32 + surrogate state against
     the FP64 oracle, and the plain FP32 state against it, field by field."""
     c = cases.nozzle_case(nx=400)
     o = O.Oracle(c)

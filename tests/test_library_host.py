@@ -61,3 +61,45 @@ def test_binding_has_no_oracle_dependency():
     src = open(os.path.join(ROOT, "paper_2504_20742_gb300", "_lib.py")).read()
     src += open(os.path.join(ROOT, "paper_2504_20742_gb300", "solver.py")).read()
     assert "oracle" not in src and "synth" not in src
+
+
+def test_tile_shapes_and_registry_without_a_gpu(P):
+    from synth import cases
+    n = P.ct_tile_shape_count()
+    shapes = [P.ct_tile_shape(s) for s in range(n)]
+    assert shapes[0] == (32, 8) and len(set(shapes)) == n
+    c, _ = cases.plume_case(nx=64, nr=16)
+    # FP64 tiles of 32 x 16 cells do not fit the shared memory of an SM
+    k = shapes.index((32, 16))
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_set_tile_shape(c, P.CT_FP64, k)
+    assert e.value.status == 1
+    P.ct_set_tile_shape(c, P.CT_FP32, k)
+    P.ct_set_tile_shape(c, P.CT_FP32, -1)
+    with pytest.raises(P.ContrailError):
+        P.ct_set_tile_shape(c, P.CT_FP32, n)
+    # the workspace holds the partials of the shape with the most tiles
+    ragged, _ = cases.plume_case(nx=40, nr=24)
+    tiles = max(-(-40 // tx) * -(-24 // ty) for tx, ty in shapes)
+    assert P.ct_workspace_bytes(ragged, P.CT_FP32) >= tiles * 26 * 8
+
+
+def test_batch_sizes_and_validation_without_a_gpu(P):
+    from synth import cases
+    bc = [c for c, _ in cases.batch_cases(n=8)]
+    elems = sum(14 * c["nx"] * c["nr"] for c in bc)
+    assert P.ct_batch_state_elems(bc) == elems
+    ws = P.ct_batch_workspace_bytes(bc)
+    assert ws >= sum(P.ct_workspace_bytes(c, P.CT_FP32) for c in bc)
+    noz = cases.nozzle_case()
+    assert P.ct_batch_workspace_bytes(bc + [noz]) == 0
+    assert "geom" in P.ct_last_error()
+    assert P.ct_batch_workspace_bytes([]) == 0
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_batch_create(bc, P.CT_FP64, None, 0x100, ws, None)
+    assert e.value.status == 1
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_batch_create(bc, P.CT_FP32, None, 0x100, ws - 1, None)
+    assert e.value.status == 6
+    with pytest.raises(P.ContrailError):
+        P.ct_batch_create(bc, P.CT_FP32, None, 0x101, ws, None)
