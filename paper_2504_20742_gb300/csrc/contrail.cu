@@ -284,10 +284,15 @@ static int tiles_y(const ct_case* c, int shape) {
   return (case_nr(c) + ty - 1) / ty;
 }
 static int num_blocks(const ct_case* c, int shape) { return tiles_x(c, shape) * tiles_y(c, shape); }
-// partial records the workspace holds: enough for every shape
+// partial records and tile rows the workspace holds: enough for every shape
 static int max_blocks(const ct_case* c) {
   int m = 0;
   for (int s = 0; s < NSHAPES; ++s) m = std::max(m, num_blocks(c, s));
+  return m;
+}
+static int max_rows(const ct_case* c) {
+  int m = 0;
+  for (int s = 0; s < NSHAPES; ++s) m = std::max(m, tiles_y(c, s));
   return m;
 }
 
@@ -332,6 +337,8 @@ static size_t ws_bytes(const ct_case* c) {
   b += align256(nr * NF * sizeof(double));
   b += align256(NF * sizeof(double));
   b += align256((size_t)max_blocks(c) * NPART * sizeof(double));
+  b += align256((size_t)max_rows(c) * sizeof(unsigned int));
+  b += align256((size_t)max_rows(c) * NPART * sizeof(double));
   return b;
 }
 
@@ -377,7 +384,13 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.amb = (const double*)(base + off);
   off += align256(NF * sizeof(double));
   d.partials = (double*)(base + off);
+  off += align256((size_t)max_blocks(c) * NPART * sizeof(double));
+  d.row_count = (unsigned int*)(base + off);
+  off += align256((size_t)max_rows(c) * sizeof(unsigned int));
+  d.row_part = (double*)(base + off);
   d.nblocks = num_blocks(c, shape);
+  d.tiles_x = tiles_x(c, shape);
+  d.tiles_y = tiles_y(c, shape);
   return d;
 }
 
@@ -434,6 +447,8 @@ ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host
     }
   }
   if (cudaMemcpyAsync(work, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) return cuda_check("ct_setup header");
+  if (cudaMemsetAsync(d.row_count, 0, (size_t)max_rows(c) * sizeof(unsigned int), st) != cudaSuccess)
+    return cuda_check("ct_setup row tickets");
   if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr);
   // the header copy and the profile kernel read host memory that must outlive them
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_setup sync");
@@ -451,7 +466,8 @@ static ct_status launch_dt(const ct_case* c, int precision, void* work, const vo
   DevCase d = make_dev(c, work);
   d.cfl = cfl;
   const size_t N = (size_t)c->nx * case_nr(c);
-  int grid = (int)std::min<size_t>((N + NT_AUX - 1) / NT_AUX, (size_t)d.nblocks);
+  // a grid-stride kernel: a few hundred CTAs keep its one-level reduction short
+  int grid = (int)std::min<size_t>(std::min<size_t>((N + NT_AUX - 1) / NT_AUX, (size_t)d.nblocks), (size_t)512);
   d.nblocks = grid;
   if (precision == CT_FP64) k_dt<double><<<grid, NT_AUX, 0, st>>>(d, (const double*)U);
   else k_dt<float><<<grid, NT_AUX, 0, st>>>(d, (const float*)U);
@@ -637,14 +653,15 @@ static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_B
 constexpr int MAX_DEVICES = 64;
 static void* g_static_ptr[MAX_DEVICES];   // device address of g_static_scratch, per device
 
-__global__ void k_scratch_reset(int nblocks) {
-  // everything of the header that must start at zero for a fresh run
+__global__ void k_scratch_reset(int nblocks, unsigned int* row_count, int nrows) {
+  // everything that must start at zero for a fresh run: the header and the row tickets
   WsHeader* h = reinterpret_cast<WsHeader*>(g_static_scratch);
   if (threadIdx.x == 0) {
     memset(h, 0, sizeof(WsHeader));
     h->setup_magic = SETUP_MAGIC;
     h->nblocks = nblocks;
   }
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) row_count[r] = 0u;
 }
 
 static ct_status static_scratch_address(void** out) {
@@ -688,7 +705,7 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   if ((s = static_scratch_address(&work)) != CT_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, work);
-  k_scratch_reset<<<1, 32, 0, st>>>(d.nblocks);
+  k_scratch_reset<<<1, 256, 0, st>>>(d.nblocks, d.row_count, max_rows(c));
   if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_rows_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr);
   if ((s = cuda_check("ct_step_static setup")) != CT_OK) return s;
   if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;

@@ -7,12 +7,14 @@
 
 namespace ct {
 
-// van Leer limited slope psi(r) (q_i - q_{i-1}), psi(r) = (r+|r|)/(1+|r|), in its
-// harmonic-mean form 2 dm dp/(dm+dp) (zero unless dm and dp share a sign).
+// Half of van Leer's limited slope psi(r) (q_i - q_{i-1}), psi(r) = (r+|r|)/(1+|r|): in its
+// harmonic-mean form the slope is 2 dm dp/(dm+dp) when dm and dp share a sign and 0
+// otherwise, so the half slope is dm (dp/(dm+dp)) when dm dp > 0.  The quotient lies in
+// (0, 1), which keeps the fast FP32 division in range.  (A product that underflows to
+// zero gives a zero slope.)
 template <class T>
-__device__ __forceinline__ T vl_slope(T dm, T dp) {
-  const bool same = (dm > T(0) && dp > T(0)) || (dm < T(0) && dp < T(0));
-  return same ? T(2) * dm * fdiv(dp, dm + dp) : T(0);
+__device__ __forceinline__ T vl_half_slope(T dm, T dp) {
+  return dm * dp > T(0) ? dm * fdiv(dp, dm + dp) : T(0);
 }
 
 // Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns.

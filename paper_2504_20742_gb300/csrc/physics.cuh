@@ -479,7 +479,9 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
   }
   lnJ2[0] = lnJ2[1] = -INFINITY;
   if (!sc.phase_change) return false;
-  if (sizeof(T) == 4 && !aux && !ext) {
+  if (!aux && !ext) {
+    // the FP32 screen's margin (1e-3 in ln S_l) is far above its rounding error, so a
+    // screened cell is inactive in FP64 too: both paths give the same (zero) source
     bool pl, ps;
     if (!populations(w, pl, ps) && clearly_inactive(w)) return false;
   }

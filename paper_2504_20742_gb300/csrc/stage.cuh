@@ -8,9 +8,9 @@
 // x-face and r-face Roe fluxes once per face, the flux divergence with the axisymmetric /
 // area geometric sources, the per-cell phase-change source (limited on the flux-updated
 // state), the RK combine, and block partials of the CFL time step and of the conservation
-// diagnostics.  The last CTA of a case to finish reduces the partials in a fixed order
-// (deterministic) and publishes the next time step to the workspace, so that N steps run
-// without any host round trip.  Per-cell results do not depend on the tile shape.
+// diagnostics.  The partials are reduced by the last CTAs to arrive, per tile row and then
+// per case, in a fixed order (deterministic); the case's last CTA publishes the next time
+// step to the workspace, so that N steps run without any host round trip.  Per-cell results do not depend on the tile shape.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -50,6 +50,7 @@ static_assert(sizeof(WsHeader) <= HDR_BYTES, "header");
 
 struct DevCase {
   int geom, nx, nr, bc_xlo, bc_xhi, bc_rhi, jw, nblocks;
+  int tiles_x, tiles_y;   // tile grid of the shape in use (nblocks = tiles_x * tiles_y)
   double dx, dr, idx, idr, cfl;
   double area_a, x_throat, wall_len;
   double p0, T0, Yv0, cp0, gam0;       // nozzle inlet mixture
@@ -58,7 +59,9 @@ struct DevCase {
   const double* inflow;   // nr x NF (plume)
   const double* amb;      // NF
   WsHeader* hdr;
-  double* partials;       // nblocks x NPART
+  double* partials;       // nblocks x NPART, tile by * tiles_x + bx
+  unsigned int* row_count;  // tiles_y arrival tickets (zero between launches)
+  double* row_part;       // tiles_y x NPART row records
 };
 
 // Tile of TX x TY cells per CTA with a two-cell halo (HX x HY).  NT threads: the larger of
@@ -184,29 +187,66 @@ __device__ __forceinline__ V warp_min(V v) {
 // kind: 0 sum, 1 max, 2 min
 __device__ __forceinline__ int slot_kind(int q) { return q == 0 ? 2 : ((q >= 9 && q <= 24) ? 1 : 0); }
 
-// Last CTA: reduce the partial records of all CTAs in a fixed order; returns true in the
-// CTA that did it (red[] then holds the totals).
-__device__ inline bool last_block_reduce(const DevCase& dc, double* red_smem) {
-  __shared__ unsigned int ticket;
-  __threadfence();   // every thread that wrote partials makes them visible device-wide
-  __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(&dc.hdr->counter, 1u);
-  __syncthreads();
-  if (ticket != (unsigned int)(dc.nblocks - 1)) return false;
-  __threadfence();
+// Reduce n partial records (NPART slots each, consecutive) at `base` into out[NPART]
+// (shared memory), in a fixed order: lane-strided over the records, then a warp tree.
+// All threads call this; it ends with a barrier.
+__device__ inline void reduce_records(const double* base, int n, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   for (int q = warp; q < NPART; q += nwarps) {
     const int kind = slot_kind(q);
     double acc = kind == 0 ? 0.0 : (kind == 1 ? -INFINITY : INFINITY);
-    for (int b = lane; b < dc.nblocks; b += 32) {
-      const double v = __ldcg(&dc.partials[(size_t)b * NPART + q]);
+    for (int b = lane; b < n; b += 32) {
+      const double v = __ldcg(&base[(size_t)b * NPART + q]);
       acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
     }
     acc = kind == 0 ? warp_sum(acc) : (kind == 1 ? warp_max(acc) : warp_min(acc));
-    if (lane == 0) red_smem[q] = acc;
+    if (lane == 0) out[q] = acc;
   }
   __syncthreads();
+}
+
+// Called by all threads after threads 0..NPART-1 wrote this CTA's partial record.  Returns
+// true in the last CTA to arrive (out[] then holds the totals of the dc.nblocks records).
+// One level: for launches of a few hundred CTAs (the time-step kernel).
+__device__ inline bool last_block_reduce(const DevCase& dc, double* out) {
+  __shared__ unsigned int ticket;
+  if (threadIdx.x < NPART) __threadfence();   // the record's writers publish it
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&dc.hdr->counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(dc.nblocks - 1)) return false;
+  __threadfence();
+  reduce_records(dc.partials, dc.nblocks, out);
+  if (threadIdx.x == 0) dc.hdr->counter = 0u;
+  return true;
+}
+
+// Two levels, for the stage kernels: the last tile of each tile row to arrive reduces that
+// row's records into a row record, and the last row to complete reduces the row records.
+// Both orders are fixed, so the totals are deterministic; no CTA waits for another, and
+// the serial part on the critical path is one row of records instead of all of them.
+// `by`: this tile's row.  Returns true in the CTA that completed the case.
+__device__ inline bool tile_reduce(const DevCase& dc, int by, double* out) {
+  __shared__ unsigned int ticket;
+  if (threadIdx.x < NPART) __threadfence();   // the record's writers publish it
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&dc.row_count[by], 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(dc.tiles_x - 1)) return false;
+  __threadfence();
+  reduce_records(dc.partials + (size_t)by * dc.tiles_x * NPART, dc.tiles_x, out);
+  if (threadIdx.x < NPART) {
+    dc.row_part[(size_t)by * NPART + threadIdx.x] = out[threadIdx.x];
+    __threadfence();
+  }
+  if (threadIdx.x == 0) dc.row_count[by] = 0u;   // every tile of the row has arrived
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&dc.hdr->counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(dc.tiles_y - 1)) return false;
+  __threadfence();
+  reduce_records(dc.row_part, dc.tiles_y, out);
   if (threadIdx.x == 0) dc.hdr->counter = 0u;
   return true;
 }
@@ -454,7 +494,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const T am = qs[f][hj + 2][c + 1], a0 = qs[f][hj + 2][c + 2], a1 = qs[f][hj + 2][c + 3];
-      const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
+      const T hs = vl_half_slope(a0 - am, a1 - a0);
       if (c < TX) fL[f][hj * (TX + 1) + c + 1] = a0 + hs;
       if (c >= 0) fR[f][hj * (TX + 1) + c] = a0 - hs;
     }
@@ -526,7 +566,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const T am = qs[f][c + 1][hi + 2], a0 = qs[f][c + 2][hi + 2], a1 = qs[f][c + 3][hi + 2];
-        const T hs = T(0.5) * vl_slope(a0 - am, a1 - a0);
+        const T hs = vl_half_slope(a0 - am, a1 - a0);
         if (c < TY) fL[f][(c + 1) * TX + hi] = a0 + hs;
         if (c >= 0) fR[f][c * TX + hi] = a0 - hs;
       }
@@ -681,7 +721,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     }
     dc.partials[(size_t)tile * NPART + tid] = acc2;
   }
-  if (!last_block_reduce(dc, fin)) return;
+  if (!tile_reduce(dc, by, fin)) return;
   if (tid == 0) {
     WsHeader* h = dc.hdr;
     if (STAGE == 1) {
