@@ -785,7 +785,8 @@ struct ct_batch {
   double* diag = nullptr;          // ncases x CT_NDIAG gather area
   std::vector<size_t> case_off;    // byte offset of each case's workspace
   std::vector<long long> state_off;
-  int grid = 0;                    // persistent CTAs
+  int grid = 0;                    // CTAs of a launch
+  int max_tiles = 0;               // tiles one CTA takes at most
   // the captured graph of the last ct_batch_step call and what it was captured for
   cudaGraphExec_t exec = nullptr;
   const void *g_U = nullptr, *g_U1 = nullptr, *g_blob = nullptr;
@@ -852,7 +853,14 @@ static ct_status batch_upload(ct_batch* b) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ss->batch[1][0], ss->nt, ss->smem[p]) != cudaSuccess)
     return cuda_check("occupancy");
   per_sm = std::max(1, per_sm);
-  b->grid = std::min(t, nsm * per_sm);
+  if (b->precision == CT_FP32_MLP) {
+    // CTAs that finish often, so that every SM keeps per_sm of them resident
+    b->max_tiles = 4;
+    b->grid = (t + b->max_tiles - 1) / b->max_tiles;
+  } else {
+    b->max_tiles = t;
+    b->grid = std::min(t, nsm * per_sm);
+  }
   return CT_OK;
 }
 
@@ -866,7 +874,8 @@ static void batch_launch(ct_batch* b, int stage, const void* Uin, const void* Un
   void* a3 = Uout;
   const void* a4 = blob;
   double a5 = cfl;
-  void* args[] = {&bd, &a1, &a2, &a3, &a4, &a5};
+  int a6 = b->max_tiles;
+  void* args[] = {&bd, &a1, &a2, &a3, &a4, &a5, &a6};
   cudaLaunchKernel(ss->batch[p][stage - 1], dim3(b->grid), dim3(ss->nt), args, ss->smem[p], st);
 }
 

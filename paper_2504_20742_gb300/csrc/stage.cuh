@@ -184,6 +184,25 @@ __device__ __forceinline__ V warp_min(V v) {
   }
   return v;
 }
+// Single-instruction warp reductions (redux.sync) through order-preserving integer keys.
+__device__ __forceinline__ int warp_count(int v) { return __reduce_add_sync(0xffffffffu, v); }
+// maximum / minimum of non-negative floats (their bit patterns order as unsigned integers)
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+}
+__device__ __forceinline__ float warp_min_nonneg(float v) {
+  return __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(v)));
+}
+// maximum of any floats: negative values have their magnitude bits flipped
+__device__ __forceinline__ float warp_max_any(float v) {
+  const int i = __float_as_int(v);
+  const int k = __reduce_max_sync(0xffffffffu, i >= 0 ? i : i ^ 0x7fffffff);
+  return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
+}
+__device__ __forceinline__ double warp_max_nonneg(double v) { return warp_max(v); }
+__device__ __forceinline__ double warp_min_nonneg(double v) { return warp_min(v); }
+__device__ __forceinline__ double warp_max_any(double v) { return warp_max(v); }
+
 // kind: 0 sum, 1 max, 2 min
 __device__ __forceinline__ int slot_kind(int q) { return q == 0 ? 2 : ((q >= 9 && q <= 24) ? 1 : 0); }
 
@@ -685,26 +704,26 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     v = warp_sum(bw); if (lane == 0) red[warp][5] = double(v);
     v = warp_sum(be); if (lane == 0) red[warp][6] = double(v);
     if (SURR) {
-      a = warp_sum(ntimeout);
+      a = warp_count(ntimeout);
       if (lane == 0) red[warp][26] = a;
     } else if (lane == 0) {
       red[warp][26] = 0.0;
     }
     if (STAGE == 2) {
-      v = warp_min(dtmin); if (lane == 0) red[warp][0] = double(v);
+      v = warp_min_nonneg(dtmin); if (lane == 0) red[warp][0] = double(v);
       v = warp_sum(pM); if (lane == 0) red[warp][1] = double(v);
       v = warp_sum(pW); if (lane == 0) red[warp][2] = double(v);
       v = warp_sum(pE); if (lane == 0) red[warp][3] = double(v);
-      a = warp_sum(nactive); if (lane == 0) red[warp][7] = a;
-      a = warp_sum(nbad); if (lane == 0) red[warp][8] = a;
+      a = warp_count(nactive); if (lane == 0) red[warp][7] = a;
+      a = warp_count(nbad); if (lane == 0) red[warp][8] = a;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        v = warp_max(rmax[f]);
+        v = warp_max_nonneg(rmax[f]);
         if (lane == 0) red[warp][9 + f] = double(v);
       }
-      v = warp_max(lnJh); if (lane == 0) red[warp][23] = double(v);
-      v = warp_max(lnJt); if (lane == 0) red[warp][24] = double(v);
-      a = warp_sum(nfallback); if (lane == 0) red[warp][25] = a;
+      v = warp_max_any(lnJh); if (lane == 0) red[warp][23] = double(v);
+      v = warp_max_any(lnJt); if (lane == 0) red[warp][24] = double(v);
+      a = warp_count(nfallback); if (lane == 0) red[warp][25] = a;
     } else if (lane == 0) {
       // stage 1 needs the boundary inflow and the timeouts only
       for (int q = 0; q < NPART; ++q)
@@ -779,6 +798,9 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
 // counter, so a CTA that drew a cheap tile takes the next one at once.  Each case keeps its
 // own workspace (time step, partials, diagnostics): its last tile reduces it as in the
 // single-case kernel.  The last CTA to leave resets the counter for the next launch.
+// max_tiles bounds the tiles one CTA takes.  The surrogate variant uses a small bound: the
+// SM places a further CTA of a kernel that holds TMEM only when one of its CTAs finishes,
+// so CTAs that never finished would keep one CTA per SM for the whole launch.
 constexpr int MAX_BATCH = 256;
 struct BatchDev {
   unsigned int next_tile;
@@ -794,7 +816,7 @@ struct BatchDev {
 template <class TL, class T, int STAGE, bool SURR>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     k_batch_stage(BatchDev* __restrict__ bd, const T* __restrict__ Uin, const T* Un, T* Uout,
-                  const unsigned char* __restrict__ blob, double cfl) {
+                  const unsigned char* __restrict__ blob, double cfl, int max_tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) DevCase s_dc;
   __shared__ int s_t, s_slot;
@@ -810,7 +832,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     tcx.ready = true;
   }
   __syncthreads();
-  for (;;) {
+  for (int taken = 0; taken < max_tiles; ++taken) {
     if (tid == 0) {
       const int t = (int)atomicAdd(&bd->next_tile, 1u);
       int lo = 0, hi = ncases;   // slot with s_start[slot] <= t < s_start[slot + 1]
