@@ -77,13 +77,14 @@ def _workload(name):
     return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
-# Per-cell figures of the fused stage kernel with 32 x 8 tiles, from one ncu capture each
-# (see profiles/): FP64 arithmetic per cell-stage (mean of the two stages: 1283 and 1472
-# flops) and DRAM bytes per cell per launch (mean of the two stages).  The traffic is
-# reported only when the autotuner keeps that shape.
-FP64_FLOPS_PER_CELL_STAGE = 1377.7
-FP64_TRAFFIC_PER_CELL_LAUNCH = 172.4
-FP32_TRAFFIC_PER_CELL_LAUNCH = 134.3
+# Per-cell figures of the fused stage kernel with 16 x 16 tiles (the shape the autotuner
+# picks for both workloads), from one ncu capture each (see profiles/): FP64 arithmetic per
+# cell-stage (mean of the two stages: 1005 and 1191 flops) and DRAM bytes per cell per
+# launch (mean of the two stages).  The traffic is reported only for that shape.
+TRAFFIC_SHAPE = 1
+FP64_FLOPS_PER_CELL_STAGE = 1098.2
+FP64_TRAFFIC_PER_CELL_LAUNCH = 173.0
+FP32_TRAFFIC_PER_CELL_LAUNCH = 133.4
 
 
 def measure_dgemm_tflops(dev) -> float:
@@ -146,6 +147,34 @@ class Clocks:
                     "samples": len(rows)}
         except Exception as e:  # noqa: BLE001
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
+
+
+def max_over_ranks(values, dist, dev=None):
+    """Per-rank timings -> their maximum over all ranks (the job's time); identity on one rank."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return [float(v) for v in t.tolist()]
+
+
+def total_over_ranks(count, dist):
+    """Units processed by all ranks (each rank its own work: weak scaling)."""
+    if not dist:
+        return int(count)
+    import torch
+    backend = dist.get_backend()
+    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    t = torch.tensor([int(count)], dtype=torch.int64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def batch_seed(rank: int) -> int:
+    """Seed of the plume sweep a rank steps: independent cases per rank."""
+    return 5 + 1000 * int(rank)
 
 
 def run_cuda(args):
@@ -213,11 +242,7 @@ def run_cuda(args):
         for _ in range(e2e_steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-    ms_t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    step_ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    step_ms, e2e_s = max_over_ranks([step_ms, e2e_s], dist, dev)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -237,7 +262,7 @@ def run_cuda(args):
         ach = flops / (launch_ms_ev * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fpk, 4),
-                "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells if shape == 0 else None,
+                "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells if shape == TRAFFIC_SHAPE else None,
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{FP64_FLOPS_PER_CELL_STAGE} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"}
@@ -246,7 +271,7 @@ def run_cuda(args):
         bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(bw / peaks["hbm_gbs"], 4),
-                "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells if shape == 0 else None,
+                "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells if shape == TRAFFIC_SHAPE else None,
                 "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
@@ -293,8 +318,8 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    bc = cases.batch_cases(n=64)
-    cells = int(sum(c["nx"] * c["nr"] for c, _ in bc))
+    bc = cases.batch_cases(seed=batch_seed(rank), n=64)   # every rank its own sweep
+    cells_rank = int(sum(c["nx"] * c["nr"] for c, _ in bc))
     cfl = 0.5
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
@@ -338,26 +363,23 @@ def run_batch(args):
         for _ in range(e2e_steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-    ms_t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    step_ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    step_ms, e2e_s = max_over_ranks([step_ms, e2e_s], dist, dev)
+    cells = total_over_ranks(cells_rank, dist)      # collective: every rank takes part
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    value = world * cells / (step_ms * 1e-3) / 1e9
+    value = cells / (step_ms * 1e-3) / 1e9
     peaks, peak_kind = _peaks()
     launch_ms = step_ms / 2.0
-    bw = cells * 14 * 4 * 2.5 / (launch_ms * 1e-3) / 1e9
+    bw = cells_rank * 14 * 4 * 2.5 / (launch_ms * 1e-3) / 1e9
     tx, ty = P.ct_tile_shape(shape)
-    bytes_state = cells * 14 * 4
+    bytes_state = cells_rank * 14 * 4
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic", "impl": "cuda",
-        "config": {"workload": BATCH_DESC, "cases": len(bc), "cells": cells, "cfl": cfl,
+        "config": {"workload": BATCH_DESC, "cases": len(bc) * world, "cells": cells, "cfl": cfl,
                    "tile": f"{tx}x{ty} (autotuned; ms per stage-1 launch per shape: "
                            f"{[round(m, 4) for m in tune_ms]})",
                    "l2": "inputs larger than L2 (1.25 GB per FP32 state copy)",
@@ -367,13 +389,13 @@ def run_batch(args):
                      "kernel": "ct::k_batch_stage<float, surrogate>", "peak_source": peak_kind,
                      "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
                              f"mean launch {launch_ms:.4f} ms"},
-        "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
+        "e2e": {"value": round(cells / e2e_s / 1e9, 5), "unit": UNIT,
                 "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
         "diag": {"dt_min": float(d[:, 0].min()), "dt_max": float(d[:, 0].max()),
-                 "active_cells": float(d[:, 7].sum()), "active_frac": round(float(d[:, 7].sum()) / cells, 5),
+                 "active_cells": float(d[:, 7].sum()), "active_frac": round(float(d[:, 7].sum()) / cells_rank, 5),
                  "nonfinite": float(d[:, 8].sum()), "surrogate_fallback_cells": float(d[:, 26].sum())},
     }
     if not args.no_cpu_baseline and world == 1:

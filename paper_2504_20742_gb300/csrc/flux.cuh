@@ -17,38 +17,36 @@ __device__ __forceinline__ T vl_half_slope(T dm, T dp) {
   return dm * dp > T(0) ? dm * fdiv(dp, dm + dp) : T(0);
 }
 
+// Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
+// formation energy and frozen sound speed squared.  One reciprocal, E = 1/(rho R_g c_v),
+// gives T = p c_v E, R_g/c_v = rho R_g^2 E, and H = (c_v + R_g) T + e_f + |u|^2/2.
+template <class T>
+struct FaceThermo {
+  T g, H, ef, c2;
+};
+template <class T>
+__device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
+  const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
+  const T Ya = T(1) - q[4] - Yl - Ys;
+  const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
+  const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
+  const T rR = q[0] * Rg;
+  const T E = frcp(rR * cv);
+  const T Tg = q[3] * cv * E;
+  FaceThermo<T> t;
+  t.ef = q[4] * T(k::E0V) + Ys * T(k::E0S);
+  t.g = T(1) + Rg * rR * E;
+  t.H = (cv + Rg) * Tg + t.ef + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
+  t.c2 = t.g * Rg * Tg;
+  return t;
+}
+
 // Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns.
 // Roe flux in direction DIR (0: normal velocity u, 1: normal velocity v) -> F[14].
 template <class T, int DIR>
 __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
-  // face thermodynamics (frozen composition)
-  T gL, gR, HL, HR, efL, efR, c2L, c2R;
-  {
-    const T* q = qL;
-    const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
-    const T Ya = T(1) - q[4] - Yl - Ys;
-    const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
-    const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
-    const T pr = fdiv(q[3], q[0]);
-    efL = q[4] * T(k::E0V) + Ys * T(k::E0S);
-    const T gm1 = fdiv(Rg, cv);
-    gL = T(1) + gm1;
-    HL = pr * fdiv(cv, Rg) + efL + pr + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
-    c2L = gL * pr;
-  }
-  {
-    const T* q = qR;
-    const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
-    const T Ya = T(1) - q[4] - Yl - Ys;
-    const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
-    const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
-    const T pr = fdiv(q[3], q[0]);
-    efR = q[4] * T(k::E0V) + Ys * T(k::E0S);
-    const T gm1 = fdiv(Rg, cv);
-    gR = T(1) + gm1;
-    HR = pr * fdiv(cv, Rg) + efR + pr + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
-    c2R = gR * pr;
-  }
+  const FaceThermo<T> tL = face_thermo(qL), tR = face_thermo(qR);
+  const T gL = tL.g, gR = tR.g, HL = tL.H, HR = tR.H, efL = tL.ef, efR = tR.ef, c2L = tL.c2, c2R = tR.c2;
   const T unL = DIR == 0 ? qL[1] : qL[2], utL = DIR == 0 ? qL[2] : qL[1];
   const T unR = DIR == 0 ? qR[1] : qR[2], utR = DIR == 0 ? qR[2] : qR[1];
   const T mL = qL[0] * unL, mR = qR[0] * unR;
@@ -66,8 +64,9 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   T c2 = (gam - T(1)) * (H - T(0.5) * q2 - ef);
   const T c2min = T(0.01) * (c2L < c2R ? c2L : c2R);
   c2 = c2 < c2min ? c2min : c2;
-  const T c = m_sqrt(c2);
-  const T ic2 = frcp(c2);
+  const T rc = m_rsqrt(c2);
+  const T c = c2 * rc;
+  const T ic2 = rc * rc;
   const T dp = qR[3] - qL[3];
   const T dun = unR - unL;
   const T a1 = (dp - rt * c * dun) * T(0.5) * ic2;

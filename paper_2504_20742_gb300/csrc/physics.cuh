@@ -61,6 +61,8 @@ __device__ __forceinline__ T frcp(T a) { return fdiv(T(1), a); }
 // FP64 pipe of GB300 is a small fraction of its FP32 rate).
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
@@ -131,7 +133,12 @@ struct Prim {
 template <class T>
 __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   const T rho = U[0];
-  const T ir = frcp(rho);
+  // rho c_v straight from the conserved partial densities, then one reciprocal serves
+  // 1/rho = (rho c_v) X and 1/c_v = rho^2 X, X = 1/(rho rho c_v)
+  const T rYl = T(k::YL3) * U[8], rYs = T(k::YS3) * U[12];
+  const T rcv = (rho - U[4] - rYl - rYs) * T(k::CVA) + U[4] * T(k::CVV) + rYl * T(k::CL) + rYs * T(k::CS);
+  const T X = frcp(rho * rcv);
+  const T ir = rcv * X;
   w.rho = rho;
   w.u = U[1] * ir;
   w.v = U[2] * ir;
@@ -146,8 +153,8 @@ __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   w.Ys = T(k::YS3) * w.ms[3];
   const T Ya = T(1) - w.Yv - w.Yl - w.Ys;
   const T e = U[3] * ir - T(0.5) * (w.u * w.u + w.v * w.v);
-  w.cv = Ya * T(k::CVA) + w.Yv * T(k::CVV) + w.Yl * T(k::CL) + w.Ys * T(k::CS);
-  const T icv = frcp(w.cv);
+  w.cv = rcv * ir;
+  const T icv = rho * rho * X;
   w.Tg = (e - w.Yv * T(k::E0V) - w.Ys * T(k::E0S)) * icv;
   w.Rg = Ya * T(k::RA) + w.Yv * T(k::RV);
   w.p = rho * w.Rg * w.Tg;
