@@ -14,7 +14,7 @@ namespace ct {
 // zero gives a zero slope.)
 template <class T>
 __device__ __forceinline__ T vl_half_slope(T dm, T dp) {
-  return dm * dp > T(0) ? dm * fdiv(dp, dm + dp) : T(0);
+  return dm * dp > T(0) ? dm * tdiv(dp, dm + dp) : T(0);
 }
 
 // Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
@@ -31,7 +31,7 @@ __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
   const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
   const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
   const T rR = q[0] * Rg;
-  const T E = frcp(rR * cv);
+  const T E = trcp(rR * cv);
   const T Tg = q[3] * cv * E;
   FaceThermo<T> t;
   t.ef = q[4] * T(k::E0V) + Ys * T(k::E0S);
@@ -52,7 +52,7 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   const T mL = qL[0] * unL, mR = qR[0] * unR;
   // Roe averages
   const T sL = m_sqrt(qL[0]), sR = m_sqrt(qR[0]);
-  const T isum = frcp(sL + sR);
+  const T isum = trcp(sL + sR);
   const T wL = sL * isum, wR = sR * isum;
   const T rt = sL * sR;
   const T un = wL * unL + wR * unR;

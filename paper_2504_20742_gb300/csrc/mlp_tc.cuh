@@ -28,7 +28,9 @@ constexpr int WBYTES = woff(5);                 // 106,496
 constexpr int BLOB_BYTES = WOFF + WBYTES;       // 109,184
 constexpr int ABYTES = 128 * 128 * 2;           // activation operand, 32 KB
 
-__device__ __forceinline__ float silu(float z) { return z * (1.0f / (1.0f + __expf(-z))); }
+// z sigmoid(z) with the fast exponential and division (a few ulp; for z below about -87
+// the exponential overflows the divisor's range and the result is 0, the limit)
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Write 16 values of row `row` (columns c16*16 .. +15) as BF16 into a K-major operand with K
 // columns (two 16-byte core-matrix rows).
@@ -52,14 +54,17 @@ __device__ __forceinline__ void store_row16(unsigned char* buf, int row, int c16
 // 0..127 and return the 10 standardised outputs of their row in `out`.  `W`: weights in
 // shared memory; `bias`: the 4x128 + 16 biases; `tmem`: 128 allocated TMEM columns;
 // `mbar`/`phase`: the MMA-completion barrier.  Returns false if a wait timed out.
-// STREAM: W is a 32 KB shared buffer and each layer's weights are copied into it from the
-// global blob weights Wg just before that layer's MMA (keeps the fused step at 2 CTAs/SM).
+// STREAM: W is a 32 KB shared buffer; each layer's weights arrive there from the global
+// blob weights Wg by one bulk copy (completion on `wbar`/`wphase`), issued as soon as the
+// previous layer's MMAs have finished, so that the copy overlaps that layer's epilogue
+// (keeps the fused step at 2 CTAs/SM).
 // nrows: rows of the tile that carry data; 32-row groups beyond it skip the epilogue.  With
 // 8 or more warps, warps w and w+4 share the lane quarter of TMEM and split the columns.
 template <bool STREAM = false>
 __device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, const float* bias, uint32_t tmem,
                                          uint32_t mbar, uint32_t& phase, float* out,
-                                         const unsigned char* __restrict__ Wg = nullptr, int nrows = 128) {
+                                         const unsigned char* __restrict__ Wg = nullptr, int nrows = 128,
+                                         uint32_t wbar = 0, uint32_t* wphase = nullptr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -72,18 +77,17 @@ __device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, con
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (STREAM && tid == 0) {   // layer 0's weights
+    tc::mbar_arrive_expect_tx(wbar, (uint32_t)wbytes(0));
+    tc::bulk_g2s(tc::smem_addr(W), Wg + woff(0), (uint32_t)wbytes(0), wbar);
+  }
   for (int l = 0; l < 5; ++l) {
     const int K = kdim(l), N = ndim(l);
-    if (STREAM) {
-      const uint4* src = reinterpret_cast<const uint4*>(Wg + woff(l));
-      uint4* dst = reinterpret_cast<uint4*>(W);
-      for (int i = tid; i < wbytes(l) / 16; i += blockDim.x) dst[i] = src[i];
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-    }
     if (tid == 0) {
+      if (STREAM) {
+        if (!tc::mbar_wait(wbar, *wphase)) ok = false;
+        *wphase ^= 1u;
+      }
       const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(STREAM ? W : W + woff(l));
       const uint32_t sbo = (uint32_t)(K / 8) * 128u;
       const uint32_t idesc = tc::idesc_bf16_f32(128, N);
@@ -95,6 +99,10 @@ __device__ __forceinline__ bool run_tile(unsigned char* A, unsigned char* W, con
     if (!tc::mbar_wait(mbar, phase)) ok = false;
     phase ^= 1u;
     tc::fence_after_sync();
+    if (STREAM && tid == 0 && l < 4) {   // W is free again: fetch the next layer's weights
+      tc::mbar_arrive_expect_tx(wbar, (uint32_t)wbytes(l + 1));
+      tc::bulk_g2s(tc::smem_addr(W), Wg + woff(l + 1), (uint32_t)wbytes(l + 1), wbar);
+    }
     if (epi) {
       const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
       if (l < 4) {

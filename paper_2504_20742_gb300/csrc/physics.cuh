@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fastmath.cuh"
+
 namespace ct {
 
 constexpr int NF = 14;
@@ -57,6 +59,17 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 template <class T>
 __device__ __forceinline__ T frcp(T a) { return fdiv(T(1), a); }
+// Transport arithmetic (primitive recovery, reconstruction, Roe flux): FP64 divisions by
+// the Newton reciprocal of fastmath.cuh (a few ulp); the source terms keep IEEE division.
+__device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double tdiv(double a, double b) { return a * rcp_nr(b); }
+__device__ __forceinline__ float trcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double trcp(double a) { return rcp_nr(a); }
+// finiteness from the exponent bits (integer pipe, not the FP64 one)
+__device__ __forceinline__ bool finite_bits(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
 // Explicit precision overloads: a templated call must never promote float to double (the
 // FP64 pipe of GB300 is a small fraction of its FP32 rate).
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
@@ -137,7 +150,7 @@ __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   // 1/rho = (rho c_v) X and 1/c_v = rho^2 X, X = 1/(rho rho c_v)
   const T rYl = T(k::YL3) * U[8], rYs = T(k::YS3) * U[12];
   const T rcv = (rho - U[4] - rYl - rYs) * T(k::CVA) + U[4] * T(k::CVV) + rYl * T(k::CL) + rYs * T(k::CS);
-  const T X = frcp(rho * rcv);
+  const T X = trcp(rho * rcv);
   const T ir = rcv * X;
   w.rho = rho;
   w.u = U[1] * ir;

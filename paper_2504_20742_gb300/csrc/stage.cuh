@@ -286,10 +286,11 @@ constexpr size_t stage_smem_surr() {
 // (ready = true); the surrogate routine can also take and free them around a single call
 // (ready = false), since a CTA that has relinquished its allocation permit may not
 // allocate again.
-static __shared__ uint64_t s_tc_mbar;
+static __shared__ uint64_t s_tc_mbar;   // MMA completion
+static __shared__ uint64_t s_tc_wbar;   // weight bulk copies
 static __shared__ uint32_t s_tc_slot;
 struct TcCtx {
-  uint32_t tmem, phase;
+  uint32_t tmem, phase, wphase;
   bool ready;
 };
 __device__ __forceinline__ uint32_t tc_acquire() {
@@ -299,6 +300,7 @@ __device__ __forceinline__ uint32_t tc_acquire() {
   }
   if (threadIdx.x == 0) {
     tc::mbar_init(tc::smem_addr(&s_tc_mbar), 1);
+    tc::mbar_init(tc::smem_addr(&s_tc_wbar), 1);
     tc::fence_mbar_init();
   }
   tc::fence_before_sync();
@@ -332,10 +334,11 @@ __device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ bl
   float* hdr = reinterpret_cast<float*>(smem + SM_HDR);
   float* res = reinterpret_cast<float*>(smem + SM_RES);
   for (int q = tid; q < mlp::NFLOAT; q += NT) hdr[q] = ghdr[q];
-  uint32_t tmem, phase = 0;
+  uint32_t tmem, phase = 0, wphase = 0;
   if (tcx->ready) {
     tmem = tcx->tmem;
     phase = tcx->phase;
+    wphase = tcx->wphase;
     __syncthreads();
   } else {
     tmem = tc_acquire();   // includes the barrier
@@ -357,7 +360,7 @@ __device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ bl
     }
     float o[10];
     ok = mlp::run_tile<true>(A, W, hdr + mlp::F_BIAS, tmem, tc::smem_addr(&s_tc_mbar), phase, o, blob + mlp::WOFF,
-                             total - c0) && ok;
+                             total - c0, tc::smem_addr(&s_tc_wbar), &wphase) && ok;
     if (tid < 128) {
 #pragma unroll
       for (int q = 0; q < 10; ++q) outs[tid * 10 + q] = o[q] * hdr[mlp::F_YSD + q] + hdr[mlp::F_YMEAN + q];
@@ -370,8 +373,12 @@ __device__ __noinline__ void surrogate_tile(const unsigned char* __restrict__ bl
     }
     __syncthreads();
   }
-  if (tcx->ready) tcx->phase = phase;
-  else tc_release(tmem);
+  if (tcx->ready) {
+    tcx->phase = phase;
+    tcx->wphase = wphase;
+  } else {
+    tc_release(tmem);
+  }
   if (!ok && tid == 0) ntimeout += 1;   // a tensor-core wait gave up: the step reports it
 }
 
@@ -552,7 +559,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       area_w = T(1) + g.area_a * sw * sw;
       area_e = T(1) + g.area_a * se * se;
       const T Ac = T(1) + g.area_a * sc * sc;
-      const T iv = frcp(Ac * g.dx);
+      const T iv = trcp(Ac * g.dx);
       cw = area_w * iv;
       ce = area_e * iv;
       vol = Ac * g.dx;
@@ -625,7 +632,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
     cons_to_prim<T>(u14, w);
     if (dc.geom == 1) {
-      const T ijh = frcp(T(j) + T(0.5));
+      const T ijh = trcp(T(j) + T(0.5));
       const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
       const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
 #pragma unroll
@@ -644,7 +651,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         be -= An * fb[3][e];
       }
     } else {
-      acc[1] += w.p * fdiv(area_e - area_w, vol);
+      acc[1] += w.p * tdiv(area_e - area_w, vol);
     }
     // phase-change source limited on the flux-updated state
     T Q[NF];
@@ -669,7 +676,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
       for (int f = 0; f < NF; ++f) out[f] = u14[f] + dt * acc[f];
     } else {
-      const T idt = frcp(dt);
+      const T idt = trcp(dt);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const T un = Un[f * N + n];
@@ -680,7 +687,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       Uout[f * N + n] = out[f];
-      nbad += isfinite(out[f]) ? 0 : 1;
+      nbad += finite_bits(out[f]) ? 0 : 1;
     }
     if (STAGE == 2) {
       Prim<T> wn;
@@ -688,7 +695,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const T c = m_sqrt(wn.c2);
       T rate = (m_fabs(wn.u) + c) * g.idx;
       if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
-      dtmin = T(1) / rate;   // times cfl at the end
+      dtmin = trcp(rate);   // times cfl at the end
       pM = vol * out[0];
       pW = vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]);
       pE = vol * out[3];
@@ -785,6 +792,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     // up its allocation permit, so a lazy allocation would halve the CTAs per SM.
     tcx.tmem = tc_acquire();
     tcx.phase = 0;
+    tcx.wphase = 0;
     tcx.ready = true;
   }
   stage_tile<TL, T, STAGE, SURR>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
@@ -829,6 +837,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
   if (SURR) {
     tcx.tmem = tc_acquire();   // includes the barrier
     tcx.phase = 0;
+    tcx.wphase = 0;
     tcx.ready = true;
   }
   __syncthreads();
