@@ -28,9 +28,15 @@ constexpr int WBYTES = woff(5);                 // 106,496
 constexpr int BLOB_BYTES = WOFF + WBYTES;       // 109,184
 constexpr int ABYTES = 128 * 128 * 2;           // activation operand, 32 KB
 
-// z sigmoid(z) with the fast exponential and division (a few ulp; for z below about -87
-// the exponential overflows the divisor's range and the result is 0, the limit)
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// z sigmoid(z) = (z/2)(1 + tanh(z/2)) with the hardware tanh approximation (one
+// special-function operation; its relative error, below 2^-10, is under the BF16 rounding
+// that follows)
+__device__ __forceinline__ float silu(float z) {
+  const float h = 0.5f * z;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
 
 // Write 16 values of row `row` (columns c16*16 .. +15) as BF16 into a K-major operand with K
 // columns (two 16-byte core-matrix rows).

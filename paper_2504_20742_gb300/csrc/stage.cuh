@@ -479,35 +479,52 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   const T dt = T(dtd);
   const Geo<T> g = geo_of(dc, T(0));
 
-  // phase A: halo primitives
-  for (int p = tid; p < HX * HY; p += NT) {
-    const int hi = p % HX, hj = p / HX;
-    const int i = i0 + hi - 2, j = j0 + hj - 2;
-    const bool xin = i >= 0 && i < nx, rin = j >= 0 && j < nr;
-    bool need = (xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1;
-    if (dc.geom == 0) need = need && j == 0;
-    if (!need) continue;
-    T u14[NF];
-    if (xin && rin) {
-      const size_t n = (size_t)j * nx + i;
+  // phase A: halo primitives.  A thread owns up to NA halo cells; the interior loads of all
+  // of them are issued before any is converted, so their latencies overlap.
+  {
+    constexpr int NA = (HX * HY + NT - 1) / NT;
+    T u14[NA][NF];
+    int kind[NA];   // 0 skip, 1 interior, 2 ghost
 #pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-    } else {
-      load_ghost<T>(dc, Uin, N, i, j, u14);
-    }
-    Prim<T> w;
-    cons_to_prim<T>(u14, w);
-    qs[0][hj][hi] = w.rho;
-    qs[1][hj][hi] = w.u;
-    qs[2][hj][hi] = w.v;
-    qs[3][hj][hi] = w.p;
-    qs[4][hj][hi] = w.Yv;
+    for (int r = 0; r < NA; ++r) {
+      const int p = tid + r * NT;
+      const int hi = p % HX, hj = p / HX;
+      const int i = i0 + hi - 2, j = j0 + hj - 2;
+      const bool xin = i >= 0 && i < nx, rin = j >= 0 && j < nr;
+      bool need = p < HX * HY && (xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1;
+      if (dc.geom == 0) need = need && j == 0;
+      kind[r] = !need ? 0 : (xin && rin ? 1 : 2);
+      if (kind[r] == 1) {
+        const size_t n = (size_t)j * nx + i;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      qs[5 + q][hj][hi] = w.ml[q];
-      qs[9 + q][hj][hi] = w.ms[q];
+        for (int f = 0; f < NF; ++f) u14[r][f] = Uin[f * N + n];
+      }
     }
-    qs[13][hj][hi] = w.ns;
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      if (kind[r] == 0) continue;
+      const int p = tid + r * NT;
+      const int hi = p % HX, hj = p / HX;
+      if (kind[r] == 2) {   // out of line, through its own array: u14 stays in registers
+        T g14[NF];
+        load_ghost<T>(dc, Uin, N, i0 + hi - 2, j0 + hj - 2, g14);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u14[r][f] = g14[f];
+      }
+      Prim<T> w;
+      cons_to_prim<T>(u14[r], w);
+      qs[0][hj][hi] = w.rho;
+      qs[1][hj][hi] = w.u;
+      qs[2][hj][hi] = w.v;
+      qs[3][hj][hi] = w.p;
+      qs[4][hj][hi] = w.Yv;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        qs[5 + q][hj][hi] = w.ml[q];
+        qs[9 + q][hj][hi] = w.ms[q];
+      }
+      qs[13][hj][hi] = w.ns;
+    }
   }
   __syncthreads();
 
