@@ -65,6 +65,10 @@ def _workload(name):
     if name == "fp64":
         c, uf = cases.plume_case()
         return c, uf, "axisymmetric coaxial plume 1024x256, FP64 plain method", 0
+    if name == "fp64_viscous":
+        c, uf = cases.plume_case()
+        return (dict(c, viscous=1, nu_t=0.5), uf,
+                "axisymmetric coaxial plume 1024x256, FP64, viscous and diffusive fluxes (nu_t 0.5 m^2/s)", 0)
     if name in ("fp32", "fp32_mlp"):
         c, uf = cases.plume_case_mixed_precision()
         if name == "fp32":
@@ -85,6 +89,8 @@ TRAFFIC_SHAPE = 1
 FP64_FLOPS_PER_CELL_STAGE = 1098.2
 FP64_TRAFFIC_PER_CELL_LAUNCH = 173.0
 FP32_TRAFFIC_PER_CELL_LAUNCH = 133.4
+# the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s)
+FP64_VISC_FLOPS_PER_CELL_STAGE = 1754.7
 
 
 def measure_dgemm_tflops(dev) -> float:
@@ -258,14 +264,16 @@ def run_cuda(args):
         # kernel's FP64 arithmetic (2 DFMA + DADD + DMUL), counted once with ncu
         # (profiles/k_stage_fp64_plume1024x256.md); the peak is cuBLAS DGEMM measured here.
         fpk = measure_dgemm_tflops(dev)
-        flops = cells * FP64_FLOPS_PER_CELL_STAGE
+        per_cell = FP64_VISC_FLOPS_PER_CELL_STAGE if c.get("viscous") else FP64_FLOPS_PER_CELL_STAGE
+        flops = cells * per_cell
         ach = flops / (launch_ms_ev * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fpk, 4),
-                "traffic": FP64_TRAFFIC_PER_CELL_LAUNCH * cells if shape == TRAFFIC_SHAPE else None,
+                "traffic": (FP64_TRAFFIC_PER_CELL_LAUNCH * cells
+                            if shape == TRAFFIC_SHAPE and not c.get("viscous") else None),
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
-                "note": f"{FP64_FLOPS_PER_CELL_STAGE} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"}
+                "note": f"{per_cell} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"}
     else:
         alg_bytes = cells * 14 * elem * 2.5      # stage 1: read U, write U1; stage 2: read U1, U, write U
         bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
@@ -467,7 +475,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
     ap.add_argument("--workload", default="fp64",
-                    choices=("fp64", "fp32", "fp32_mlp", "active_fp32", "active_mlp", "batch64"))
+                    choices=("fp64", "fp64_viscous", "fp32", "fp32_mlp", "active_fp32", "active_mlp", "batch64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

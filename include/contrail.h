@@ -77,6 +77,9 @@ typedef struct {
   double p0, T0, Yv_inlet;                 /* nozzle inlet total conditions */
   double seed_l_n, seed_l_r, seed_s_n, seed_s_r; /* initial monodisperse populations in the core */
   double mix_width;                        /* > 0: core blends into ambient over this width */
+  double nu_t;                             /* turbulent kinematic viscosity, m^2/s (viscous = 1) */
+  int32_t viscous;                         /* 1: viscous and diffusive fluxes, Eqs. (25)-(26) */
+  int32_t pad_;                            /* unused, 0 */
 } ct_case;
 
 /* Diagnostics record of the last completed step (CT_NDIAG doubles):
@@ -276,7 +279,7 @@ size_t ct_batch_workspace_bytes(const ct_case *cases, int ncases);
 /* Elements of one batch state (sum over cases of 14 nx nr). */
 size_t ct_batch_state_elems(const ct_case *cases, int ncases);
 
-/* Validate 1..256 cases, set up every case's part of `work` (device, 256-byte aligned,
+/* Validate 1..96 cases, set up every case's part of `work` (device, 256-byte aligned,
  * ct_batch_workspace_bytes) with its inflow rows (ufac_rows_host: host, sum of nr doubles,
  * case after case, or NULL = all 1), and create the host object.  The batch's calls
  * enqueue on `stream`; the object owns a private stream used only for graph capture.

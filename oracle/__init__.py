@@ -15,6 +15,8 @@ from .oracle import (  # noqa: F401
     koop_log10J,
     hfg,
     roe_flux,
+    dv_mol,
+    diffusive_flux,
     source_batch,
     prim_to_cons_batch,
     cons_to_prim_batch,

@@ -102,6 +102,9 @@ typedef struct {
   double p0, T0, Yv_inlet;                 /* quasi-1D inlet total conditions */
   double seed_l_n, seed_l_r, seed_s_n, seed_s_r; /* optional initial populations in core */
   double mix_width;      /* > 0: core blends into the ambient through a tanh layer */
+  double nu_t;           /* turbulent kinematic viscosity, m^2/s (viscous cases) */
+  int32_t viscous;       /* 1: viscous and diffusive fluxes (reading M) */
+  int32_t pad_;
 } or_case;
 
 #define NDIAG 32
@@ -223,6 +226,85 @@ static void prim_to_cons(double p, double T, double u, double v, double Yv,
     u14[F_MS + k] = rho * ms[k];
   }
   u14[F_NS] = rho * ns;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Viscous and diffusive fluxes (Sec. 3.1 Eqs. (25)-(26); Sec. 3.2 "viscous fluxes are
+ * discretized using central differences"; reading M).  The Spalart-Allmaras model is out
+ * of scope: the turbulent viscosity is a case constant nu_t.  Effective transport:
+ *   mu_e = mu(T) + rho nu_t,   lambda_e = mu(T) c_p / Pr + rho c_p nu_t / Pr_t,
+ *   D_v = D_mol(T, p) + nu_t / Sc_t (vapour),   D_p = nu_t / Sc_t (moments, soot),
+ * with D_mol = 2.11e-5 (T/273.15)^1.94 (101325/p) m^2/s (the paper gives the scaling
+ * T^1.94/p).  Momentum diffuses in the vector-Laplacian form (mu_e grad u per face; the
+ * radial component also loses mu_e v / r^2 per volume), energy by conduction, by the work
+ * mu_e grad(|u|^2/2), and by the enthalpy that the diffusing water carries against dry air.
+ * Walls are adiabatic, impermeable and slip: nothing diffuses through them.
+ * ---------------------------------------------------------------------------------- */
+static const double PR_T = 0.9;     /* turbulent Prandtl number (silent) */
+static const double SC_T = 0.7;     /* turbulent Schmidt number (Sec. 3.1) */
+static const double DV0 = 2.11e-5;  /* vapour diffusivity at 273.15 K and 101325 Pa */
+
+double or_dv_mol(double T, double p) { return DV0 * pow(T / 273.15, 1.94) * (101325.0 / p); }
+
+typedef struct { double rho, u, v, p, T, Yv, Yl, Ys, Ya, cp; } tcell_t;
+
+/* transport state of a cell from its primitive vector (layout of prim_vec) */
+static void tcell(const double *q, tcell_t *t) {
+  t->rho = q[0]; t->u = q[1]; t->v = q[2]; t->p = q[3]; t->Yv = q[4];
+  t->Yl = 4.0 / 3.0 * PI * RHOL * q[8] * moment_scale(3);
+  t->Ys = 4.0 / 3.0 * PI * RHOS * q[12] * moment_scale(3);
+  t->Ya = 1.0 - t->Yv - t->Yl - t->Ys;
+  double Rg = t->Ya * RA + t->Yv * rv_gas();
+  t->T = t->p / (t->rho * Rg);
+  t->cp = t->Ya * cpa() + t->Yv * CPV + t->Yl * CL + t->Ys * CS;
+}
+
+/* effective viscosity, conductivity and diffusivities at (rho, T, p, c_p) */
+static void transport_coeff(double rho, double T, double p, double cp, double nu_t, double *mu_e,
+                            double *lam_e, double *Dv, double *Dp) {
+  double mu = mu_sutherland(T);
+  *mu_e = mu + rho * nu_t;
+  *lam_e = mu * cp / PR + rho * cp * nu_t / PR_T;
+  *Dv = or_dv_mol(T, p) + nu_t / SC_T;
+  *Dp = nu_t / SC_T;
+}
+
+/* Face flux G (along +n) between the cell on the minus side (qa) and on the plus side (qb),
+ * centres h apart.  The face's total flux is the Roe flux minus G. */
+void or_diffusive_flux(const double *qa, const double *qb, double h, double nu_t, double *G) {
+  tcell_t a, b;
+  tcell(qa, &a);
+  tcell(qb, &b);
+  double rho = 0.5 * (a.rho + b.rho), T = 0.5 * (a.T + b.T), p = 0.5 * (a.p + b.p), cp = 0.5 * (a.cp + b.cp);
+  double mu_e, lam_e, Dv, Dp;
+  transport_coeff(rho, T, p, cp, nu_t, &mu_e, &lam_e, &Dv, &Dp);
+  G[F_RHO] = 0.0;
+  G[F_RU] = mu_e * (b.u - a.u) / h;
+  G[F_RV] = mu_e * (b.v - a.v) / h;
+  G[F_RYV] = rho * Dv * (qb[4] - qa[4]) / h;
+  for (int f = 5; f < NF; ++f) G[f] = rho * Dp * (qb[f] - qa[f]) / h;
+  /* mass fluxes of liquid and ice water, against which dry air diffuses back */
+  double Gl = 4.0 / 3.0 * PI * RHOL * G[F_ML + 3] * moment_scale(3);
+  double Gs = 4.0 / 3.0 * PI * RHOS * G[F_MS + 3] * moment_scale(3);
+  double hva = (CPV - cpa()) * T + e0v();   /* h_v - h_a */
+  double hla = (CL - cpa()) * T;            /* h_l - h_a */
+  double hsa = (CS - cpa()) * T + e0s();    /* h_s - h_a */
+  double ka = 0.5 * (a.u * a.u + a.v * a.v), kb = 0.5 * (b.u * b.u + b.v * b.v);
+  G[F_RE] = lam_e * (b.T - a.T) / h + mu_e * (kb - ka) / h + hva * G[F_RYV] + hla * Gl + hsa * Gs;
+}
+
+/* viscous rate of a cell for the time step: 2 nu_max (1/dx^2 + 1/dr^2), and its mu_e */
+static double viscous_rate(const prim_t *w, double nu_t, double idx2_sum, double *mu_e_out) {
+  double cp = w->Ya * cpa() + w->Yv * CPV + w->Yl * CL + w->Ys * CS;
+  double mu_e, lam_e, Dv, Dp;
+  transport_coeff(w->rho, w->T, w->p, cp, nu_t, &mu_e, &lam_e, &Dv, &Dp);
+  if (mu_e_out) *mu_e_out = mu_e;
+  double nu = mu_e / w->rho;
+  double kap = lam_e / (w->rho * w->cv);
+  if (kap > nu) nu = kap;
+  if (Dv > nu) nu = Dv;
+  if (Dp > nu) nu = Dp;
+  return 2.0 * nu * idx2_sum;
 }
 
 /* ------------------------------------------------------------------------------------
@@ -829,6 +911,14 @@ static void residual(or_ctx *g, const double *U, double dt) {
         qR[f] = a1 - 0.5 * vl_slope(a1 - a0, a2 - a1);
       }
       or_roe_flux(qL, qR, 0, F);
+      /* walls are adiabatic, impermeable and slip: no diffusive flux through them */
+      int xwall = (i == 0 && c->bc_xlo == 1) || (i == nx && c->bc_xhi == 1);
+      if (c->viscous && !xwall) {
+        double qa[NF], qb[NF], G[NF];
+        for (int f = 0; f < NF; ++f) { qa[f] = WP(g, f, i - 1, j); qb[f] = WP(g, f, i, j); }
+        or_diffusive_flux(qa, qb, g->dx, c->nu_t, G);
+        for (int f = 0; f < NF; ++f) F[f] -= G[f];
+      }
       for (int f = 0; f < NF; ++f) g->Fx[((size_t)f * nr + j) * (nx + 1) + i] = F[f];
     }
   }
@@ -844,6 +934,13 @@ static void residual(or_ctx *g, const double *U, double dt) {
           qR[f] = a1 - 0.5 * vl_slope(a1 - a0, a2 - a1);
         }
         or_roe_flux(qL, qR, 1, F);
+        int rwall = j == nr && c->bc_rhi == 1;
+        if (c->viscous && !rwall) {
+          double qa[NF], qb[NF], G[NF];
+          for (int f = 0; f < NF; ++f) { qa[f] = WP(g, f, i, j - 1); qb[f] = WP(g, f, i, j); }
+          or_diffusive_flux(qa, qb, g->dr, c->nu_t, G);
+          for (int f = 0; f < NF; ++f) F[f] -= G[f];
+        }
         for (int f = 0; f < NF; ++f) g->Fr[((size_t)f * (nr + 1) + j) * nx + i] = F[f];
       }
     }
@@ -890,6 +987,11 @@ static void residual(or_ctx *g, const double *U, double dt) {
         Lf[F_RU] += w.p * (Ae - Aw) / (Ac * g->dx);
       } else {
         Lf[F_RV] += w.p / r_center(g, j);
+        if (c->viscous) {   /* radial component of the vector Laplacian: -mu_e v / r^2 */
+          double mu_e, rc = r_center(g, j);
+          viscous_rate(&w, c->nu_t, 0.0, &mu_e);
+          Lf[F_RV] -= mu_e * w.v / (rc * rc);
+        }
       }
       /* phase-change source, limited on the flux-updated stage state */
       double A[NF], Q[NF], aux[11];
@@ -944,6 +1046,10 @@ double or_compute_dt(or_ctx *g, const double *U, double cfl) {
     double c = sqrt(w.c2);
     double rate = (fabs(w.u) + c) / g->dx;
     if (g->c.geom == 1) rate += (fabs(w.v) + c) / g->dr;
+    if (g->c.viscous) {
+      double s2 = 1.0 / (g->dx * g->dx) + (g->c.geom == 1 ? 1.0 / (g->dr * g->dr) : 0.0);
+      rate += viscous_rate(&w, g->c.nu_t, s2, NULL);
+    }
     double dt = cfl / rate;
     if (dt < dtmin) dtmin = dt;
   }

@@ -84,6 +84,9 @@ def _L():
         lib.or_residual.argtypes = [C.c_void_p, _dp, d, _dp, _dp]
         lib.or_const.restype = d
         lib.or_const.argtypes = [C.c_int]
+        lib.or_dv_mol.restype = d
+        lib.or_dv_mol.argtypes = [d, d]
+        lib.or_diffusive_flux.argtypes = [_dp, _dp, d, d, _dp]
         _lib = lib
     return _lib
 
@@ -124,6 +127,19 @@ def const(which: str) -> float:
 
 def hfg(T: float) -> float:
     return _L().or_hfg(T)
+
+
+def dv_mol(T: float, p: float) -> float:
+    return _L().or_dv_mol(T, p)
+
+
+def diffusive_flux(qa, qb, h: float, nu_t: float) -> np.ndarray:
+    """Viscous/diffusive face flux G between primitive vectors qa (minus side), qb."""
+    qa = np.ascontiguousarray(qa, dtype=np.float64)
+    qb = np.ascontiguousarray(qb, dtype=np.float64)
+    G = np.zeros(NF)
+    _L().or_diffusive_flux(_ptr(qa), _ptr(qb), h, nu_t, _ptr(G))
+    return G
 
 
 def roe_flux(qL, qR, direction: int) -> np.ndarray:

@@ -37,6 +37,10 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
     const T c = m_sqrt(w.c2);
     T rate = (m_fabs(w.u) + c) * T(dc.idx);
     if (dc.geom == 1) rate += (m_fabs(w.v) + c) * T(dc.idr);
+    if (dc.viscous) {
+      T mu_e;
+      rate += viscous_rate<T>(w, T(dc.nu_t), T(dc.idx * dc.idx + (dc.geom == 1 ? dc.idr * dc.idr : 0.0)), mu_e);
+    }
     const T d = T(1) / rate;
     dtmin = d < dtmin ? d : dtmin;
   }
@@ -326,6 +330,8 @@ static ct_status validate(const ct_case* c, int precision) {
   if (c->geom == 0 && !(c->x_throat > 0.0)) return fail(CT_ERR_ARG, "x_throat must be > 0");
   if (c->geom == 1 && !(c->p_amb > 0.0 && c->T_amb > 0.0)) return fail(CT_ERR_ARG, "ambient p, T must be > 0");
   if (c->n_soot < 0.0 || c->soot_sigma <= 0.0) return fail(CT_ERR_ARG, "soot parameters invalid");
+  if (c->viscous != 0 && c->viscous != 1) return fail(CT_ERR_ARG, "viscous must be 0 or 1");
+  if (!(c->nu_t >= 0.0) || c->nu_t > 1.0e3) return fail(CT_ERR_ARG, "nu_t out of range [0, 1e3]");
   return CT_OK;
 }
 
@@ -371,6 +377,9 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.Yv0 = c->Yv_inlet;
   d.cp0 = (1.0 - c->Yv_inlet) * k::CPA + c->Yv_inlet * k::CPV;
   d.gam0 = d.cp0 / ((1.0 - c->Yv_inlet) * k::CVA + c->Yv_inlet * k::CVV);
+  d.viscous = c->viscous;
+  d.nu_t = c->nu_t;
+  d.fnu_t = (float)c->nu_t;
   d.sc.n_soot_ref = c->n_soot;
   const double ls = std::log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   d.sc.rp2 = c->soot_rm * c->soot_rm * std::exp(2.0 * ls * ls);
@@ -781,7 +790,8 @@ struct ct_batch {
   cudaStream_t stream = nullptr;   // the caller's
   cudaStream_t cap = nullptr;      // private stream the step graphs are captured on
   char* work = nullptr;            // device workspace (caller-owned)
-  BatchDev* bd = nullptr;          // its head
+  BatchCounters* ctr = nullptr;    // its head: the work-list counters
+  std::vector<BatchTable> table;   // one element: the kernels' parameter
   double* diag = nullptr;          // ncases x CT_NDIAG gather area
   std::vector<size_t> case_off;    // byte offset of each case's workspace
   std::vector<long long> state_off;
@@ -795,11 +805,11 @@ struct ct_batch {
 };
 
 static size_t batch_head_bytes(int ncases) {
-  return align256(sizeof(BatchDev)) + align256((size_t)ncases * CT_NDIAG * sizeof(double));
+  return align256(sizeof(BatchCounters)) + align256((size_t)ncases * CT_NDIAG * sizeof(double));
 }
 
 static ct_status batch_validate(const ct_case* cases, int ncases, int precision) {
-  if (!cases || ncases < 1 || ncases > MAX_BATCH) return fail(CT_ERR_ARG, "ncases out of range [1, 256]");
+  if (!cases || ncases < 1 || ncases > MAX_BATCH) return fail(CT_ERR_ARG, "ncases out of range [1, 96]");
   if (precision != CT_FP32 && precision != CT_FP32_MLP) return fail(CT_ERR_ARG, "batched steps are FP32 or FP32_MLP");
   for (int k = 0; k < ncases; ++k) {
     ct_status s = validate(&cases[k], precision);
@@ -809,11 +819,11 @@ static ct_status batch_validate(const ct_case* cases, int ncases, int precision)
   return CT_OK;
 }
 
-// Upload the work list and case table for the batch's current tile shape.
+// Build the work list and case table (the kernels' parameter) for the current tile shape.
 static ct_status batch_upload(ct_batch* b) {
   const int n = (int)b->cases.size();
-  std::vector<BatchDev> hv(1);
-  BatchDev& h = hv[0];
+  b->table.assign(1, BatchTable());
+  BatchTable& h = b->table[0];
   memset(&h, 0, sizeof(h));
   h.ncases = n;
   std::vector<int> order(n);
@@ -836,9 +846,6 @@ static ct_status batch_upload(ct_batch* b) {
     h.state_off[k] = b->state_off[k];
     h.cases[k] = make_dev(&b->cases[k], b->work + b->case_off[k], b->shape);
   }
-  if (cudaMemcpyAsync(b->bd, &h, sizeof(BatchDev), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
-    return cuda_check("batch table copy");
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return cuda_check("batch table sync");
   // persistent grid: every SM full, never more CTAs than tiles
   ct_status s = set_stage_attrs(b->shape, b->precision);
   if (s != CT_OK) return s;
@@ -868,20 +875,20 @@ static void batch_launch(ct_batch* b, int stage, const void* Uin, const void* Un
                          double cfl, cudaStream_t st) {
   const StageSet* ss = stage_set(b->shape);
   const int p = prec_index(b->precision);
-  BatchDev* bd = b->bd;
+  BatchCounters* ctr = b->ctr;
   const void* a1 = Uin;
   const void* a2 = Un;
   void* a3 = Uout;
   const void* a4 = blob;
   double a5 = cfl;
   int a6 = b->max_tiles;
-  void* args[] = {&bd, &a1, &a2, &a3, &a4, &a5, &a6};
+  void* args[] = {b->table.data(), &ctr, &a1, &a2, &a3, &a4, &a5, &a6};
   cudaLaunchKernel(ss->batch[p][stage - 1], dim3(b->grid), dim3(ss->nt), args, ss->smem[p], st);
 }
 
-__global__ void k_batch_diag(const BatchDev* __restrict__ bd, double* __restrict__ out) {
+__global__ void k_batch_diag(const __grid_constant__ BatchTable bt, double* __restrict__ out) {
   const int k = blockIdx.x, q = threadIdx.x;
-  if (k < bd->ncases && q < CT_NDIAG) out[(size_t)k * CT_NDIAG + q] = bd->cases[k].hdr->diag[q];
+  if (k < bt.ncases && q < CT_NDIAG) out[(size_t)k * CT_NDIAG + q] = bt.cases[k].hdr->diag[q];
 }
 
 extern "C" {
@@ -912,8 +919,8 @@ ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const
   b->precision = precision;
   b->stream = (cudaStream_t)stream;
   b->work = (char*)work;
-  b->bd = (BatchDev*)work;
-  b->diag = (double*)((char*)work + align256(sizeof(BatchDev)));
+  b->ctr = (BatchCounters*)work;
+  b->diag = (double*)((char*)work + align256(sizeof(BatchCounters)));
   size_t off = batch_head_bytes(ncases);
   long long so = 0;
   size_t row = 0;
@@ -930,6 +937,8 @@ ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const
                  ws_bytes(c), stream);
     row += (size_t)case_nr(c);
   }
+  if (s == CT_OK && cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), b->stream) != cudaSuccess)
+    s = cuda_check("batch counters");
   if (s == CT_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     s = cuda_check("capture stream");
   if (s == CT_OK) s = batch_upload(b);
@@ -1053,7 +1062,7 @@ ct_status ct_batch_step(ct_batch* b, void* U, void* U1, const void* blob, int ns
 ct_status ct_batch_diagnostics(ct_batch* b, double* host_out) {
   if (!b || !host_out) return fail(CT_ERR_ARG, "null batch or output");
   const int n = (int)b->cases.size();
-  k_batch_diag<<<n, 32, 0, b->stream>>>(b->bd, b->diag);
+  k_batch_diag<<<n, 32, 0, b->stream>>>(b->table[0], b->diag);
   if (cudaMemcpyAsync(host_out, b->diag, (size_t)n * CT_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, b->stream) !=
       cudaSuccess)
     return cuda_check("batch diag copy");

@@ -96,4 +96,86 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   for (int f = 4; f < NF; ++f) F[f] = fm * qu[f];
 }
 
+// ---- viscous and diffusive face fluxes (Sec. 3.1 Eqs. (25)-(26), central differences) ----
+// Turbulent viscosity nu_t is a case constant (the Spalart-Allmaras model is out of scope).
+// mu_e = mu(T) + rho nu_t, lambda_e = mu c_p / Pr + rho c_p nu_t / Pr_t (Pr_t = 0.9),
+// D_v = 2.11e-5 (T/273.15)^1.94 (101325/p) + nu_t/Sc_t, D_p = nu_t/Sc_t (Sc_t = 0.7).
+namespace visc {
+constexpr double PR_T = 0.9, SC_T = 0.7, DV0 = 2.11e-5;
+}
+template <class T>
+struct Transport {
+  T mu_e, lam_e, Dv, Dp;
+};
+template <class T>
+__device__ __forceinline__ T sutherland(T Tg) {
+  return T(1.716e-5 * (273.15 + 110.4)) * Tg * m_sqrt(Tg * T(1.0 / 273.15)) * T(1.0 / 273.15) / (Tg + T(110.4));
+}
+template <class T>
+__device__ __forceinline__ Transport<T> transport(T rho, T Tg, T p, T cp, T nu_t) {
+  Transport<T> t;
+  const T mu = sutherland(Tg);
+  t.mu_e = mu + rho * nu_t;
+  t.lam_e = cp * (mu * T(1.0 / k::PR) + rho * nu_t * T(1.0 / visc::PR_T));
+  t.Dp = nu_t * T(1.0 / visc::SC_T);
+  t.Dv = T(visc::DV0 * 101325.0) * m_exp(T(1.94) * m_log(Tg * T(1.0 / 273.15))) / p + t.Dp;
+  return t;
+}
+// temperature and c_p of a cell from its primitive vector (moments scaled per kg)
+template <class T>
+__device__ __forceinline__ void cell_T_cp(T rho, T p, T Yv, T ml3, T ms3, T& Tg, T& cp) {
+  const T Yl = T(k::YL3) * ml3, Ys = T(k::YS3) * ms3;
+  const T Ya = T(1) - Yv - Yl - Ys;
+  Tg = tdiv(p, rho * (Ya * T(k::RA) + Yv * T(k::RV)));
+  cp = Ya * T(k::CPA) + Yv * T(k::CPV) + Yl * T(k::CL) + Ys * T(k::CS);
+}
+
+// G (along +n) between the cells on the minus side (a) and the plus side (b), centres 1/ih
+// apart; q(f, side) returns primitive f (0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..12 moments,
+// 13 soot).  The face's total flux is the Roe flux minus G.  The energy flux carries
+// conduction, the work mu_e grad(|u|^2/2) and the enthalpy of the diffusing water
+// (against dry air).
+template <class T, class Q>
+__device__ __forceinline__ void sub_diffusive_flux(const Q& q, T ih, T nu_t, T* F) {
+  T Ta, cpa_, Tb, cpb;
+  cell_T_cp(q(0, 0), q(3, 0), q(4, 0), q(8, 0), q(12, 0), Ta, cpa_);
+  cell_T_cp(q(0, 1), q(3, 1), q(4, 1), q(8, 1), q(12, 1), Tb, cpb);
+  const T rho = T(0.5) * (q(0, 0) + q(0, 1)), Tf = T(0.5) * (Ta + Tb), pf = T(0.5) * (q(3, 0) + q(3, 1));
+  const Transport<T> tr = transport(rho, Tf, pf, T(0.5) * (cpa_ + cpb), nu_t);
+  const T ua = q(1, 0), ub = q(1, 1), va = q(2, 0), vb = q(2, 1);
+  const T Gu = tr.mu_e * (ub - ua) * ih, Gv = tr.mu_e * (vb - va) * ih;
+  const T rDv = rho * tr.Dv * ih, rDp = rho * tr.Dp * ih;
+  const T Gy = rDv * (q(4, 1) - q(4, 0));
+  F[1] -= Gu;
+  F[2] -= Gv;
+  F[4] -= Gy;
+  T Gl = T(0), Gs = T(0);
+#pragma unroll
+  for (int f = 5; f < 14; ++f) {
+    const T g = rDp * (q(f, 1) - q(f, 0));
+    if (f == 8) Gl = T(k::YL3) * g;
+    if (f == 12) Gs = T(k::YS3) * g;
+    F[f] -= g;
+  }
+  const T ka = T(0.5) * (ua * ua + va * va), kb = T(0.5) * (ub * ub + vb * vb);
+  const T hva = T(k::CPV - k::CPA) * Tf + T(k::E0V), hla = T(k::CL - k::CPA) * Tf, hsa = T(k::CS - k::CPA) * Tf + T(k::E0S);
+  F[3] -= tr.lam_e * (Tb - Ta) * ih + tr.mu_e * (kb - ka) * ih + hva * Gy + hla * Gl + hsa * Gs;
+}
+
+// rate of a cell's explicit diffusion limit, 2 nu_max (1/dx^2 + 1/dr^2), and its mu_e
+template <class T>
+__device__ __forceinline__ T viscous_rate(const Prim<T>& w, T nu_t, T ih2sum, T& mu_e) {
+  const T Ya = T(1) - w.Yv - w.Yl - w.Ys;
+  const T cp = Ya * T(k::CPA) + w.Yv * T(k::CPV) + w.Yl * T(k::CL) + w.Ys * T(k::CS);
+  const Transport<T> tr = transport(w.rho, w.Tg, w.p, cp, nu_t);
+  mu_e = tr.mu_e;
+  const T irho = trcp(w.rho);
+  T nu = tr.mu_e * irho;
+  const T kap = tr.lam_e * irho * trcp(w.cv);
+  nu = kap > nu ? kap : nu;
+  nu = tr.Dv > nu ? tr.Dv : nu;
+  nu = tr.Dp > nu ? tr.Dp : nu;
+  return T(2) * nu * ih2sum;
+}
+
 }  // namespace ct

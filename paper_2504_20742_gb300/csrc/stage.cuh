@@ -51,6 +51,9 @@ static_assert(sizeof(WsHeader) <= HDR_BYTES, "header");
 struct DevCase {
   int geom, nx, nr, bc_xlo, bc_xhi, bc_rhi, jw, nblocks;
   int tiles_x, tiles_y;   // tile grid of the shape in use (nblocks = tiles_x * tiles_y)
+  int viscous;            // viscous and diffusive fluxes
+  double nu_t;            // turbulent kinematic viscosity
+  float fnu_t;
   double dx, dr, idx, idr, cfl;
   double area_a, x_throat, wall_len;
   double p0, T0, Yv0, cp0, gam0;       // nozzle inlet mixture
@@ -84,13 +87,13 @@ constexpr int NT_AUX = 288;
 // Geometry in the state precision (no double->float conversions inside FP32 kernels).
 template <class T>
 struct Geo {
-  T dx, idx, dr, idr, wall_len, area_a, ixt;
+  T dx, idx, dr, idr, wall_len, area_a, ixt, nu_t;
 };
 __device__ __forceinline__ Geo<float> geo_of(const DevCase& d, float) {
-  return {d.fdx, d.fidx, d.fdr, d.fidr, d.fwall_len, d.farea_a, d.fixt};
+  return {d.fdx, d.fidx, d.fdr, d.fidr, d.fwall_len, d.farea_a, d.fixt, d.fnu_t};
 }
 __device__ __forceinline__ Geo<double> geo_of(const DevCase& d, double) {
-  return {d.dx, d.idx, d.dr, d.idr, d.wall_len, d.area_a, 1.0 / d.x_throat};
+  return {d.dx, d.idx, d.dr, d.idr, d.wall_len, d.area_a, 1.0 / d.x_throat, d.nu_t};
 }
 
 // ---- boundary ghost cells (Sec. 4.1; reading A1) ---------------------------------------
@@ -556,6 +559,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       qR[f] = fR[f][p];
     }
     roe_flux<T, 0>(qL, qR, F);
+    // walls are adiabatic, impermeable and slip: nothing diffuses through them
+    if (dc.viscous && !((i == 0 && dc.bc_xlo == 1) || (i == nx && dc.bc_xhi == 1))) {
+      const auto q = [&](int f, int side) -> T { return qs[f][hj + 2][fx + 1 + side]; };
+      sub_diffusive_flux<T>(q, g.idx, g.nu_t, F);
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
   }
@@ -627,6 +635,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         qR[f] = fR[f][p];
       }
       roe_flux<T, 1>(qL, qR, F);
+      if (dc.viscous && !(jj == nr && dc.bc_rhi == 1)) {
+        const auto q = [&](int f, int side) -> T { return qs[f][fy + 1 + side][hi + 2]; };
+        sub_diffusive_flux<T>(q, g.idr, g.nu_t, F);
+      }
 #pragma unroll
       for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
     }
@@ -660,6 +672,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         acc[f] += cs * Fs - cn * Fn;
       }
       acc[2] += w.p * ijh * g.idr;
+      if (dc.viscous) {   // radial component of the vector Laplacian: -mu_e v / r^2
+        T mu_e;
+        viscous_rate<T>(w, g.nu_t, T(0), mu_e);
+        acc[2] -= mu_e * w.v * (ijh * ijh) * (g.idr * g.idr);
+      }
       if (j == nr - 1) {
         const T An = T(nr) * g.dr * g.dx;
         const int e = (cj + 1) * TX + ci;
@@ -712,6 +729,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const T c = m_sqrt(wn.c2);
       T rate = (m_fabs(wn.u) + c) * g.idx;
       if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
+      if (dc.viscous) {
+        T mu_e;
+        rate += viscous_rate<T>(wn, g.nu_t, g.idx * g.idx + (dc.geom == 1 ? g.idr * g.idr : T(0)), mu_e);
+      }
       dtmin = trcp(rate);   // times cfl at the end
       pM = vol * out[0];
       pW = vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]);
@@ -797,6 +818,9 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   }
 }
 
+// Register budget from __launch_bounds__: the register file is split between the SM's four
+// schedulers, so 18 warps (two CTAs of 288 threads) leave 96 registers per thread and 9
+// warps (one FP64 CTA) 168; a larger cap fails at launch.
 template <class TL, class T, int STAGE, bool SURR>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
@@ -826,10 +850,11 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
 // max_tiles bounds the tiles one CTA takes.  The surrogate variant uses a small bound: the
 // SM places a further CTA of a kernel that holds TMEM only when one of its CTAs finishes,
 // so CTAs that never finished would keep one CTA per SM for the whole launch.
-constexpr int MAX_BATCH = 256;
-struct BatchDev {
-  unsigned int next_tile;
-  unsigned int exited;
+constexpr int MAX_BATCH = 96;
+// The work list and the case table travel as the kernel's parameter (__grid_constant__,
+// about 28 KB): every field a tile reads is a constant-cache load indexed by the case, with
+// no copy into shared memory and no registers to hold it.
+struct BatchTable {
   int ncases, total_tiles;
   int tile_start[MAX_BATCH + 1];   // first work-list tile of each slot
   int case_of[MAX_BATCH];          // case index of each work-list slot
@@ -837,18 +862,20 @@ struct BatchDev {
   long long state_off[MAX_BATCH];  // element offset of the case's first plane
   DevCase cases[MAX_BATCH];
 };
+static_assert(sizeof(BatchTable) + 128 <= 32764, "kernel parameter space");
+struct BatchCounters {
+  unsigned int next_tile;
+  unsigned int exited;
+};
 
 template <class TL, class T, int STAGE, bool SURR>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
-    k_batch_stage(BatchDev* __restrict__ bd, const T* __restrict__ Uin, const T* Un, T* Uout,
-                  const unsigned char* __restrict__ blob, double cfl, int max_tiles) {
+    k_batch_stage(const __grid_constant__ BatchTable bt, BatchCounters* __restrict__ ctr, const T* __restrict__ Uin,
+                  const T* Un, T* Uout, const unsigned char* __restrict__ blob, double cfl, int max_tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) DevCase s_dc;
   __shared__ int s_t, s_slot;
-  __shared__ int s_start[MAX_BATCH + 1];
   const int tid = threadIdx.x;
-  const int ncases = bd->ncases, total = bd->total_tiles;
-  for (int q = tid; q <= ncases; q += TL::NT) s_start[q] = bd->tile_start[q];
+  const int ncases = bt.ncases, total = bt.total_tiles;
   TcCtx tcx;
   tcx.ready = false;
   if (SURR) {
@@ -857,14 +884,13 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     tcx.wphase = 0;
     tcx.ready = true;
   }
-  __syncthreads();
   for (int taken = 0; taken < max_tiles; ++taken) {
     if (tid == 0) {
-      const int t = (int)atomicAdd(&bd->next_tile, 1u);
-      int lo = 0, hi = ncases;   // slot with s_start[slot] <= t < s_start[slot + 1]
+      const int t = (int)atomicAdd(&ctr->next_tile, 1u);
+      int lo = 0, hi = ncases;   // slot with tile_start[slot] <= t < tile_start[slot + 1]
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (s_start[mid] <= t) lo = mid; else hi = mid;
+        if (bt.tile_start[mid] <= t) lo = mid; else hi = mid;
       }
       s_t = t;
       s_slot = lo;
@@ -872,25 +898,19 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     __syncthreads();
     const int t = s_t, slot = s_slot;
     if (t >= total) break;
-    const int k = bd->case_of[slot];
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(&bd->cases[k]);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_dc);
-      for (int q = tid; q < (int)(sizeof(DevCase) / 4); q += TL::NT) dst[q] = src[q];
-    }
-    __syncthreads();
-    const int lt = t - s_start[slot], tx = bd->tiles_x[k];
-    const long long off = bd->state_off[k];
-    stage_tile<TL, T, STAGE, SURR>(s_dc, lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off, blob,
-                                   smem_raw, cfl, &tcx);
+    const int k = bt.case_of[slot];
+    const int lt = t - bt.tile_start[slot], tx = bt.tiles_x[k];
+    const long long off = bt.state_off[k];
+    stage_tile<TL, T, STAGE, SURR>(bt.cases[k], lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off,
+                                   blob, smem_raw, cfl, &tcx);
     __syncthreads();
   }
   if (SURR) tc_release(tcx.tmem);
   if (tid == 0) {
     __threadfence();
-    if (atomicAdd(&bd->exited, 1u) == gridDim.x - 1) {   // every CTA has left the loop
-      bd->next_tile = 0u;
-      bd->exited = 0u;
+    if (atomicAdd(&ctr->exited, 1u) == gridDim.x - 1) {   // every CTA has left the loop
+      ctr->next_tile = 0u;
+      ctr->exited = 0u;
       __threadfence();
     }
   }

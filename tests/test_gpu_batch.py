@@ -54,9 +54,10 @@ def _single(P, c, uf, prec, nsteps, blob=None, shape=-1):
     return s.U.clone(), d
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
-def test_every_tile_shape_gives_the_same_state(P, blob, prec):
+@pytest.mark.parametrize("prec,viscous", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
+def test_every_tile_shape_gives_the_same_state(P, blob, prec, viscous):
     c, uf = cases.mixing_layer_case(nx=100, nr=44)
+    c = dict(c, viscous=viscous, nu_t=0.05)
     ref, d0 = _single(P, c, uf, prec, 12, blob, 0)
     assert d0[8] == 0 and d0[7] > 0
     for shape in range(1, P.ct_tile_shape_count()):

@@ -37,6 +37,11 @@ def _run_pair(P, c, uf, nsteps, precision=0, cfl=0.5):
     return s, o, U0g, s.state64(), Uo, np.array(diags), do
 
 
+def _viscous(cu, nu_t):
+    c, uf = cu
+    return dict(c, viscous=1, nu_t=nu_t), uf
+
+
 # Well-conditioned cases: 100 steps at 1e-9.  The nucleating mixing layers amplify a
 # rounding-level perturbation of the oracle's own input to O(1) within about 50 steps
 # (pinned in test_oracle_solver.py); they are checked by shadowing in
@@ -47,10 +52,16 @@ CASES = {
     "freezing_ragged_77x29": (lambda: cases.freezing_case(nx=77, nr=29), 100),
     "mixing96x40_2steps": (lambda: cases.mixing_layer_case(), 2),
     "closed_box_2steps": (lambda: cases.closed_box_case(), 2),
+    # viscous and diffusive fluxes (Eqs. (25)-(26), constant turbulent viscosity)
+    "freezing96x40_viscous": (lambda: _viscous(cases.freezing_case(), 0.05), 100),
+    "nozzle400_viscous": (lambda: (dict(cases.nozzle_case(nx=400), viscous=1, nu_t=1e-4), None), 100),
+    "plume256x64_viscous": (lambda: _viscous(cases.plume_case(nx=256, nr=64), 0.5), 100),
+    "closed_box_viscous_2steps": (lambda: _viscous(cases.closed_box_case(), 0.05), 2),
 }
 
 CHAOTIC = {
     "mixing96x40": lambda: cases.mixing_layer_case(),
+    "mixing96x40_viscous": lambda: _viscous(cases.mixing_layer_case(), 0.05),
     "mixing_ragged_77x29": lambda: cases.mixing_layer_case(nx=77, nr=29),
     "closed_box": lambda: cases.closed_box_case(),
 }
@@ -109,6 +120,28 @@ def test_fp64_parity_plume_1024x256_100_steps(P):
     assert np.all(e <= TOL), report(e)
     for k in (1, 2, 3):
         assert np.allclose(dg[:, k], do[:, k], rtol=1e-12, atol=0), k
+
+
+def test_fp64_parity_plume_1024x256_viscous_50_steps(P):
+    """The benchmark plume with viscous and diffusive fluxes (nu_t = 0.5 m^2/s)."""
+    c, uf = _viscous(cases.plume_case(), 0.5)
+    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 50)
+    e = field_rel_err(Ug, Uo)
+    assert np.all(e <= TOL), report(e)
+    assert np.allclose(dg[:, 0], do[:, 0], rtol=1e-11, atol=0)
+
+
+def test_fp32_viscous_against_oracle(P):
+    """FP32 transport with FP64 islands and the diffusive fluxes, 100 steps of the freezing
+    plume, field by field against the FP64 oracle."""
+    c, uf = _viscous(cases.freezing_case(), 0.05)
+    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 100, precision=1)
+    e = field_rel_err(Ug, Uo)
+    print("FP32 viscous freezing plume, 100 steps:", report(e))
+    # bulk fields to FP32 rounding accumulated over the run; the droplet moments also carry
+    # the FP32 rates of freezing and evaporation (exponentials of the Koop rate)
+    assert np.all(e[[0, 1, 3, 4, 13]] <= 1e-4), report(e)
+    assert np.all(e <= 5e-3), report(e)
 
 
 def test_conservation_closed_box_on_gpu(P):
