@@ -79,7 +79,7 @@ typedef struct {
   double mix_width;                        /* > 0: core blends into ambient over this width */
   double nu_t;                             /* turbulent kinematic viscosity, m^2/s (viscous = 1) */
   int32_t viscous;                         /* 1: viscous and diffusive fluxes, Eqs. (25)-(26) */
-  int32_t pad_;                            /* unused, 0 */
+  int32_t tables;                          /* 1: water properties from tables, 2nd-order Taylor */
 } ct_case;
 
 /* Diagnostics record of the last completed step (CT_NDIAG doubles):

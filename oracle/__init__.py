@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     hfg,
     roe_flux,
     dv_mol,
+    table_eval,
     diffusive_flux,
     source_batch,
     prim_to_cons_batch,

@@ -104,7 +104,7 @@ typedef struct {
   double mix_width;      /* > 0: core blends into the ambient through a tanh layer */
   double nu_t;           /* turbulent kinematic viscosity, m^2/s (viscous cases) */
   int32_t viscous;       /* 1: viscous and diffusive fluxes (reading M) */
-  int32_t pad_;
+  int32_t tables;        /* 1: water properties from tables, second-order Taylor (reading N) */
 } or_case;
 
 #define NDIAG 32
@@ -318,7 +318,75 @@ typedef struct {
   double n_soot_ref;   /* exit soot number per m^3 (0: no heterogeneous nucleation) */
   double rp2;          /* lognormal soot <r_p^2> */
   int phase_change, freezing;
+  int tables;          /* reading N */
 } src_par_t;
+
+/* ------------------------------------------------------------------------------------
+ * Tabulated water properties (Sec. 3.2: properties tabulated before the run and
+ * interpolated by a second-order Taylor expansion; reading N).  Nodes every 0.5 K from
+ * 150 K to 640 K; each node holds the value and the first and half the second derivative
+ * of ln p_sat,l, ln p_sat,i and sigma_lg, from the closed forms of readings B and C.  A
+ * query uses the nearest node: f(T) = c0 + d (c1 + d c2), d = T - T_k (|d| <= 0.25 K; out of
+ * range, the end node's expansion).
+ * ---------------------------------------------------------------------------------- */
+#define TAB_N 981
+static const double TAB_T0 = 150.0, TAB_DT = 0.5;
+static double g_tab[3][TAB_N][3];
+static int g_tab_ready = 0;
+
+static void build_tables(void) {
+  if (g_tab_ready) return;
+  const double al = -6096.9385, cl1 = -2.711193e-2, dl = 1.673952e-5, el = 2.433502;   /* Sonntag, liquid */
+  const double ai = -6024.5282, ci1 = 1.0613868e-2, di = -1.3198825e-5, ei = -0.49382577;   /* ice */
+  const double Tc = 647.096, B = 0.2358, mu = 1.256, b = 0.625;                       /* IAPWS sigma */
+  for (int k = 0; k < TAB_N; ++k) {
+    double T = TAB_T0 + TAB_DT * k;
+    /* ln p = a/T + b0 + c T + d T^2 + e ln T: f' = -a/T^2 + c + 2 d T + e/T, f'' = 2a/T^3 + 2d - e/T^2 */
+    g_tab[0][k][0] = or_ln_psat_l(T);
+    g_tab[0][k][1] = -al / (T * T) + cl1 + 2.0 * dl * T + el / T;
+    g_tab[0][k][2] = 0.5 * (2.0 * al / (T * T * T) + 2.0 * dl - el / (T * T));
+    g_tab[1][k][0] = or_ln_psat_i(T);
+    g_tab[1][k][1] = -ai / (T * T) + ci1 + 2.0 * di * T + ei / T;
+    g_tab[1][k][2] = 0.5 * (2.0 * ai / (T * T * T) + 2.0 * di - ei / (T * T));
+    /* sigma = B tau^mu (1 - b tau), tau = 1 - T/Tc */
+    double tau = 1.0 - T / Tc;
+    double ds_dtau = B * pow(tau, mu - 1.0) * (mu * (1.0 - b * tau) - b * tau);
+    double d2s_dtau2 = B * (mu * (mu - 1.0) * pow(tau, mu - 2.0) * (1.0 - b * tau) - 2.0 * b * mu * pow(tau, mu - 1.0));
+    g_tab[2][k][0] = or_sigma_lg(T);
+    g_tab[2][k][1] = -ds_dtau / Tc;
+    g_tab[2][k][2] = 0.5 * d2s_dtau2 / (Tc * Tc);
+  }
+  g_tab_ready = 1;
+}
+
+/* value (der = 0) or first derivative (der = 1) of tabulated property `which` at T */
+static double tab_eval(int which, double T, int der) {
+  int k = (int)floor((T - TAB_T0) / TAB_DT + 0.5);
+  if (k < 0) k = 0;
+  if (k > TAB_N - 1) k = TAB_N - 1;
+  double d = T - (TAB_T0 + TAB_DT * k);
+  const double *c = g_tab[which][k];
+  return der ? c[1] + 2.0 * c[2] * d : c[0] + d * (c[1] + d * c[2]);
+}
+
+double or_table_eval(int which, double T, int der) {
+  build_tables();
+  return tab_eval(which, T, der);
+}
+
+static double prop_lnpl(const src_par_t *sp, double T) { return sp->tables ? tab_eval(0, T, 0) : or_ln_psat_l(T); }
+static double prop_lnpi(const src_par_t *sp, double T) { return sp->tables ? tab_eval(1, T, 0) : or_ln_psat_i(T); }
+static double prop_sigma(const src_par_t *sp, double T) { return sp->tables ? tab_eval(2, T, 0) : or_sigma_lg(T); }
+
+/* T_sat of reading D with the tabulated curve and its derivative (same start, 6 steps) */
+static double prop_tsat(const src_par_t *sp, double pv, int which) {
+  if (!sp->tables) return or_tsat(pv, which);
+  double lnpv = log(pv);
+  double h0 = which == 0 ? HLV0 : HLV0 + HSL0;
+  double T = 1.0 / (1.0 / TREF - rv_gas() * log(pv / 611.2) / h0);
+  for (int it = 0; it < 6; ++it) T = T - (tab_eval(which, T, 0) - lnpv) / tab_eval(which, T, 1);
+  return T;
+}
 
 /* Young's nu, Eq. (16). */
 static double young_nu(double Tsat, double h, double gam_g, double cp_g) {
@@ -369,7 +437,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   /* a vapour-free cell keeps a vanishing partial pressure so that ln S stays finite */
   double pv = rho * w->Yv * Rv * T;
   if (pv < 1.0e-30) pv = 1.0e-30;
-  double lnpsl = or_ln_psat_l(T), lnpsi = or_ln_psat_i(T);
+  double lnpsl = prop_lnpl(sp, T), lnpsi = prop_lnpi(sp, T);
   double lnSl = log(pv) - lnpsl;
   double lnSi = log(pv) - lnpsi;
   aux[0] = lnSl;
@@ -403,7 +471,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   /* Nucleation, Eqs. (3)-(6), (9)-(11); J_het gated by the soot number (reading F). */
   double Jeff = 0.0, rc = 0.0;
   if (lnSl > 0.0) {
-    double sig = or_sigma_lg(T);
+    double sig = prop_sigma(sp, T);
     rc = 2.0 * sig / (RHOL * Rv * T * lnSl);
     double dGkT = 4.0 / 3.0 * PI * sig * rc * rc / (KB * T);
     double rhov = rho * w->Yv;
@@ -420,7 +488,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
     }
     aux[2] = lnJhom;
     /* Eq. (5), alpha_crit from Young's heat-transfer law at r_crit (reading F). */
-    double Tsat = or_tsat(pv, 0);
+    double Tsat = prop_tsat(sp, pv, 0);
     double nu = young_nu(Tsat, hfg, gam_g, cp_g);
     double Knc = lbar / (2.0 * rc);
     double alpha_c = lam_g / (rc * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Knc) + 3.78 * (1.0 - nu) * Knc / PR));
@@ -435,12 +503,12 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   double Gl = 0.0, Gs = 0.0;
   if (present_l) {
     double r20 = sqrt(ml[2] / ml[0]);
-    double Tsat = or_tsat(pv, 0);
-    Gl = or_growth(r20, T, Tsat, lnSl, or_sigma_lg(T), RHOL, hfg, lam_g, lbar, gam_g, cp_g);
+    double Tsat = prop_tsat(sp, pv, 0);
+    Gl = or_growth(r20, T, Tsat, lnSl, prop_sigma(sp, T), RHOL, hfg, lam_g, lbar, gam_g, cp_g);
   }
   if (present_s) {
     double r20 = sqrt(ms[2] / ms[0]);
-    double Tsat = or_tsat(pv, 1);
+    double Tsat = prop_tsat(sp, pv, 1);
     Gs = or_growth(r20, T, Tsat, lnSi, SIGMA_SV, RHOS, hsg, lam_g, lbar, gam_g, cp_g);
   }
   /* Stage relaxation limiter (reading J): the vapour-growth exchange relaxes the driving
@@ -452,7 +520,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   double xsum = 0.0;
   if (present_l) {
     double r20 = sqrt(ml[2] / ml[0]);
-    double Tsat = or_tsat(pv, 0);
+    double Tsat = prop_tsat(sp, pv, 0);
     double nu = young_nu(Tsat, hfg, gam_g, cp_g);
     double Kn = lbar / (2.0 * r20);
     double cond = lam_g / (RHOL * hfg * r20 * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Kn) + 3.78 * (1.0 - nu) * Kn / PR));
@@ -461,7 +529,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   }
   if (present_s) {
     double r20 = sqrt(ms[2] / ms[0]);
-    double Tsat = or_tsat(pv, 1);
+    double Tsat = prop_tsat(sp, pv, 1);
     double nu = young_nu(Tsat, hsg, gam_g, cp_g);
     double Kn = lbar / (2.0 * r20);
     double cond = lam_g / (RHOS * hsg * r20 * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Kn) + 3.78 * (1.0 - nu) * Kn / PR));
@@ -714,7 +782,7 @@ static void inflow_state(const or_case *c, double r, double ufac, double *u14) {
 }
 
 /* Quasi-1D subsonic inlet from total conditions with the interior velocity (Sec. 4.1
- * "total-condition inlets"; isentropic relation of the inlet mixture). */
+ * prescribes total conditions at the inlets; isentropic relation of the inlet mixture). */
 static void q1d_inlet_state(const or_case *c, double u, double *u14) {
   double zero[4] = {0, 0, 0, 0};
   double Yv = c->Yv_inlet;
@@ -753,6 +821,8 @@ or_ctx *or_create(const or_case *c, const double *ufac_rows) {
   g->sp.phase_change = c->phase_change;
   g->sp.freezing = c->freezing;
   g->sp.n_soot_ref = c->n_soot;
+  g->sp.tables = c->tables;
+  build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   g->sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);   /* lognormal E[r^2] */
   if (c->geom == 1) {
@@ -1033,7 +1103,7 @@ static void residual(or_ctx *g, const double *U, double dt) {
   g->bflux[2] = be;
 }
 
-/* Global CFL time step (Sec. 3.2, "globally controlled CFL"; reading A10). */
+/* Global CFL time step (Sec. 3.2: one CFL number controls the whole domain; reading A10). */
 double or_compute_dt(or_ctx *g, const double *U, double cfl) {
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
@@ -1148,6 +1218,8 @@ void or_source_batch(const or_case *c, const double *U, int n, double dt, double
   sp.phase_change = c->phase_change;
   sp.freezing = c->freezing;
   sp.n_soot_ref = c->n_soot;
+  sp.tables = c->tables;
+  build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);
   for (int m = 0; m < n; ++m) {

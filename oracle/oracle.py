@@ -84,6 +84,8 @@ def _L():
         lib.or_residual.argtypes = [C.c_void_p, _dp, d, _dp, _dp]
         lib.or_const.restype = d
         lib.or_const.argtypes = [C.c_int]
+        lib.or_table_eval.restype = d
+        lib.or_table_eval.argtypes = [C.c_int, d, C.c_int]
         lib.or_dv_mol.restype = d
         lib.or_dv_mol.argtypes = [d, d]
         lib.or_diffusive_flux.argtypes = [_dp, _dp, d, d, _dp]
@@ -127,6 +129,11 @@ def const(which: str) -> float:
 
 def hfg(T: float) -> float:
     return _L().or_hfg(T)
+
+
+def table_eval(which: int, T: float, der: int = 0) -> float:
+    """Tabulated property (0 ln p_sat,l, 1 ln p_sat,i, 2 sigma_lg) or its derivative."""
+    return _L().or_table_eval(which, T, der)
 
 
 def dv_mol(T: float, p: float) -> float:

@@ -64,6 +64,32 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
   if (threadIdx.x == 0) dc.hdr->dt_cur = dc.cfl * fin[0];
 }
 
+// ---- tables of water properties (Sec. 3.2) -------------------------------------------------
+// Node k of each property: value, first derivative, half the second derivative of the
+// closed forms (Sonntag ln p = a/T + b + cT + dT^2 + e ln T; IAPWS sigma = B tau^mu (1 - b tau)).
+__global__ void k_tables(double* __restrict__ tab, float* __restrict__ tabf) {
+  for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < TAB_N; kk += gridDim.x * blockDim.x) {
+    const double T = 150.0 + 0.5 * kk, iT = 1.0 / T;
+    double c[3][3];
+    c[0][0] = ln_psat_liq<double>(T);
+    c[0][1] = dln_psat_liq<double>(T);
+    c[0][2] = 0.5 * (2.0 * -6096.9385 * iT * iT * iT + 2.0 * 1.673952e-5 - 2.433502 * iT * iT);
+    c[1][0] = ln_psat_ice<double>(T);
+    c[1][1] = dln_psat_ice<double>(T);
+    c[1][2] = 0.5 * (2.0 * -6024.5282 * iT * iT * iT + 2.0 * -1.3198825e-5 + 0.49382577 * iT * iT);
+    const double tau = 1.0 - T / 647.096, mu = 1.256, bb = 0.625, B = 0.2358;
+    const double tm2 = pow(tau, mu - 2.0), tm1 = tm2 * tau;
+    c[2][0] = sigma_liq<double>(T);
+    c[2][1] = -B * tm1 * (mu * (1.0 - bb * tau) - bb * tau) / 647.096;
+    c[2][2] = 0.5 * B * (mu * (mu - 1.0) * tm2 * (1.0 - bb * tau) - 2.0 * bb * mu * tm1) / (647.096 * 647.096);
+    for (int w = 0; w < 3; ++w)
+      for (int q = 0; q < 3; ++q) {
+        tab[((size_t)w * TAB_N + kk) * 3 + q] = c[w][q];
+        tabf[((size_t)w * TAB_N + kk) * 3 + q] = (float)c[w][q];
+      }
+  }
+}
+
 // ---- setup: inflow profile per row and ambient state (Sec. 4.1, Table 2 readings) -------
 __device__ double yv_from_pv(double pv, double p) { return pv * k::RA / (k::RV * (p - pv) + pv * k::RA); }
 
@@ -209,7 +235,7 @@ __global__ void k_mlp_dataset(SrcCase sc, const double* __restrict__ U, int n, f
     for (int f = 0; f < NF; ++f) u14[f] = U[(size_t)m * NF + f];
     Prim<double> w;
     cons_to_prim<double>(u14, w);
-    const Sat<double> st = saturation(w);
+    const Sat<double> st = saturation(w, sc);
     float x[CT_MLP_IN];
     mlp_features<double>(w, st, sc.rp2, x);
     double ext[10];
@@ -331,6 +357,7 @@ static ct_status validate(const ct_case* c, int precision) {
   if (c->geom == 1 && !(c->p_amb > 0.0 && c->T_amb > 0.0)) return fail(CT_ERR_ARG, "ambient p, T must be > 0");
   if (c->n_soot < 0.0 || c->soot_sigma <= 0.0) return fail(CT_ERR_ARG, "soot parameters invalid");
   if (c->viscous != 0 && c->viscous != 1) return fail(CT_ERR_ARG, "viscous must be 0 or 1");
+  if (c->tables != 0 && c->tables != 1) return fail(CT_ERR_ARG, "tables must be 0 or 1");
   if (!(c->nu_t >= 0.0) || c->nu_t > 1.0e3) return fail(CT_ERR_ARG, "nu_t out of range [0, 1e3]");
   return CT_OK;
 }
@@ -346,6 +373,32 @@ static size_t ws_bytes(const ct_case* c) {
   b += align256((size_t)max_rows(c) * sizeof(unsigned int));
   b += align256((size_t)max_rows(c) * NPART * sizeof(double));
   return b;
+}
+
+// The property tables are case-independent: one copy per device in these arrays, built
+// once (synchronously, so that every stream sees them) the first time a case asks for them.
+static __device__ double g_tab[3 * TAB_N * 3];
+static __device__ float g_tabf[3 * TAB_N * 3];
+static std::mutex g_tab_mu;
+static const double* g_tab_ptr[64];
+static const float* g_tabf_ptr[64];
+
+static ct_status property_tables(const double** tab, const float** tabf) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(CT_ERR_CUDA, "device for the tables");
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (!g_tab_ptr[dev]) {
+    void *p = nullptr, *pf = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tab) != cudaSuccess || cudaGetSymbolAddress(&pf, g_tabf) != cudaSuccess)
+      return cuda_check("table symbols");
+    k_tables<<<8, 128>>>((double*)p, (float*)pf);
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_check("k_tables");
+    g_tab_ptr[dev] = (const double*)p;
+    g_tabf_ptr[dev] = (const float*)pf;
+  }
+  *tab = g_tab_ptr[dev];
+  *tabf = g_tabf_ptr[dev];
+  return CT_OK;
 }
 
 static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
@@ -385,6 +438,10 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.sc.rp2 = c->soot_rm * c->soot_rm * std::exp(2.0 * ls * ls);
   d.sc.phase_change = c->phase_change;
   d.sc.freezing = c->freezing;
+  d.sc.tables = c->tables;
+  d.sc.tab = nullptr;
+  d.sc.tabf = nullptr;
+  if (c->tables) property_tables(&d.sc.tab, &d.sc.tabf);
   char* base = (char*)work;
   d.hdr = (WsHeader*)base;
   size_t off = HDR_BYTES;

@@ -84,6 +84,8 @@ __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_cbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double m_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
 
@@ -202,7 +204,51 @@ struct SrcCase {
   double n_soot_ref;   // exit soot number per m^3 (0: no heterogeneous nucleation)
   double rp2;          // lognormal soot <r_p^2> (m^2)
   int phase_change, freezing;
+  int tables;          // water properties from the tables below
+  const double* tab;   // TAB_N x 3 nodes per property (FP64)
+  const float* tabf;   // the same in FP32
 };
+
+// ---- tabulated water properties (Sec. 3.2: tables before the run, second-order Taylor
+// expansion at run time) -----------------------------------------------------------------
+// Properties 0 ln p_sat,l, 1 ln p_sat,i, 2 sigma_lg on nodes T_k = 150 K + 0.5 K k,
+// k < TAB_N (up to 640 K); each node stores the value, the first derivative and half the
+// second derivative of the closed form.  A query expands about the nearest node.
+constexpr int TAB_N = 981;
+template <class R>
+__device__ __forceinline__ R tab_prop(const R* __restrict__ tab, int which, R T, bool der) {
+  int kk = (int)m_floor((T - R(150)) * R(2) + R(0.5));
+  kk = kk < 0 ? 0 : (kk > TAB_N - 1 ? TAB_N - 1 : kk);
+  const R d = T - (R(150) + R(0.5) * R(kk));
+  const R* c = tab + ((size_t)which * TAB_N + kk) * 3;
+  const R c1 = __ldg(c + 1), c2 = __ldg(c + 2);
+  return der ? c1 + R(2) * c2 * d : __ldg(c) + d * (c1 + d * c2);
+}
+__device__ __forceinline__ const double* tab_of(const SrcCase& sc, double) { return sc.tab; }
+__device__ __forceinline__ const float* tab_of(const SrcCase& sc, float) { return sc.tabf; }
+template <class R>
+__device__ __forceinline__ R prop_lnpl(const SrcCase& sc, R T) {
+  return sc.tables ? tab_prop(tab_of(sc, R(0)), 0, T, false) : ln_psat_liq(T);
+}
+template <class R>
+__device__ __forceinline__ R prop_lnpi(const SrcCase& sc, R T) {
+  return sc.tables ? tab_prop(tab_of(sc, R(0)), 1, T, false) : ln_psat_ice(T);
+}
+template <class R>
+__device__ __forceinline__ R prop_sigma(const SrcCase& sc, R T) {
+  return sc.tables ? tab_prop(tab_of(sc, R(0)), 2, T, false) : sigma_liq(T);
+}
+// T_sat of reading D with the tabulated curve and its derivative (same start and steps)
+template <class R, bool ICE>
+__device__ __forceinline__ R prop_tsat(const SrcCase& sc, R lnpv) {
+  if (!sc.tables) return t_sat<R, ICE>(lnpv);
+  const R h0 = ICE ? R(k::HLV0 + k::HSL0) : R(k::HLV0);
+  R T = R(1) / (R(1.0 / k::TREF) - R(k::RV) * (lnpv - R(6.415424237852311)) / h0);
+  const R* tab = tab_of(sc, R(0));
+#pragma unroll
+  for (int it = 0; it < 6; ++it) T -= (tab_prop(tab, ICE ? 1 : 0, T, false) - lnpv) / tab_prop(tab, ICE ? 1 : 0, T, true);
+  return T;
+}
 
 // Young's growth law, Eq. (16), split as G = cond * D: cond = lambda / den (m/s per K) and
 // the driving potential D = Delta T (1 - r_crit/r) (K), with
@@ -348,15 +394,15 @@ __device__ __forceinline__ bool clearly_inactive(const Prim<T>& w) {
 }
 
 template <class T>
-__device__ __forceinline__ Sat<T> saturation(const Prim<T>& w) {
+__device__ __forceinline__ Sat<T> saturation(const Prim<T>& w, const SrcCase& sc) {
   Sat<T> s;
   populations(w, s.pres_l, s.pres_s);
   // Eq. (1) in FP64: ln S = ln p_v - ln p_sat(T)
   double pv = double(w.rho) * double(w.Yv) * k::RV * double(w.Tg);
   pv = pv < 1e-30 ? 1e-30 : pv;
   s.lnpv = m_log(pv);
-  s.lnSl = s.lnpv - ln_psat_liq<double>(double(w.Tg));
-  s.lnSi = s.lnpv - ln_psat_ice<double>(double(w.Tg));
+  s.lnSl = s.lnpv - prop_lnpl<double>(sc, double(w.Tg));
+  s.lnSi = s.lnpv - prop_lnpi<double>(sc, double(w.Tg));
   s.active = s.lnSl > 0.0 || s.pres_l || s.pres_s;
   return s;
 }
@@ -389,7 +435,7 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
   T Tsat_l = T(0);
   bool have_tsat_l = false;
   if (lnSl > 0.0) {
-    const T sig = sigma_liq(Tg);
+    const T sig = prop_sigma<T>(sc, Tg);
     const double sigd = double(sig);
     const double rc = 2.0 * sigd / (k::RHOL * k::RV * double(Tg) * lnSl);
     const double dGkT = k::FOUR_PI_3 * sigd * rc * rc / (k::KB * double(Tg));
@@ -408,7 +454,7 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
       lnJ2[1] = lnJhet + m_log(gate);
     }
     // Eq. (5) with alpha_crit from Young's law at r_crit (reading F)
-    Tsat_l = t_sat<T, false>(lnpv_t);
+    Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
     have_tsat_l = true;
     const T rcT = T(rc);
     const T ih = T(1) / hfg;
@@ -432,14 +478,14 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
 
   // growth at r20, Eqs. (16), (21) -- G in um/s, relaxation rates of reading J
   if (st.pres_l) {
-    if (!have_tsat_l) Tsat_l = t_sat<T, false>(lnpv_t);
+    if (!have_tsat_l) Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
     const T r20 = m_sqrt(w.ml[2] / w.ml[0]) * T(1e-6);
-    const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), sigma_liq(Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
+    const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), prop_sigma<T>(sc, Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
     r.Gl = g.cond * g.D * T(1e6);
     r.xl = T(4.0 * k::PI * k::RHOL * 1e-12) * w.ml[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
   }
   if (st.pres_s) {
-    const T Tsat_i = t_sat<T, true>(lnpv_t);
+    const T Tsat_i = prop_tsat<T, true>(sc, lnpv_t);
     const T r20 = m_sqrt(w.ms[2] / w.ms[0]) * T(1e-6);
     const Growth<T> g = young_growth<T>(r20, Tg, Tsat_i, T(lnSi), T(k::SIGMA_SV), T(k::RHOS), hsg, lam, lbar, gam_g, cp_g);
     r.Gs = g.cond * g.D * T(1e6);
@@ -450,7 +496,7 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
     ext[3] = double(r.Gs);
     ext[4] = double(r.xl);
     ext[5] = double(r.xs);
-    if (!have_tsat_l) Tsat_l = t_sat<T, false>(lnpv_t);
+    if (!have_tsat_l) Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
     ext[9] = double(Tsat_l - Tg);
   }
   return r;
@@ -505,7 +551,7 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
     bool pl, ps;
     if (!populations(w, pl, ps) && clearly_inactive(w)) return false;
   }
-  const Sat<T> st = saturation(w);
+  const Sat<T> st = saturation(w, sc);
   if (aux) { aux[0] = st.lnSl; aux[1] = st.lnSi; aux[4] = st.active ? 1.0 : 0.0; }
   if (!st.active) return false;
   const Rates<T> r = plain_rates<T>(w, st, sc, lnJ2, aux, ext);

@@ -408,7 +408,7 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
     bool pl, ps;
     const bool pops = populations(w, pl, ps);
     if (pops || !clearly_inactive(w)) {
-      st = saturation(w);
+      st = saturation(w, dc.sc);
       if (st.active) {
         mlp_features<T>(w, st, dc.sc.rp2, x);
         bool inside = true;
@@ -433,7 +433,7 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
       Rates<T> r;
       r.Jeff = nuc ? T(__expf(y[0])) : T(0);
       // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
-      r.rc_um = nuc ? T(2.0f * sigma_liq<float>(float(w.Tg)) * 1e6f /
+      r.rc_um = nuc ? T(2.0f * prop_sigma<float>(dc.sc, float(w.Tg)) * 1e6f /
                         (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
                     : T(0);
       r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);

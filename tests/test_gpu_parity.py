@@ -42,6 +42,11 @@ def _viscous(cu, nu_t):
     return dict(c, viscous=1, nu_t=nu_t), uf
 
 
+def _tables(cu):
+    c, uf = cu
+    return dict(c, tables=1), uf
+
+
 # Well-conditioned cases: 100 steps at 1e-9.  The nucleating mixing layers amplify a
 # rounding-level perturbation of the oracle's own input to O(1) within about 50 steps
 # (pinned in test_oracle_solver.py); they are checked by shadowing in
@@ -57,6 +62,9 @@ CASES = {
     "nozzle400_viscous": (lambda: (dict(cases.nozzle_case(nx=400), viscous=1, nu_t=1e-4), None), 100),
     "plume256x64_viscous": (lambda: _viscous(cases.plume_case(nx=256, nr=64), 0.5), 100),
     "closed_box_viscous_2steps": (lambda: _viscous(cases.closed_box_case(), 0.05), 2),
+    # water properties from tables with second-order Taylor interpolation (Sec. 3.2)
+    "freezing96x40_tables": (lambda: _tables(cases.freezing_case()), 100),
+    "nozzle400_tables": (lambda: (dict(cases.nozzle_case(nx=400), tables=1), None), 100),
 }
 
 CHAOTIC = {
@@ -129,6 +137,29 @@ def test_fp64_parity_plume_1024x256_viscous_50_steps(P):
     e = field_rel_err(Ug, Uo)
     assert np.all(e <= TOL), report(e)
     assert np.allclose(dg[:, 0], do[:, 0], rtol=1e-11, atol=0)
+
+
+def test_source_batch_parity_with_tables(P):
+    """Pointwise source with tabulated properties, FP64, against the oracle's tables."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_source import _random_states, _case
+    U = _random_states(2000, seed=12)
+    c = dict(_case(), tables=1)
+    Qo, ao = O.source_batch(c, U, 1e-6)
+    Ud = torch.tensor(U, device="cuda")
+    Q = torch.zeros_like(Ud)
+    aux = torch.zeros((U.shape[0], 11), dtype=torch.float64, device="cuda")
+    P.ct_source_batch(c, P.CT_FP64, Ud, U.shape[0], 1e-6, Q, aux)
+    Qg = Q.cpu().numpy()
+    scale = np.maximum(np.abs(Qo).max(axis=0), 1e-300)
+    rel = np.abs(Qg - Qo) / (np.abs(Qo) + 1e-6 * scale)
+    assert np.max(rel) < 1e-8, np.max(rel)
+    # and the tables move the source only at their interpolation error
+    Qc, _ = O.source_batch(dict(c, tables=0), U, 1e-6)
+    act = np.abs(Qc).max(axis=1) > 0
+    relc = np.abs(Qo - Qc)[act] / (np.abs(Qc)[act] + 1e-6 * scale)
+    assert 0 < np.median(relc) < 1e-4
 
 
 def test_fp32_viscous_against_oracle(P):
