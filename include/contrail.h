@@ -80,6 +80,8 @@ typedef struct {
   double nu_t;                             /* turbulent kinematic viscosity, m^2/s (viscous = 1) */
   int32_t viscous;                         /* 1: viscous and diffusive fluxes, Eqs. (25)-(26) */
   int32_t tables;                          /* 1: water properties from tables, 2nd-order Taylor */
+  int32_t equilibrium;                     /* 1: equilibrium phase change (not with CT_FP32_MLP) */
+  int32_t pad_;                            /* unused, 0 */
 } ct_case;
 
 /* Diagnostics record of the last completed step (CT_NDIAG doubles):

@@ -105,6 +105,8 @@ typedef struct {
   double nu_t;           /* turbulent kinematic viscosity, m^2/s (viscous cases) */
   int32_t viscous;       /* 1: viscous and diffusive fluxes (reading M) */
   int32_t tables;        /* 1: water properties from tables, second-order Taylor (reading N) */
+  int32_t equilibrium;   /* 1: equilibrium phase change instead of the kinetic model (reading O) */
+  int32_t pad_;
 } or_case;
 
 #define NDIAG 32
@@ -319,6 +321,7 @@ typedef struct {
   double rp2;          /* lognormal soot <r_p^2> */
   int phase_change, freezing;
   int tables;          /* reading N */
+  int equilibrium;     /* reading O */
 } src_par_t;
 
 /* ------------------------------------------------------------------------------------
@@ -422,6 +425,57 @@ double or_koop_log10J(double daw) {
 /* A (may be NULL) is the cell's conserved state after the flux-only part of the stage
  * update, U + dt (-div F + S_geo); the limiters of reading J keep A + dt Q non-negative.
  * NULL means the cell's own state (a pointwise evaluation without transport). */
+/* ------------------------------------------------------------------------------------
+ * Equilibrium phase change (Sec. 4.3 compares it with the kinetic model; reading O).
+ * The water of a cell is at thermodynamic equilibrium at the end of every stage: with the
+ * density, velocity, total energy and total water of the flux-updated state fixed, vapour
+ * is in excess of saturation over the condensed phase only if no condensate could take it
+ * up.  The condensate is liquid above T_FRZ = 235.15 K (homogeneous freezing) and ice
+ * below, monodisperse with radius 1 um (the model carries no size); a condensate below
+ * 1e-15 per kg counts as none.  The temperature solves
+ * the energy balance e(T) = Y_a c_va T + Y_v (c_vv T + e0v) + Y_c e_c(T) with
+ * Y_v = p_sat(T) / (rho R_v T) by eight Newton steps from the all-vapour temperature.
+ * ---------------------------------------------------------------------------------- */
+static const double T_FRZ = 235.15;
+static const double Y_MIN_EQ = 1.0e-15;   /* condensate mass fraction taken as none */
+
+/* saturation vapour mass fraction over liquid (ice = 0) or ice (1) and its T derivative */
+static double ysat(const src_par_t *sp, double rho, double T, int ice, double *dydT) {
+  double lnp = ice ? prop_lnpi(sp, T) : prop_lnpl(sp, T);
+  double dlnp = sp->tables ? tab_eval(ice, T, 1) : (ice ? dln_psat_i(T) : dln_psat_l(T));
+  double y = exp(lnp) / (rho * rv_gas() * T);
+  if (dydT) *dydT = y * (dlnp - 1.0 / T);
+  return y;
+}
+
+/* Equilibrium split of total water W at density rho and specific internal energy e:
+ * returns T and sets Y_v, Y_c (condensate) and the phase (0 liquid, 1 ice). */
+static double equilibrium_split(const src_par_t *sp, double rho, double e, double W, double *Yv, double *Yc,
+                                int *ice) {
+  double Ya = 1.0 - W;
+  double Tv = (e - W * e0v()) / (Ya * cva() + W * cvv());   /* all vapour */
+  *ice = Tv < T_FRZ;
+  if (W <= ysat(sp, rho, Tv, *ice, NULL)) { *Yv = W; *Yc = 0.0; return Tv; }
+  for (int pass = 0; pass < 2; ++pass) {
+    int ic = pass == 0 ? 0 : 1;
+    double cc = ic ? CS : CL, ec0 = ic ? e0s() : 0.0;
+    double T = Tv;
+    for (int it = 0; it < 8; ++it) {
+      double dy, y = ysat(sp, rho, T, ic, &dy);
+      double g = Ya * cva() * T + y * (cvv() * T + e0v()) + (W - y) * (cc * T + ec0) - e;
+      double dg = Ya * cva() + y * cvv() + (W - y) * cc + dy * (cvv() * T + e0v() - cc * T - ec0);
+      T -= g / dg;
+    }
+    double y = ysat(sp, rho, T, ic, NULL);
+    if (ic == 1 || T >= T_FRZ) {
+      if (y >= W) { *Yv = W; *Yc = 0.0; *ice = ic; return Tv; }   /* no condensate after all */
+      *Yv = y; *Yc = W - y; *ice = ic;
+      return T;
+    }
+  }
+  return Tv;   /* not reached */
+}
+
 static void phase_source(const prim_t *w, const double *A, double dt, const src_par_t *sp,
                          double *Q, double *aux) {
   for (int f = 0; f < NF; ++f) Q[f] = 0.0;
@@ -430,6 +484,45 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   aux[3] = -INFINITY;
   aux[9] = -INFINITY;
   if (!sp->phase_change) return;
+  if (sp->equilibrium) {
+    /* the equilibrium state of the flux-updated stage state (or of the cell itself) */
+    double X[NF];
+    prim_t x;
+    if (A) {
+      for (int f = 0; f < NF; ++f) X[f] = A[f];
+      cons_to_prim(X, &x);
+    } else {
+      x = *w;
+      prim_to_cons(w->p, w->T, w->u, w->v, w->Yv, w->ml, w->ms, w->ns, X);
+    }
+    double pv0 = x.rho * x.Yv * rv_gas() * x.T;
+    if (pv0 < 1.0e-30) pv0 = 1.0e-30;
+    aux[0] = log(pv0) - prop_lnpl(sp, x.T);
+    aux[1] = log(pv0) - prop_lnpi(sp, x.T);
+    double W = x.Yv + x.Yl + x.Ys;
+    double e = x.cv * x.T + x.ef;
+    double Yv, Yc;
+    int ice;
+    double Teq = equilibrium_split(sp, x.rho, e, W, &Yv, &Yc, &ice);
+    /* condensate below 1e-15 per kg counts as none: the explicit stage leaves rounding
+     * residues where the target is exactly zero */
+    int had = x.Yl + x.Ys > Y_MIN_EQ;
+    int active = Yc > Y_MIN_EQ || had;
+    aux[4] = active ? 1.0 : 0.0;
+    if (!active) return;
+    /* target conserved water fields: monodisperse condensate of radius 1 um */
+    double Xt[NF];
+    for (int f = 0; f < NF; ++f) Xt[f] = X[f];
+    Xt[F_RYV] = x.rho * Yv;
+    double n = Yc / (4.0 / 3.0 * PI * (ice ? RHOS : RHOL) * moment_scale(3));   /* mu_hat, scaled */
+    for (int k = 0; k < 4; ++k) {
+      Xt[F_ML + k] = ice ? 0.0 : x.rho * n;
+      Xt[F_MS + k] = ice ? x.rho * n : 0.0;
+    }
+    for (int f = F_RYV; f <= F_MS + 3; ++f) Q[f] = (Xt[f] - X[f]) / dt;
+    aux[5] = Teq;   /* slot 5 carries the equilibrium temperature in this model */
+    return;
+  }
   const double Rv = rv_gas();
   double T = w->T, rho = w->rho, p = w->p;
 
@@ -822,6 +915,7 @@ or_ctx *or_create(const or_case *c, const double *ufac_rows) {
   g->sp.freezing = c->freezing;
   g->sp.n_soot_ref = c->n_soot;
   g->sp.tables = c->tables;
+  g->sp.equilibrium = c->equilibrium;
   build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   g->sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);   /* lognormal E[r^2] */
@@ -1219,6 +1313,7 @@ void or_source_batch(const or_case *c, const double *U, int n, double dt, double
   sp.freezing = c->freezing;
   sp.n_soot_ref = c->n_soot;
   sp.tables = c->tables;
+  sp.equilibrium = c->equilibrium;
   build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);

@@ -358,6 +358,9 @@ static ct_status validate(const ct_case* c, int precision) {
   if (c->n_soot < 0.0 || c->soot_sigma <= 0.0) return fail(CT_ERR_ARG, "soot parameters invalid");
   if (c->viscous != 0 && c->viscous != 1) return fail(CT_ERR_ARG, "viscous must be 0 or 1");
   if (c->tables != 0 && c->tables != 1) return fail(CT_ERR_ARG, "tables must be 0 or 1");
+  if (c->equilibrium != 0 && c->equilibrium != 1) return fail(CT_ERR_ARG, "equilibrium must be 0 or 1");
+  if (c->equilibrium && precision == CT_FP32_MLP)
+    return fail(CT_ERR_ARG, "the surrogate stands in for the kinetic source: no equilibrium with CT_FP32_MLP");
   if (!(c->nu_t >= 0.0) || c->nu_t > 1.0e3) return fail(CT_ERR_ARG, "nu_t out of range [0, 1e3]");
   return CT_OK;
 }
@@ -439,6 +442,7 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.sc.phase_change = c->phase_change;
   d.sc.freezing = c->freezing;
   d.sc.tables = c->tables;
+  d.sc.equilibrium = c->equilibrium;
   d.sc.tab = nullptr;
   d.sc.tabf = nullptr;
   if (c->tables) property_tables(&d.sc.tab, &d.sc.tabf);

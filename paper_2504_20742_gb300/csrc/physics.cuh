@@ -205,6 +205,7 @@ struct SrcCase {
   double rp2;          // lognormal soot <r_p^2> (m^2)
   int phase_change, freezing;
   int tables;          // water properties from the tables below
+  int equilibrium;     // equilibrium phase change instead of the kinetic model
   const double* tab;   // TAB_N x 3 nodes per property (FP64)
   const float* tabf;   // the same in FP32
 };
@@ -533,6 +534,96 @@ __device__ __forceinline__ void mlp_features(const Prim<T>& w, const Sat<T>& st,
 // the flux-updated state A = U + dt acc non-negative; Q gets fields 4..12.  aux (optional):
 // ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s, Koop log10 J, omega.
 // Returns true for an active cell.
+// ---- equilibrium phase change (the comparison model of Sec. 4.3) ---------------------------
+// The water of the flux-updated stage state is brought to equilibrium with its density,
+// velocity, total energy and total water fixed: vapour above saturation over the condensed
+// phase condenses, condensate below it evaporates.  Liquid above 235.15 K (homogeneous
+// freezing), ice below; monodisperse condensate of radius 1 um.  The temperature solves the
+// energy balance by eight Newton steps from the all-vapour temperature; all in FP64.
+constexpr double T_FRZ = 235.15;
+__device__ __forceinline__ double sat_fraction(const SrcCase& sc, double rho, double T, bool ice, double& dy) {
+  const double lnp = ice ? prop_lnpi<double>(sc, T) : prop_lnpl<double>(sc, T);
+  const double dlnp = sc.tables ? tab_prop(sc.tab, ice ? 1 : 0, T, true)
+                                : (ice ? dln_psat_ice<double>(T) : dln_psat_liq<double>(T));
+  const double y = exp(lnp) / (rho * k::RV * T);
+  dy = y * (dlnp - 1.0 / T);
+  return y;
+}
+// returns the temperature; sets the vapour and condensate fractions and the phase
+static __device__ __noinline__ double equilibrium_split(const SrcCase& sc, double rho, double e, double W, double& Yv,
+                                                 double& Yc, bool& ice) {
+  const double Ya = 1.0 - W;
+  const double Tv = (e - W * k::E0V) / (Ya * k::CVA + W * k::CVV);
+  double dy;
+  ice = Tv < T_FRZ;
+  if (W <= sat_fraction(sc, rho, Tv, ice, dy)) {
+    Yv = W;
+    Yc = 0.0;
+    return Tv;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool ic = pass == 1;
+    const double cc = ic ? k::CS : k::CL, ec = ic ? k::E0S : 0.0;
+    double T = Tv;
+    for (int it = 0; it < 8; ++it) {
+      const double y = sat_fraction(sc, rho, T, ic, dy);
+      const double g = Ya * k::CVA * T + y * (k::CVV * T + k::E0V) + (W - y) * (cc * T + ec) - e;
+      const double dg = Ya * k::CVA + y * k::CVV + (W - y) * cc + dy * (k::CVV * T + k::E0V - cc * T - ec);
+      T -= g / dg;
+    }
+    if (ic || T >= T_FRZ) {
+      const double y = sat_fraction(sc, rho, T, ic, dy);
+      ice = ic;
+      if (y >= W) {
+        Yv = W;
+        Yc = 0.0;
+        return Tv;
+      }
+      Yv = y;
+      Yc = W - y;
+      return T;
+    }
+  }
+  Yv = W;
+  Yc = 0.0;
+  return Tv;
+}
+template <class T>
+__device__ __forceinline__ bool equilibrium_source(const T* U, const T* acc, T dt, const SrcCase& sc, T* Q,
+                                                   double* aux) {
+  double X[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) X[f] = acc ? double(U[f]) + double(dt) * double(acc[f]) : double(U[f]);
+  Prim<double> x;
+  cons_to_prim<double>(X, x);
+  if (aux) {
+    double pv = x.rho * x.Yv * k::RV * x.Tg;
+    pv = pv < 1e-30 ? 1e-30 : pv;
+    aux[0] = log(pv) - prop_lnpl<double>(sc, x.Tg);
+    aux[1] = log(pv) - prop_lnpi<double>(sc, x.Tg);
+  }
+  const double W = x.Yv + x.Yl + x.Ys;
+  const double e = x.cv * x.Tg + x.Yv * k::E0V + x.Ys * k::E0S;
+  double Yv, Yc;
+  bool ice;
+  const double Teq = equilibrium_split(sc, x.rho, e, W, Yv, Yc, ice);
+  // a condensate below 1e-15 per kg counts as none (rounding residues of the explicit stage)
+  const bool had = x.Yl + x.Ys > 1e-15;
+  const bool active = Yc > 1e-15 || had;
+  if (aux) aux[4] = active ? 1.0 : 0.0;
+  if (!active) return false;
+  if (aux) aux[5] = Teq;
+  const double idt = 1.0 / double(dt);
+  const double n = Yc / (ice ? k::YS3 : k::YL3);   // scaled moments of 1 um condensate
+  Q[4] = T((x.rho * Yv - X[4]) * idt);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Q[5 + q] = T(((ice ? 0.0 : x.rho * n) - X[5 + q]) * idt);
+    Q[9 + q] = T(((ice ? x.rho * n : 0.0) - X[9 + q]) * idt);
+  }
+  return true;
+}
+
 template <class T>
 __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
                                              T* Q, double* lnJ2, double* aux, double* ext = nullptr) {
@@ -545,6 +636,7 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
   }
   lnJ2[0] = lnJ2[1] = -INFINITY;
   if (!sc.phase_change) return false;
+  if (sc.equilibrium) return equilibrium_source<T>(U, acc, dt, sc, Q, aux);
   if (!aux && !ext) {
     // the FP32 screen's margin (1e-3 in ln S_l) is far above its rounding error, so a
     // screened cell is inactive in FP64 too: both paths give the same (zero) source

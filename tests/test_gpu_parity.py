@@ -47,6 +47,11 @@ def _tables(cu):
     return dict(c, tables=1), uf
 
 
+def _equilibrium(cu):
+    c, uf = cu
+    return dict(c, equilibrium=1), uf
+
+
 # Well-conditioned cases: 100 steps at 1e-9.  The nucleating mixing layers amplify a
 # rounding-level perturbation of the oracle's own input to O(1) within about 50 steps
 # (pinned in test_oracle_solver.py); they are checked by shadowing in
@@ -65,6 +70,10 @@ CASES = {
     # water properties from tables with second-order Taylor interpolation (Sec. 3.2)
     "freezing96x40_tables": (lambda: _tables(cases.freezing_case()), 100),
     "nozzle400_tables": (lambda: (dict(cases.nozzle_case(nx=400), tables=1), None), 100),
+    # equilibrium phase change (the comparison model of Sec. 4.3)
+    "freezing96x40_equilibrium": (lambda: _equilibrium(cases.freezing_case()), 100),
+    "mixing96x40_equilibrium": (lambda: _equilibrium(cases.mixing_layer_case()), 100),
+    "nozzle400_equilibrium": (lambda: (dict(cases.nozzle_case(nx=400), equilibrium=1), None), 100),
 }
 
 CHAOTIC = {
@@ -160,6 +169,31 @@ def test_source_batch_parity_with_tables(P):
     act = np.abs(Qc).max(axis=1) > 0
     relc = np.abs(Qo - Qc)[act] / (np.abs(Qc)[act] + 1e-6 * scale)
     assert 0 < np.median(relc) < 1e-4
+
+
+def test_source_batch_parity_equilibrium(P):
+    """Pointwise equilibrium adjustment, FP64, against the oracle (random physical states)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_source import _random_states, _case
+    U = _random_states(2000, seed=13)
+    c = dict(_case(), equilibrium=1)
+    Qo, ao = O.source_batch(c, U, 1e-6)
+    Ud = torch.tensor(U, device="cuda")
+    Q = torch.zeros_like(Ud)
+    aux = torch.zeros((U.shape[0], 11), dtype=torch.float64, device="cuda")
+    P.ct_source_batch(c, P.CT_FP64, Ud, U.shape[0], 1e-6, Q, aux)
+    Qg, ag = Q.cpu().numpy(), aux.cpu().numpy()
+    assert np.array_equal(ag[:, 4], ao[:, 4]) and ao[:, 4].sum() > 100
+    scale = np.maximum(np.abs(Qo).max(axis=0), 1e-300)
+    rel = np.abs(Qg - Qo) / (np.abs(Qo) + 1e-6 * scale)
+    assert np.max(rel) < 1e-8, np.max(rel)
+
+
+def test_equilibrium_rejected_with_the_surrogate(P):
+    c, uf = _equilibrium(cases.freezing_case(nx=32, nr=16))
+    with pytest.raises(P.ContrailError):
+        P.Solver(c, uf, precision=P.CT_FP32_MLP)
 
 
 def test_fp32_viscous_against_oracle(P):
