@@ -84,6 +84,21 @@ typedef struct {
   int32_t pad_;                            /* unused, 0 */
 } ct_case;
 
+/* Optional parts of the model, each off by default:
+ *   viscous = 1      viscous and diffusive fluxes (Sec. 3.1 Eqs. (25)-(26), central
+ *                    differences of Sec. 3.2) with effective viscosity mu(T) + rho nu_t,
+ *                    conductivity mu c_p/Pr + rho c_p nu_t/0.9, vapour diffusivity
+ *                    2.11e-5 (T/273.15)^1.94 (101325/p) + nu_t/0.7 and particle diffusivity
+ *                    nu_t/0.7 (m^2/s); walls are adiabatic, impermeable and slip.
+ *   tables = 1       ln p_sat (liquid, ice) and the surface tension from tables every 0.5 K
+ *                    (150-640 K) with a second-order Taylor expansion about the nearest node
+ *                    (Sec. 3.2).  The tables are built once per device on the first call
+ *                    that needs them, which synchronises the device: make that call before
+ *                    any stream capture.
+ *   equilibrium = 1  equilibrium phase change instead of the kinetic model (the comparison
+ *                    of Sec. 4.3): every stage leaves each cell's water at saturation over
+ *                    its condensate (liquid above 235.15 K, ice below, 1 um monodisperse). */
+
 /* Diagnostics record of the last completed step (CT_NDIAG doubles):
  *   0 dt of the step, 1 total mass, 2 total water (vapour + liquid + ice), 3 total energy
  *   (volume integrals per radian for geom 1, per unit throat area for geom 0),
@@ -138,7 +153,9 @@ ct_status ct_diagnostics(const void *work, double *host_out, int nout, void *str
 /* Per-cell derived quantity of state U into out (device, N doubles): which =
  * 0 T, 1 p, 2 ln S_l, 3 ln S_i, 4 log10 J_hom, 5 log10 J_het,eff, 6 active flag,
  * 7 r_crit, 8 Kantrowitz phi, 9 G_l(r20), 10 G_s(r20), 11 Koop log10 J_s (cm^-3 s^-1),
- * 12 per-droplet freezing rate omega.  Non-applicable values are -inf (logs) or 0.
+ * 12 per-droplet freezing rate omega, 13/14 median radius (um) and geometric standard
+ * deviation of the lognormal liquid spectrum with the cell's mu0, mu1, mu2 (the droplet
+ * spectra of Sec. 4.3), 15/16 the same for ice.  Non-applicable values are -inf (logs) or 0.
  * dt enters only the limiters. */
 ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, double dt,
                      double *out, void *stream);

@@ -19,6 +19,10 @@
  * OpenMP (if enabled) only splits independent per-cell/per-face loops over rows;
  * reductions are serial, so results do not depend on the thread count.
  *
+ * Bimodal liquid (Sec. 2.2: two independent liquid moment sets, one per nucleation
+ * mechanism; reading P): droplets of homogeneous origin keep fields 5..8, droplets of
+ * heterogeneous (soot-activated) origin get four more fields 14..17.
+ *
  * Parity pins: see tests/test_oracle_*.py.  Parity unpinned (no independent reference
  * available): the Koop (2000) freezing polynomial coefficients, the alpha_crit reading of
  * the Kantrowitz factor, and everything that needs the paper's REFPROP/IAPWS-95 backend.
@@ -34,8 +38,13 @@
  *   0 rho, 1 rho*u, 2 rho*v, 3 rho*E, 4 rho*Y_v,
  *   5..8  rho*mu_k(liquid)/(1 um)^k, 9..12 rho*mu_k(ice)/(1 um)^k, 13 rho*n_soot.
  * Moments mu_k are specific (per kg of mixture), Eq. (26) transports rho*mu_k.
+ * Bimodal cases append 14..17 rho*mu_k of the liquid of heterogeneous origin (reading P),
+ * NF_BI = 18 fields; fields 5..8 then hold the liquid of homogeneous origin.
  * ---------------------------------------------------------------------------------- */
 #define NF 14
+#define NF_BI 18
+#define NFMAX 18
+#define F_MH 14
 #define F_RHO 0
 #define F_RU 1
 #define F_RV 2
@@ -106,7 +115,7 @@ typedef struct {
   int32_t viscous;       /* 1: viscous and diffusive fluxes (reading M) */
   int32_t tables;        /* 1: water properties from tables, second-order Taylor (reading N) */
   int32_t equilibrium;   /* 1: equilibrium phase change instead of the kinetic model (reading O) */
-  int32_t pad_;
+  int32_t bimodal;       /* 1: two liquid moment sets, by nucleation mechanism (reading P) */
 } or_case;
 
 #define NDIAG 32
@@ -114,7 +123,8 @@ typedef struct {
  * 0 dt, 1 total mass, 2 total water, 3 total energy (all after the step),
  * 4 boundary mass inflow over the step, 5 boundary water inflow, 6 boundary energy inflow,
  * 7 number of active cells in stage 2, 8 non-finite count,
- * 9..22 max-norm residual max |U^{n+1}-U^n|/dt per field, 23 max log10 J_hom over cells,
+ * 9..22 max-norm residual max |U^{n+1}-U^n|/dt per field (bimodal: the heterogeneous
+ * liquid's fields 14..17 share the slots of fields 5..8, max of both), 23 max log10 J_hom over cells,
  * 24 max log10 J_het. */
 
 /* ------------------------------------------------------------------------------------
@@ -174,6 +184,8 @@ typedef struct {
   double rho, u, v, p, T;
   double Yv, Yl, Ys, Ya;
   double ml[4], ms[4];      /* specific moments, scaled by (1 um)^k */
+  double mh[4];             /* bimodal: liquid of heterogeneous origin (0 otherwise) */
+  int bi;                   /* bimodal state (18 fields) */
   double ns;                /* soot number per kg */
   double cv, Rg, gam, ef, c2;
 } prim_t;
@@ -184,18 +196,22 @@ static double moment_scale(int k) {   /* (1 um)^k */
   return s;
 }
 
-static void cons_to_prim(const double *u14, prim_t *w) {
+/* bi: the state has the 18 fields of the bimodal liquid (reading P) */
+static void cons_to_prim(const double *u14, int bi, prim_t *w) {
   double rho = u14[F_RHO];
   w->rho = rho;
   w->u = u14[F_RU] / rho;
   w->v = u14[F_RV] / rho;
   w->Yv = u14[F_RYV] / rho;
+  w->bi = bi;
   for (int k = 0; k < 4; ++k) {
     w->ml[k] = u14[F_ML + k] / rho;
     w->ms[k] = u14[F_MS + k] / rho;
+    w->mh[k] = bi ? u14[F_MH + k] / rho : 0.0;
   }
   w->ns = u14[F_NS] / rho;
-  w->Yl = 4.0 / 3.0 * PI * RHOL * w->ml[3] * moment_scale(3);
+  /* liquid water of both sets */
+  w->Yl = 4.0 / 3.0 * PI * RHOL * (bi ? w->ml[3] + w->mh[3] : w->ml[3]) * moment_scale(3);
   w->Ys = 4.0 / 3.0 * PI * RHOS * w->ms[3] * moment_scale(3);
   w->Ya = 1.0 - w->Yv - w->Yl - w->Ys;
   double e = u14[F_RE] / rho - 0.5 * (w->u * w->u + w->v * w->v);
@@ -251,9 +267,9 @@ double or_dv_mol(double T, double p) { return DV0 * pow(T / 273.15, 1.94) * (101
 typedef struct { double rho, u, v, p, T, Yv, Yl, Ys, Ya, cp; } tcell_t;
 
 /* transport state of a cell from its primitive vector (layout of prim_vec) */
-static void tcell(const double *q, tcell_t *t) {
+static void tcell(const double *q, int bi, tcell_t *t) {
   t->rho = q[0]; t->u = q[1]; t->v = q[2]; t->p = q[3]; t->Yv = q[4];
-  t->Yl = 4.0 / 3.0 * PI * RHOL * q[8] * moment_scale(3);
+  t->Yl = 4.0 / 3.0 * PI * RHOL * (bi ? q[8] + q[17] : q[8]) * moment_scale(3);
   t->Ys = 4.0 / 3.0 * PI * RHOS * q[12] * moment_scale(3);
   t->Ya = 1.0 - t->Yv - t->Yl - t->Ys;
   double Rg = t->Ya * RA + t->Yv * rv_gas();
@@ -272,11 +288,13 @@ static void transport_coeff(double rho, double T, double p, double cp, double nu
 }
 
 /* Face flux G (along +n) between the cell on the minus side (qa) and on the plus side (qb),
- * centres h apart.  The face's total flux is the Roe flux minus G. */
-void or_diffusive_flux(const double *qa, const double *qb, double h, double nu_t, double *G) {
+ * centres h apart, nf fields (14, or 18 for the bimodal liquid).  The face's total flux is
+ * the Roe flux minus G. */
+static void diffusive_flux(const double *qa, const double *qb, double h, double nu_t, int nf, double *G) {
   tcell_t a, b;
-  tcell(qa, &a);
-  tcell(qb, &b);
+  int bi = nf == NF_BI;
+  tcell(qa, bi, &a);
+  tcell(qb, bi, &b);
   double rho = 0.5 * (a.rho + b.rho), T = 0.5 * (a.T + b.T), p = 0.5 * (a.p + b.p), cp = 0.5 * (a.cp + b.cp);
   double mu_e, lam_e, Dv, Dp;
   transport_coeff(rho, T, p, cp, nu_t, &mu_e, &lam_e, &Dv, &Dp);
@@ -284,15 +302,21 @@ void or_diffusive_flux(const double *qa, const double *qb, double h, double nu_t
   G[F_RU] = mu_e * (b.u - a.u) / h;
   G[F_RV] = mu_e * (b.v - a.v) / h;
   G[F_RYV] = rho * Dv * (qb[4] - qa[4]) / h;
-  for (int f = 5; f < NF; ++f) G[f] = rho * Dp * (qb[f] - qa[f]) / h;
+  for (int f = 5; f < nf; ++f) G[f] = rho * Dp * (qb[f] - qa[f]) / h;
   /* mass fluxes of liquid and ice water, against which dry air diffuses back */
-  double Gl = 4.0 / 3.0 * PI * RHOL * G[F_ML + 3] * moment_scale(3);
+  double Gl = 4.0 / 3.0 * PI * RHOL * (bi ? G[F_ML + 3] + G[F_MH + 3] : G[F_ML + 3]) * moment_scale(3);
   double Gs = 4.0 / 3.0 * PI * RHOS * G[F_MS + 3] * moment_scale(3);
   double hva = (CPV - cpa()) * T + e0v();   /* h_v - h_a */
   double hla = (CL - cpa()) * T;            /* h_l - h_a */
   double hsa = (CS - cpa()) * T + e0s();    /* h_s - h_a */
   double ka = 0.5 * (a.u * a.u + a.v * a.v), kb = 0.5 * (b.u * b.u + b.v * b.v);
   G[F_RE] = lam_e * (b.T - a.T) / h + mu_e * (kb - ka) / h + hva * G[F_RYV] + hla * Gl + hsa * Gs;
+}
+void or_diffusive_flux(const double *qa, const double *qb, double h, double nu_t, double *G) {
+  diffusive_flux(qa, qb, h, nu_t, NF, G);
+}
+void or_diffusive_flux_n(const double *qa, const double *qb, double h, double nu_t, int nf, double *G) {
+  diffusive_flux(qa, qb, h, nu_t, nf, G);
 }
 
 /* viscous rate of a cell for the time step: 2 nu_max (1/dx^2 + 1/dr^2), and its mu_e */
@@ -322,6 +346,7 @@ typedef struct {
   int phase_change, freezing;
   int tables;          /* reading N */
   int equilibrium;     /* reading O */
+  int bimodal;         /* reading P */
 } src_par_t;
 
 /* ------------------------------------------------------------------------------------
@@ -478,19 +503,21 @@ static double equilibrium_split(const src_par_t *sp, double rho, double e, doubl
 
 static void phase_source(const prim_t *w, const double *A, double dt, const src_par_t *sp,
                          double *Q, double *aux) {
-  for (int f = 0; f < NF; ++f) Q[f] = 0.0;
+  for (int f = 0; f < (sp->bimodal ? NF_BI : NF); ++f) Q[f] = 0.0;
   for (int a = 0; a < 11; ++a) aux[a] = 0.0;
   aux[2] = -INFINITY;
   aux[3] = -INFINITY;
   aux[9] = -INFINITY;
   if (!sp->phase_change) return;
   if (sp->equilibrium) {
-    /* the equilibrium state of the flux-updated stage state (or of the cell itself) */
+    /* the equilibrium state of the flux-updated stage state (or of the cell itself); the
+     * model carries one condensate population, so it is not combined with the bimodal
+     * liquid */
     double X[NF];
     prim_t x;
     if (A) {
       for (int f = 0; f < NF; ++f) X[f] = A[f];
-      cons_to_prim(X, &x);
+      cons_to_prim(X, 0, &x);
     } else {
       x = *w;
       prim_to_cons(w->p, w->T, w->u, w->v, w->Yv, w->ml, w->ms, w->ns, X);
@@ -536,17 +563,20 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   aux[0] = lnSl;
   aux[1] = lnSi;
 
-  /* moments in SI units */
-  double ml[4], ms[4];
+  /* moments in SI units; mh: the liquid of heterogeneous origin (bimodal, reading P) */
+  const int bi = sp->bimodal;
+  double ml[4], ms[4], mh[4];
   for (int k = 0; k < 4; ++k) {
     ml[k] = w->ml[k] * moment_scale(k);
     ms[k] = w->ms[k] * moment_scale(k);
+    mh[k] = bi ? w->mh[k] * moment_scale(k) : 0.0;
   }
   int present_l = ml[0] > MU_MIN && ml[1] > 0.0 && ml[2] > 0.0 && ml[3] > 0.0;
   int present_s = ms[0] > MU_MIN && ms[1] > 0.0 && ms[2] > 0.0 && ms[3] > 0.0;
+  int present_h = bi && mh[0] > MU_MIN && mh[1] > 0.0 && mh[2] > 0.0 && mh[3] > 0.0;
   /* Active-cell test: nucleation needs S_l > 1 (Eq. (3) has no real r_crit otherwise),
    * growth and freezing need a population; anything else gives an exactly zero source. */
-  int active = lnSl > 0.0 || present_l || present_s;
+  int active = lnSl > 0.0 || present_l || present_s || present_h;
   aux[4] = active ? 1.0 : 0.0;
   if (!active) return;
 
@@ -561,8 +591,10 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   double lbar = 1.5 * mu_g * sqrt(Rg * T) / p;
   double hfg = or_hfg(T), hsg = or_hsg(T);
 
-  /* Nucleation, Eqs. (3)-(6), (9)-(11); J_het gated by the soot number (reading F). */
-  double Jeff = 0.0, rc = 0.0;
+  /* Nucleation, Eqs. (3)-(6), (9)-(11); J_het gated by the soot number (reading F).
+   * One liquid set takes both rates; the bimodal liquid takes the homogeneous rate into
+   * the first set and the heterogeneous rate into the second (reading P). */
+  double Jeff = 0.0, Jeff_h = 0.0, rc = 0.0;
   if (lnSl > 0.0) {
     double sig = prop_sigma(sp, T);
     rc = 2.0 * sig / (RHOL * Rv * T * lnSl);
@@ -588,16 +620,26 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
     double phi = QC * rhov / alpha_c * sqrt(Rv * T / (2.0 * PI)) *
                  (hfg * hfg / (Rv * T * T) - hfg / T);
     aux[6] = phi;
-    Jeff = (Jhom + Jhet) / (1.0 + phi);
+    if (bi) {
+      Jeff = Jhom / (1.0 + phi);
+      Jeff_h = Jhet / (1.0 + phi);
+    } else {
+      Jeff = (Jhom + Jhet) / (1.0 + phi);
+    }
   }
   aux[5] = rc;
 
-  /* Growth, Eq. (16) at r20 = sqrt(mu2/mu0), Eq. (21). */
-  double Gl = 0.0, Gs = 0.0;
+  /* Growth, Eq. (16) at r20 = sqrt(mu2/mu0) of each population, Eq. (21). */
+  double Gl = 0.0, Gs = 0.0, Gh = 0.0;
   if (present_l) {
     double r20 = sqrt(ml[2] / ml[0]);
     double Tsat = prop_tsat(sp, pv, 0);
     Gl = or_growth(r20, T, Tsat, lnSl, prop_sigma(sp, T), RHOL, hfg, lam_g, lbar, gam_g, cp_g);
+  }
+  if (present_h) {
+    double r20 = sqrt(mh[2] / mh[0]);
+    double Tsat = prop_tsat(sp, pv, 0);
+    Gh = or_growth(r20, T, Tsat, lnSl, prop_sigma(sp, T), RHOL, hfg, lam_g, lbar, gam_g, cp_g);
   }
   if (present_s) {
     double r20 = sqrt(ms[2] / ms[0]);
@@ -609,16 +651,18 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
    * 1/tau = 4 pi rho_d mu2 (lambda/den) |dD/dY|, with dD/dY from the linearised saturation
    * curve and the latent heat of reading E.  Over a stage of length dt the exchanged mass
    * follows the exact exponential solution, i.e. G is scaled by (1 - exp(-x))/x with
-   * x = dt/tau (both phases together), so that no stage overshoots the equilibrium. */
+   * x = dt/tau (all populations together), so that no stage overshoots the equilibrium. */
   double xsum = 0.0;
-  if (present_l) {
-    double r20 = sqrt(ml[2] / ml[0]);
+  for (int set = 0; set < 2; ++set) {
+    const double *m = set == 0 ? ml : mh;
+    if (!(set == 0 ? present_l : present_h)) continue;
+    double r20 = sqrt(m[2] / m[0]);
     double Tsat = prop_tsat(sp, pv, 0);
     double nu = young_nu(Tsat, hfg, gam_g, cp_g);
     double Kn = lbar / (2.0 * r20);
     double cond = lam_g / (RHOL * hfg * r20 * (1.0 / (1.0 + 2.0 * YOUNG_BETA * Kn) + 3.78 * (1.0 - nu) * Kn / PR));
     double dD = Rv * Tsat * Tsat / hfg / w->Yv + (1.0 - Rv * Tsat * Tsat / (hfg * T)) * (hfg - Rv * T) / w->cv;
-    xsum += dt * 4.0 * PI * RHOL * ml[2] * cond * fabs(dD);
+    xsum += dt * 4.0 * PI * RHOL * m[2] * cond * fabs(dD);
   }
   if (present_s) {
     double r20 = sqrt(ms[2] / ms[0]);
@@ -632,58 +676,76 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   if (xsum > 0.0) {
     double theta = -expm1(-xsum) / xsum;
     Gl *= theta;
+    Gh *= theta;
     Gs *= theta;
   }
   aux[7] = Gl;
   aux[8] = Gs;
 
-  /* Freezing, Eqs. (12)-(15) (reading H): per-droplet rate omega, frozen number rate. */
-  double Nf = 0.0, rv = 0.0, rf = 0.0;
-  if (sp->freezing && present_l && T < TREF) {
-    rv = cbrt(ml[3] / ml[0]);
+  /* Freezing, Eqs. (12)-(15) (reading H): per-droplet rate omega, frozen number rate, for
+   * each liquid population.  Immersion freezing needs a soot particle inside the droplet:
+   * one set holds a fraction chi = min(1, n_soot/mu0) of such droplets; in the bimodal
+   * liquid only the droplets of heterogeneous origin do (chi = min(1, n_soot/mu0_het)),
+   * those of homogeneous origin none (reading P). */
+  double Nf[2] = {0.0, 0.0}, rv[2] = {0.0, 0.0}, rf[2] = {0.0, 0.0};
+  if (sp->freezing && (present_l || present_h) && T < TREF) {
     double daw = 1.0 - exp(lnpsi - lnpsl);   /* a_w = 1, a_w^ice = p_sat,i / p_sat,l */
     double l10 = or_koop_log10J(daw);
     aux[9] = l10;
     double Js = isinf(l10) ? 0.0 : pow(10.0, l10) * 1.0e6;   /* m^-3 s^-1 */
-    double chi = w->ns / ml[0];
-    if (chi > 1.0) chi = 1.0;
-    double omega = Js * (4.0 / 3.0 * PI * rv * rv * rv) + K_IMM * NS_SITE * 4.0 * PI * sp->rp2 * chi;
-    aux[10] = omega;
-    /* freezing over the stage as exact first-order decay of the droplet number (reading J) */
-    Nf = ml[0] * (-expm1(-omega * dt) / dt);
-    rf = rv * cbrt(RHOL / RHOS);
+    for (int set = 0; set < 2; ++set) {
+      const double *m = set == 0 ? ml : mh;
+      if (!(set == 0 ? present_l : present_h)) continue;
+      rv[set] = cbrt(m[3] / m[0]);
+      double chi = 0.0;
+      if (!bi || set == 1) {
+        chi = w->ns / m[0];
+        if (chi > 1.0) chi = 1.0;
+      }
+      double omega = Js * (4.0 / 3.0 * PI * rv[set] * rv[set] * rv[set]) + K_IMM * NS_SITE * 4.0 * PI * sp->rp2 * chi;
+      if (set == 0) aux[10] = omega;
+      /* freezing over the stage as exact first-order decay of the droplet number (reading J) */
+      Nf[set] = m[0] * (-expm1(-omega * dt) / dt);
+      rf[set] = rv[set] * cbrt(RHOL / RHOS);
+    }
   }
 
   /* Moment sources, Eq. (21) (liquid nucleates at r_crit, ice at the frozen droplet's
    * radius, Sec. 2.2 moments), per kg of mixture, SI units. */
-  double dml[4], dms[4];
+  double dml[4], dms[4], dmh[4];
   for (int k = 0; k < 4; ++k) {
     double gl = k > 0 ? k * ml[k - 1] * Gl : 0.0;
     double gs = k > 0 ? k * ms[k - 1] * Gs : 0.0;
-    dml[k] = gl + Jeff / rho * pow(rc, (double)k) - Nf * pow(rv, (double)k);
-    dms[k] = gs + Nf * pow(rf, (double)k);
+    double gh = k > 0 ? k * mh[k - 1] * Gh : 0.0;
+    dml[k] = gl + Jeff / rho * pow(rc, (double)k) - Nf[0] * pow(rv[0], (double)k);
+    dmh[k] = bi ? gh + Jeff_h / rho * pow(rc, (double)k) - Nf[1] * pow(rv[1], (double)k) : 0.0;
+    dms[k] = bi ? gs + Nf[0] * pow(rf[0], (double)k) + Nf[1] * pow(rf[1], (double)k) : gs + Nf[0] * pow(rf[0], (double)k);
   }
-  /* Limiters (reading J) act on the stage update of the cell: al, as_ and av are the
-   * specific liquid / ice moments and vapour fraction after the flux-only update. */
-  double al[4], as_[4], av;
+  /* Limiters (reading J) act on the stage update of the cell: al, ah, as_ and av are the
+   * specific moments of the liquid sets and the ice and the vapour fraction after the
+   * flux-only update. */
+  double al[4], ah[4], as_[4], av;
   if (A) {
     for (int k = 0; k < 4; ++k) {
       al[k] = A[F_ML + k] / rho * moment_scale(k);
       as_[k] = A[F_MS + k] / rho * moment_scale(k);
+      ah[k] = bi ? A[F_MH + k] / rho * moment_scale(k) : 0.0;
     }
     av = A[F_RYV] / rho;
   } else {
-    for (int k = 0; k < 4; ++k) { al[k] = ml[k]; as_[k] = ms[k]; }
+    for (int k = 0; k < 4; ++k) { al[k] = ml[k]; as_[k] = ms[k]; ah[k] = mh[k]; }
     av = w->Yv;
   }
-  /* Complete evaporation / sublimation: a phase whose mass would not stay positive is
+  /* Complete evaporation / sublimation: a population whose mass would not stay positive is
    * removed entirely within the stage. */
   if (al[3] + dt * dml[3] <= 0.0)
     for (int k = 0; k < 4; ++k) dml[k] = -al[k] / dt;
+  if (bi && ah[3] + dt * dmh[3] <= 0.0)
+    for (int k = 0; k < 4; ++k) dmh[k] = -ah[k] / dt;
   if (as_[3] + dt * dms[3] <= 0.0)
     for (int k = 0; k < 4; ++k) dms[k] = -as_[k] / dt;
   /* Mass exchange, Eqs. (18), (25): the vapour sink is the condensed gain negated. */
-  double dYl = 4.0 / 3.0 * PI * RHOL * dml[3];
+  double dYl = 4.0 / 3.0 * PI * RHOL * (bi ? dml[3] + dmh[3] : dml[3]);
   double dYs = 4.0 / 3.0 * PI * RHOS * dms[3];
   double dYv = -(dYl + dYs);
   /* Vapour positivity: condensation is scaled down so that the vapour stays >= 0. */
@@ -691,6 +753,7 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
     double th = av > 0.0 ? av / (-dt * dYv) : 0.0;
     for (int k = 0; k < 4; ++k) {
       dml[k] *= th;
+      dmh[k] *= th;
       dms[k] *= th;
     }
     dYv *= th;
@@ -699,18 +762,22 @@ static void phase_source(const prim_t *w, const double *A, double dt, const src_
   for (int k = 0; k < 4; ++k) {
     Q[F_ML + k] = rho * dml[k] / moment_scale(k);
     Q[F_MS + k] = rho * dms[k] / moment_scale(k);
+    if (bi) Q[F_MH + k] = rho * dmh[k] / moment_scale(k);
   }
 }
 
 /* ------------------------------------------------------------------------------------
  * Convective flux: MUSCL/van Leer on primitives + Roe with Harten fix (Sec. 3.2,
  * reading K).  dir = 0: normal velocity u, dir = 1: normal velocity v.
- * Face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns.
+ * Face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns
+ * (bimodal: 14..17 mh).
  * ---------------------------------------------------------------------------------- */
 static void prim_vec(const prim_t *w, double *q) {
   q[0] = w->rho; q[1] = w->u; q[2] = w->v; q[3] = w->p; q[4] = w->Yv;
   for (int k = 0; k < 4; ++k) { q[5 + k] = w->ml[k]; q[9 + k] = w->ms[k]; }
   q[13] = w->ns;
+  if (w->bi)
+    for (int k = 0; k < 4; ++k) q[14 + k] = w->mh[k];
 }
 
 /* van Leer limited slope: psi(r) * (q_i - q_{i-1}) with psi(r) = (r+|r|)/(1+|r|),
@@ -722,9 +789,9 @@ static double vl_slope(double dm, double dp) {
 
 typedef struct { double rho, u, v, p, Yv, Yl, Ys, Ya, cv, Rg, gam, ef, H, c2; } face_t;
 
-static void face_state(const double *q, face_t *s) {
+static void face_state(const double *q, int bi, face_t *s) {
   s->rho = q[0]; s->u = q[1]; s->v = q[2]; s->p = q[3]; s->Yv = q[4];
-  s->Yl = 4.0 / 3.0 * PI * RHOL * q[8] * moment_scale(3);
+  s->Yl = 4.0 / 3.0 * PI * RHOL * (bi ? q[8] + q[17] : q[8]) * moment_scale(3);
   s->Ys = 4.0 / 3.0 * PI * RHOS * q[12] * moment_scale(3);
   s->Ya = 1.0 - s->Yv - s->Yl - s->Ys;
   s->cv = s->Ya * cva() + s->Yv * cvv() + s->Yl * CL + s->Ys * CS;
@@ -737,11 +804,12 @@ static void face_state(const double *q, face_t *s) {
   s->c2 = s->gam * s->p / s->rho;
 }
 
-/* Roe flux between reconstructed primitive vectors qL, qR; F gets 14 components. */
-void or_roe_flux(const double *qL, const double *qR, int dir, double *F) {
+/* Roe flux between reconstructed primitive vectors qL, qR of nf fields (14, or 18 for the
+ * bimodal liquid); F gets nf components. */
+static void roe_flux(const double *qL, const double *qR, int dir, int nf, double *F) {
   face_t L, R;
-  face_state(qL, &L);
-  face_state(qR, &R);
+  face_state(qL, nf == NF_BI, &L);
+  face_state(qR, nf == NF_BI, &R);
   double unL = dir == 0 ? L.u : L.v, utL = dir == 0 ? L.v : L.u;
   double unR = dir == 0 ? R.u : R.v, utR = dir == 0 ? R.v : R.u;
   /* physical fluxes in (rho, rho u_n, rho u_t, rho E) */
@@ -791,24 +859,28 @@ void or_roe_flux(const double *qL, const double *qR, int dir, double *F) {
     F[F_MS + k] = Fc[0] * qu[9 + k];
   }
   F[F_NS] = Fc[0] * qu[13];
+  for (int f = NF; f < nf; ++f) F[f] = Fc[0] * qu[f];
 }
+void or_roe_flux(const double *qL, const double *qR, int dir, double *F) { roe_flux(qL, qR, dir, NF, F); }
+void or_roe_flux_n(const double *qL, const double *qR, int dir, int nf, double *F) { roe_flux(qL, qR, dir, nf, F); }
 
 /* ------------------------------------------------------------------------------------
  * Solver context: padded grids with two ghost layers per side.
  * ---------------------------------------------------------------------------------- */
 typedef struct {
   or_case c;
+  int nf;                     /* fields of the state: 14, or 18 with the bimodal liquid */
   int nx, nr, nxp, nrp;       /* padded sizes */
   double dx, dr;
   src_par_t sp;
-  double *inflow;             /* nr x NF conserved inflow states (plume) */
-  double amb[NF];             /* ambient conserved state (plume far field) */
-  double *Up;                 /* padded conserved state, NF x nrp x nxp */
-  double *Wp;                 /* padded primitive vectors, NF x nrp x nxp */
-  double *Fx;                 /* x-face fluxes, NF x nr x (nx+1) */
-  double *Fr;                 /* r-face fluxes, NF x (nr+1) x nx */
-  double *L;                  /* residual, NF x N */
-  double *U0, *U1;            /* stage states, NF x N */
+  double *inflow;             /* nr x nf conserved inflow states (plume) */
+  double amb[NFMAX];          /* ambient conserved state (plume far field) */
+  double *Up;                 /* padded conserved state, nf x nrp x nxp */
+  double *Wp;                 /* padded primitive vectors, nf x nrp x nxp */
+  double *Fx;                 /* x-face fluxes, nf x nr x (nx+1) */
+  double *Fr;                 /* r-face fluxes, nf x (nr+1) x nx */
+  double *L;                  /* residual, nf x N */
+  double *U0, *U1;            /* stage states, nf x N */
   double *aux;                /* per-cell aux (11 values) of the last source evaluation */
   double bflux[3];            /* boundary inflow rates (mass, water, energy) */
   int active_count;
@@ -893,6 +965,8 @@ static void q1d_inlet_state(const or_case *c, double u, double *u14) {
 or_ctx *or_create(const or_case *c, const double *ufac_rows) {
   or_ctx *g = (or_ctx *)calloc(1, sizeof(or_ctx));
   g->c = *c;
+  g->nf = c->bimodal ? NF_BI : NF;
+  const int nf = g->nf;
   g->nx = c->nx;
   g->nr = c->geom == 0 ? 1 : c->nr;
   g->c.nr = g->nr;
@@ -902,26 +976,27 @@ or_ctx *or_create(const or_case *c, const double *ufac_rows) {
   g->dr = c->geom == 0 ? 1.0 : c->lr / g->nr;
   size_t N = (size_t)g->nx * g->nr;
   size_t NP = (size_t)g->nxp * g->nrp;
-  g->Up = (double *)calloc(NF * NP, sizeof(double));
-  g->Wp = (double *)calloc(NF * NP, sizeof(double));
-  g->Fx = (double *)calloc(NF * (size_t)g->nr * (g->nx + 1), sizeof(double));
-  g->Fr = (double *)calloc(NF * (size_t)(g->nr + 1) * g->nx, sizeof(double));
-  g->L = (double *)calloc(NF * N, sizeof(double));
-  g->U0 = (double *)calloc(NF * N, sizeof(double));
-  g->U1 = (double *)calloc(NF * N, sizeof(double));
+  g->Up = (double *)calloc(nf * NP, sizeof(double));
+  g->Wp = (double *)calloc(nf * NP, sizeof(double));
+  g->Fx = (double *)calloc(nf * (size_t)g->nr * (g->nx + 1), sizeof(double));
+  g->Fr = (double *)calloc(nf * (size_t)(g->nr + 1) * g->nx, sizeof(double));
+  g->L = (double *)calloc(nf * N, sizeof(double));
+  g->U0 = (double *)calloc(nf * N, sizeof(double));
+  g->U1 = (double *)calloc(nf * N, sizeof(double));
   g->aux = (double *)calloc(11 * N, sizeof(double));
-  g->inflow = (double *)calloc(NF * (size_t)g->nr, sizeof(double));
+  g->inflow = (double *)calloc(nf * (size_t)g->nr, sizeof(double));
   g->sp.phase_change = c->phase_change;
   g->sp.freezing = c->freezing;
   g->sp.n_soot_ref = c->n_soot;
   g->sp.tables = c->tables;
   g->sp.equilibrium = c->equilibrium;
+  g->sp.bimodal = c->bimodal;
   build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   g->sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);   /* lognormal E[r^2] */
   if (c->geom == 1) {
     for (int j = 0; j < g->nr; ++j)
-      inflow_state(c, r_center(g, j), ufac_rows ? ufac_rows[j] : 1.0, g->inflow + (size_t)j * NF);
+      inflow_state(c, r_center(g, j), ufac_rows ? ufac_rows[j] : 1.0, g->inflow + (size_t)j * nf);
     ambient_state(c, 1.0, g->amb);
   }
   return g;
@@ -952,10 +1027,11 @@ static double mach_from_area(double ar, double gam, int supersonic) {
  * the optional seed populations in the core; nozzle = isentropic area-Mach solution. */
 void or_init_state(or_ctx *g, double *U) {
   const or_case *c = &g->c;
+  const int nf = g->nf;
   size_t N = (size_t)g->nx * g->nr;
   for (int j = 0; j < g->nr; ++j) {
     for (int i = 0; i < g->nx; ++i) {
-      double u14[NF];
+      double u14[NFMAX] = {0};   /* a bimodal state starts without heterogeneous liquid */
       if (c->geom == 0) {
         double zero[4] = {0, 0, 0, 0};
         double Yv = c->Yv_inlet;
@@ -967,10 +1043,10 @@ void or_init_state(or_ctx *g, double *U) {
         double p = c->p0 * pow(T / c->T0, gam / (gam - 1.0));
         prim_to_cons(p, T, M * sqrt(gam * Rg * T), 0.0, Yv, zero, zero, 0.0, u14);
       } else {
-        memcpy(u14, g->inflow + (size_t)j * NF, sizeof(u14));
+        memcpy(u14, g->inflow + (size_t)j * nf, sizeof(double) * nf);
         if (r_center(g, j) < 0.5 * c->d_core && (c->seed_l_n > 0.0 || c->seed_s_n > 0.0)) {
           prim_t w;
-          cons_to_prim(u14, &w);
+          cons_to_prim(u14, g->nf == NF_BI, &w);
           double ml[4], ms[4];
           for (int k = 0; k < 4; ++k) {
             ml[k] = c->seed_l_n * pow(c->seed_l_r, (double)k) / moment_scale(k);
@@ -983,7 +1059,7 @@ void or_init_state(or_ctx *g, double *U) {
           prim_to_cons(w.p, w.T, w.u, w.v, Yv, ml, ms, w.ns, u14);
         }
       }
-      for (int f = 0; f < NF; ++f) U[(size_t)f * N + (size_t)j * g->nx + i] = u14[f];
+      for (int f = 0; f < nf; ++f) U[(size_t)f * N + (size_t)j * g->nx + i] = u14[f];
     }
   }
 }
@@ -992,60 +1068,63 @@ void or_init_state(or_ctx *g, double *U) {
  * and reading A1). */
 static void fill_padded(or_ctx *g, const double *U) {
   const or_case *c = &g->c;
+  const int nf = g->nf;
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
-  for (int f = 0; f < NF; ++f)
+  for (int f = 0; f < nf; ++f)
     for (int j = 0; j < nr; ++j)
       for (int i = 0; i < nx; ++i) UP(g, f, i, j) = U[(size_t)f * N + (size_t)j * nx + i];
   for (int j = 0; j < nr; ++j) {
     for (int gl = 1; gl <= 2; ++gl) {
       /* x low */
-      double u14[NF];
+      double u14[NFMAX] = {0};
       if (c->bc_xlo == 1) {
-        for (int f = 0; f < NF; ++f) u14[f] = UP(g, f, gl - 1, j);
+        for (int f = 0; f < nf; ++f) u14[f] = UP(g, f, gl - 1, j);
         u14[F_RU] = -u14[F_RU];
       } else if (c->geom == 0) {
         q1d_inlet_state(c, UP(g, F_RU, 0, j) / UP(g, F_RHO, 0, j), u14);
       } else {
-        memcpy(u14, g->inflow + (size_t)j * NF, sizeof(u14));
+        memcpy(u14, g->inflow + (size_t)j * nf, sizeof(double) * nf);
       }
-      for (int f = 0; f < NF; ++f) UP(g, f, -gl, j) = u14[f];
+      for (int f = 0; f < nf; ++f) UP(g, f, -gl, j) = u14[f];
       /* x high */
-      for (int f = 0; f < NF; ++f) u14[f] = c->bc_xhi == 1 ? UP(g, f, nx - gl, j) : UP(g, f, nx - 1, j);
+      for (int f = 0; f < nf; ++f) u14[f] = c->bc_xhi == 1 ? UP(g, f, nx - gl, j) : UP(g, f, nx - 1, j);
       if (c->bc_xhi == 1) u14[F_RU] = -u14[F_RU];
-      for (int f = 0; f < NF; ++f) UP(g, f, nx - 1 + gl, j) = u14[f];
+      for (int f = 0; f < nf; ++f) UP(g, f, nx - 1 + gl, j) = u14[f];
     }
   }
   if (c->geom == 1) {
     for (int i = 0; i < nx; ++i) {
       for (int gl = 1; gl <= 2; ++gl) {
         /* axis: mirror with rho*v negated */
-        for (int f = 0; f < NF; ++f) UP(g, f, i, -gl) = UP(g, f, i, gl - 1);
+        for (int f = 0; f < nf; ++f) UP(g, f, i, -gl) = UP(g, f, i, gl - 1);
         UP(g, F_RV, i, -gl) = -UP(g, F_RV, i, -gl);
         /* r high */
-        double u14[NF];
+        double u14[NFMAX];
         if (c->bc_rhi == 0) {
-          memcpy(u14, g->amb, sizeof(u14));
+          memcpy(u14, g->amb, sizeof(double) * nf);
         } else if (c->bc_rhi == 1) {
-          for (int f = 0; f < NF; ++f) u14[f] = UP(g, f, i, nr - gl);
+          for (int f = 0; f < nf; ++f) u14[f] = UP(g, f, i, nr - gl);
           u14[F_RV] = -u14[F_RV];
         } else {
-          for (int f = 0; f < NF; ++f) u14[f] = UP(g, f, i, nr - 1);
+          for (int f = 0; f < nf; ++f) u14[f] = UP(g, f, i, nr - 1);
         }
-        for (int f = 0; f < NF; ++f) UP(g, f, i, nr - 1 + gl) = u14[f];
+        for (int f = 0; f < nf; ++f) UP(g, f, i, nr - 1 + gl) = u14[f];
       }
     }
   }
 }
 
-static double water_of_flux(const double *F) {
-  return F[F_RYV] + 4.0 / 3.0 * PI * (RHOL * F[F_ML + 3] + RHOS * F[F_MS + 3]) * moment_scale(3);
+static double water_of_flux(const double *F, int nf) {
+  double fl = nf == NF_BI ? F[F_ML + 3] + F[F_MH + 3] : F[F_ML + 3];
+  return F[F_RYV] + 4.0 / 3.0 * PI * (RHOL * fl + RHOS * F[F_MS + 3]) * moment_scale(3);
 }
 
 /* Residual L(U) = -div F + S_geo + Q (Sec. 3.1 Eqs. (22), (25), (26); Sec. 3.2), and the
  * boundary inflow rates of mass, water and energy. */
 static void residual(or_ctx *g, const double *U, double dt) {
   const or_case *c = &g->c;
+  const int nf = g->nf;
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
   fill_padded(g, U);
@@ -1056,34 +1135,34 @@ static void residual(or_ctx *g, const double *U, double dt) {
       int xghost = ii < 0 || ii >= nx, rghost = jj < 0 || jj >= nr;
       if (xghost && rghost) continue;
       if (rghost && c->geom == 0) continue;
-      double u14[NF], q[NF];
-      for (int f = 0; f < NF; ++f) u14[f] = UP(g, f, ii, jj);
+      double u14[NFMAX], q[NFMAX];
+      for (int f = 0; f < nf; ++f) u14[f] = UP(g, f, ii, jj);
       prim_t w;
-      cons_to_prim(u14, &w);
+      cons_to_prim(u14, g->nf == NF_BI, &w);
       prim_vec(&w, q);
-      for (int f = 0; f < NF; ++f) WP(g, f, ii, jj) = q[f];
+      for (int f = 0; f < nf; ++f) WP(g, f, ii, jj) = q[f];
     }
   }
   /* x faces: face i lies between cells i-1 and i, i = 0..nx */
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < nr; ++j) {
     for (int i = 0; i <= nx; ++i) {
-      double qL[NF], qR[NF], F[NF];
-      for (int f = 0; f < NF; ++f) {
+      double qL[NFMAX], qR[NFMAX], F[NFMAX];
+      for (int f = 0; f < nf; ++f) {
         double am = WP(g, f, i - 2, j), a0 = WP(g, f, i - 1, j), a1 = WP(g, f, i, j), a2 = WP(g, f, i + 1, j);
         qL[f] = a0 + 0.5 * vl_slope(a0 - am, a1 - a0);
         qR[f] = a1 - 0.5 * vl_slope(a1 - a0, a2 - a1);
       }
-      or_roe_flux(qL, qR, 0, F);
+      roe_flux(qL, qR, 0, nf, F);
       /* walls are adiabatic, impermeable and slip: no diffusive flux through them */
       int xwall = (i == 0 && c->bc_xlo == 1) || (i == nx && c->bc_xhi == 1);
       if (c->viscous && !xwall) {
-        double qa[NF], qb[NF], G[NF];
-        for (int f = 0; f < NF; ++f) { qa[f] = WP(g, f, i - 1, j); qb[f] = WP(g, f, i, j); }
-        or_diffusive_flux(qa, qb, g->dx, c->nu_t, G);
-        for (int f = 0; f < NF; ++f) F[f] -= G[f];
+        double qa[NFMAX], qb[NFMAX], G[NFMAX];
+        for (int f = 0; f < nf; ++f) { qa[f] = WP(g, f, i - 1, j); qb[f] = WP(g, f, i, j); }
+        diffusive_flux(qa, qb, g->dx, c->nu_t, nf, G);
+        for (int f = 0; f < nf; ++f) F[f] -= G[f];
       }
-      for (int f = 0; f < NF; ++f) g->Fx[((size_t)f * nr + j) * (nx + 1) + i] = F[f];
+      for (int f = 0; f < nf; ++f) g->Fx[((size_t)f * nr + j) * (nx + 1) + i] = F[f];
     }
   }
   /* r faces: face j lies between cells j-1 and j, j = 0..nr */
@@ -1091,21 +1170,21 @@ static void residual(or_ctx *g, const double *U, double dt) {
 #pragma omp parallel for schedule(static)
     for (int j = 0; j <= nr; ++j) {
       for (int i = 0; i < nx; ++i) {
-        double qL[NF], qR[NF], F[NF];
-        for (int f = 0; f < NF; ++f) {
+        double qL[NFMAX], qR[NFMAX], F[NFMAX];
+        for (int f = 0; f < nf; ++f) {
           double am = WP(g, f, i, j - 2), a0 = WP(g, f, i, j - 1), a1 = WP(g, f, i, j), a2 = WP(g, f, i, j + 1);
           qL[f] = a0 + 0.5 * vl_slope(a0 - am, a1 - a0);
           qR[f] = a1 - 0.5 * vl_slope(a1 - a0, a2 - a1);
         }
-        or_roe_flux(qL, qR, 1, F);
+        roe_flux(qL, qR, 1, nf, F);
         int rwall = j == nr && c->bc_rhi == 1;
         if (c->viscous && !rwall) {
-          double qa[NF], qb[NF], G[NF];
-          for (int f = 0; f < NF; ++f) { qa[f] = WP(g, f, i, j - 1); qb[f] = WP(g, f, i, j); }
-          or_diffusive_flux(qa, qb, g->dr, c->nu_t, G);
-          for (int f = 0; f < NF; ++f) F[f] -= G[f];
+          double qa[NFMAX], qb[NFMAX], G[NFMAX];
+          for (int f = 0; f < nf; ++f) { qa[f] = WP(g, f, i, j - 1); qb[f] = WP(g, f, i, j); }
+          diffusive_flux(qa, qb, g->dr, c->nu_t, nf, G);
+          for (int f = 0; f < nf; ++f) F[f] -= G[f];
         }
-        for (int f = 0; f < NF; ++f) g->Fr[((size_t)f * (nr + 1) + j) * nx + i] = F[f];
+        for (int f = 0; f < nf; ++f) g->Fr[((size_t)f * (nr + 1) + j) * nx + i] = F[f];
       }
     }
   }
@@ -1116,26 +1195,26 @@ static void residual(or_ctx *g, const double *U, double dt) {
   for (int j = 0; j < nr; ++j) {
     for (int i = 0; i < nx; ++i) {
       size_t n = (size_t)j * nx + i;
-      double Fw[NF], Fe[NF], Fs[NF], Fn[NF];
-      for (int f = 0; f < NF; ++f) {
+      double Fw[NFMAX], Fe[NFMAX], Fs[NFMAX], Fn[NFMAX];
+      for (int f = 0; f < nf; ++f) {
         Fw[f] = g->Fx[((size_t)f * nr + j) * (nx + 1) + i];
         Fe[f] = g->Fx[((size_t)f * nr + j) * (nx + 1) + i + 1];
         Fs[f] = c->geom == 1 ? g->Fr[((size_t)f * (nr + 1) + j) * nx + i] : 0.0;
         Fn[f] = c->geom == 1 ? g->Fr[((size_t)f * (nr + 1) + j + 1) * nx + i] : 0.0;
       }
-      double u14[NF];
-      for (int f = 0; f < NF; ++f) u14[f] = U[(size_t)f * N + n];
+      double u14[NFMAX];
+      for (int f = 0; f < nf; ++f) u14[f] = U[(size_t)f * N + n];
       prim_t w;
-      cons_to_prim(u14, &w);
+      cons_to_prim(u14, g->nf == NF_BI, &w);
       double x = (i + 0.5) * g->dx;
       if (c->geom == 1 && c->wall_len > 0.0 && x < c->wall_len) {
         /* thin duct wall on the face at r = d_fan/2: each side sees a pressure-only flux */
-        if (j == jw - 1) { for (int f = 0; f < NF; ++f) Fn[f] = 0.0; Fn[F_RV] = w.p; }
-        if (j == jw) { for (int f = 0; f < NF; ++f) Fs[f] = 0.0; Fs[F_RV] = w.p; }
+        if (j == jw - 1) { for (int f = 0; f < nf; ++f) Fn[f] = 0.0; Fn[F_RV] = w.p; }
+        if (j == jw) { for (int f = 0; f < nf; ++f) Fs[f] = 0.0; Fs[F_RV] = w.p; }
       }
       /* flux divergence and geometric sources (reading A5) */
-      double Lf[NF];
-      for (int f = 0; f < NF; ++f) {
+      double Lf[NFMAX];
+      for (int f = 0; f < nf; ++f) {
         double div;
         if (c->geom == 0) {
           double Aw = area_q1d(c, i * g->dx), Ae = area_q1d(c, (i + 1) * g->dx), Ac = area_q1d(c, x);
@@ -1158,12 +1237,12 @@ static void residual(or_ctx *g, const double *U, double dt) {
         }
       }
       /* phase-change source, limited on the flux-updated stage state */
-      double A[NF], Q[NF], aux[11];
-      for (int f = 0; f < NF; ++f) A[f] = u14[f] + dt * Lf[f];
+      double A[NFMAX], Q[NFMAX], aux[11];
+      for (int f = 0; f < nf; ++f) A[f] = u14[f] + dt * Lf[f];
       phase_source(&w, A, dt, &g->sp, Q, aux);
       for (int a = 0; a < 11; ++a) g->aux[(size_t)a * N + n] = aux[a];
       active += aux[4] > 0.5;
-      for (int f = 0; f < NF; ++f) g->L[(size_t)f * N + n] = Lf[f] + Q[f];
+      for (int f = 0; f < nf; ++f) g->L[(size_t)f * N + n] = Lf[f] + Q[f];
     }
   }
   g->active_count = active;
@@ -1173,22 +1252,22 @@ static void residual(or_ctx *g, const double *U, double dt) {
     double Aw, Ae;
     if (c->geom == 0) { Aw = area_q1d(c, 0.0); Ae = area_q1d(c, nx * g->dx); }
     else { Aw = Ae = r_center(g, j) * g->dr; }
-    double Fw[NF], Fe[NF];
-    for (int f = 0; f < NF; ++f) {
+    double Fw[NFMAX], Fe[NFMAX];
+    for (int f = 0; f < nf; ++f) {
       Fw[f] = g->Fx[((size_t)f * nr + j) * (nx + 1) + 0];
       Fe[f] = g->Fx[((size_t)f * nr + j) * (nx + 1) + nx];
     }
     bm += Aw * Fw[F_RHO] - Ae * Fe[F_RHO];
-    bw += Aw * water_of_flux(Fw) - Ae * water_of_flux(Fe);
+    bw += Aw * water_of_flux(Fw, nf) - Ae * water_of_flux(Fe, nf);
     be += Aw * Fw[F_RE] - Ae * Fe[F_RE];
   }
   if (c->geom == 1) {
     for (int i = 0; i < nx; ++i) {
       double An = nr * g->dr * g->dx;
-      double Fn[NF];
-      for (int f = 0; f < NF; ++f) Fn[f] = g->Fr[((size_t)f * (nr + 1) + nr) * nx + i];
+      double Fn[NFMAX];
+      for (int f = 0; f < nf; ++f) Fn[f] = g->Fr[((size_t)f * (nr + 1) + nr) * nx + i];
       bm -= An * Fn[F_RHO];
-      bw -= An * water_of_flux(Fn);
+      bw -= An * water_of_flux(Fn, nf);
       be -= An * Fn[F_RE];
     }
   }
@@ -1199,14 +1278,15 @@ static void residual(or_ctx *g, const double *U, double dt) {
 
 /* Global CFL time step (Sec. 3.2: one CFL number controls the whole domain; reading A10). */
 double or_compute_dt(or_ctx *g, const double *U, double cfl) {
+  const int nf = g->nf;
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
   double dtmin = INFINITY;
   for (size_t n = 0; n < N; ++n) {
-    double u14[NF];
-    for (int f = 0; f < NF; ++f) u14[f] = U[(size_t)f * N + n];
+    double u14[NFMAX];
+    for (int f = 0; f < nf; ++f) u14[f] = U[(size_t)f * N + n];
     prim_t w;
-    cons_to_prim(u14, &w);
+    cons_to_prim(u14, g->nf == NF_BI, &w);
     double c = sqrt(w.c2);
     double rate = (fabs(w.u) + c) / g->dx;
     if (g->c.geom == 1) rate += (fabs(w.v) + c) / g->dr;
@@ -1229,9 +1309,10 @@ static void totals(or_ctx *g, const double *U, double *M, double *W, double *E) 
       size_t n = (size_t)j * nx + i;
       double V = cell_volume(g, i, j);
       m += V * U[(size_t)F_RHO * N + n];
+      double l3 = U[(size_t)(F_ML + 3) * N + n];
+      if (g->nf == NF_BI) l3 += U[(size_t)(F_MH + 3) * N + n];
       w += V * (U[(size_t)F_RYV * N + n] +
-                4.0 / 3.0 * PI * (RHOL * U[(size_t)(F_ML + 3) * N + n] + RHOS * U[(size_t)(F_MS + 3) * N + n]) *
-                    moment_scale(3));
+                4.0 / 3.0 * PI * (RHOL * l3 + RHOS * U[(size_t)(F_MS + 3) * N + n]) * moment_scale(3));
       e += V * U[(size_t)F_RE * N + n];
     }
   *M = m; *W = w; *E = e;
@@ -1240,18 +1321,19 @@ static void totals(or_ctx *g, const double *U, double *M, double *W, double *E) 
 /* One explicit SSP-RK2 (Heun) step with the same dt and the source in both stages
  * (Sec. 3.2, readings J, K):  U1 = U + dt L(U);  U <- U/2 + (U1 + dt L(U1))/2. */
 int or_step(or_ctx *g, double *U, int nsteps, double cfl, double *diag) {
+  const int nf = g->nf;
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
   for (int s = 0; s < nsteps; ++s) {
     double dt = or_compute_dt(g, U, cfl);
     double *d = diag ? diag + (size_t)s * NDIAG : NULL;
-    memcpy(g->U0, U, sizeof(double) * NF * N);
+    memcpy(g->U0, U, sizeof(double) * nf * N);
     residual(g, g->U0, dt);
     double b1[3] = {g->bflux[0], g->bflux[1], g->bflux[2]};
-    for (size_t m = 0; m < NF * N; ++m) g->U1[m] = g->U0[m] + dt * g->L[m];
+    for (size_t m = 0; m < nf * N; ++m) g->U1[m] = g->U0[m] + dt * g->L[m];
     residual(g, g->U1, dt);
     double b2[3] = {g->bflux[0], g->bflux[1], g->bflux[2]};
-    for (size_t m = 0; m < NF * N; ++m) U[m] = 0.5 * g->U0[m] + 0.5 * (g->U1[m] + dt * g->L[m]);
+    for (size_t m = 0; m < nf * N; ++m) U[m] = 0.5 * g->U0[m] + 0.5 * (g->U1[m] + dt * g->L[m]);
     if (d) {
       memset(d, 0, sizeof(double) * NDIAG);
       d[0] = dt;
@@ -1259,15 +1341,17 @@ int or_step(or_ctx *g, double *U, int nsteps, double cfl, double *diag) {
       for (int k = 0; k < 3; ++k) d[4 + k] = 0.5 * dt * (b1[k] + b2[k]);
       d[7] = g->active_count;
       double nonfinite = 0.0;
-      for (size_t m = 0; m < NF * N; ++m) nonfinite += !isfinite(U[m]);
+      for (size_t m = 0; m < nf * N; ++m) nonfinite += !isfinite(U[m]);
       d[8] = nonfinite;
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < nf; ++f) {
         double m = 0.0;
         for (size_t n = 0; n < N; ++n) {
           double r = fabs(U[(size_t)f * N + n] - g->U0[(size_t)f * N + n]) / dt;
           if (r > m) m = r;
         }
-        d[9 + f] = m;
+        /* the heterogeneous liquid's fields share the slots of the first liquid set */
+        int slot = f < NF ? f : F_ML + (f - F_MH);
+        if (m > d[9 + slot]) d[9 + slot] = m;
       }
       double mh = -INFINITY, mt = -INFINITY;
       for (size_t n = 0; n < N; ++n) {
@@ -1283,17 +1367,37 @@ int or_step(or_ctx *g, double *U, int nsteps, double cfl, double *diag) {
 
 /* Per-cell diagnostic fields of state U: which = 0 T, 1 p, 2 ln S_l, 3 ln S_i,
  * 4 log10 J_hom, 5 log10 J_het,eff, 6 active flag, 7 r_crit, 8 phi, 9 G_l, 10 G_s,
- * 11 Koop log10 J_s, 12 omega.  Source quantities use dt for the limiters only. */
+ * 11 Koop log10 J_s, 12 omega (9 and 12 of the first liquid set), 13/14 lognormal median
+ * radius and sigma_g of the (first) liquid set, 15/16 of the ice, 17/18 of the liquid of
+ * heterogeneous origin (bimodal; 0 otherwise).  Source quantities use dt for the limiters
+ * only. */
 void or_derived(or_ctx *g, const double *U, int which, double dt, double *out) {
+  const int nf = g->nf;
   int nx = g->nx, nr = g->nr;
   size_t N = (size_t)nx * nr;
   for (size_t n = 0; n < N; ++n) {
-    double u14[NF], Q[NF], aux[11];
-    for (int f = 0; f < NF; ++f) u14[f] = U[(size_t)f * N + n];
+    double u14[NFMAX], Q[NFMAX], aux[11];
+    for (int f = 0; f < nf; ++f) u14[f] = U[(size_t)f * N + n];
     prim_t w;
-    cons_to_prim(u14, &w);
+    cons_to_prim(u14, nf == NF_BI, &w);
     if (which == 0) { out[n] = w.T; continue; }
     if (which == 1) { out[n] = w.p; continue; }
+    if (which >= 13) {
+      /* lognormal size distribution with the cell's mu0, mu1, mu2 (Sec. 4.3's droplet
+       * spectra): mu_k = N r_m^k exp(k^2 s^2 / 2) gives ln r_m = 2 ln(mu1/mu0) - ln(mu2/mu0)/2
+       * and s^2 = ln(mu0 mu2 / mu1^2); radius in um, 0 without a population */
+      const double *m = which <= 14 ? w.ml : (which <= 16 ? w.ms : w.mh);
+      double v = 0.0;
+      if (m[0] > MU_MIN && m[1] > 0.0 && m[2] > 0.0) {
+        if (which == 13 || which == 15 || which == 17) v = exp(2.0 * log(m[1] / m[0]) - 0.5 * log(m[2] / m[0]));
+        else {
+          double s2 = log(m[0] * m[2] / (m[1] * m[1]));
+          v = exp(sqrt(s2 > 0.0 ? s2 : 0.0));
+        }
+      }
+      out[n] = v;
+      continue;
+    }
     phase_source(&w, NULL, dt, &g->sp, Q, aux);
     switch (which) {
       case 2: out[n] = aux[0]; break;
@@ -1305,22 +1409,25 @@ void or_derived(or_ctx *g, const double *U, int which, double dt, double *out) {
   }
 }
 
-/* Source of a batch of cells given conserved states (n x NF, row-major), for pins and
- * for the surrogate's training targets: Q out (n x NF), aux out (n x 11). */
+/* Source of a batch of cells given conserved states (n x nf, row-major; nf = 18 for the
+ * bimodal liquid, else 14), for pins and for the surrogate's training targets: Q out
+ * (n x nf), aux out (n x 11). */
 void or_source_batch(const or_case *c, const double *U, int n, double dt, double *Q, double *aux) {
+  const int nf = c->bimodal ? NF_BI : NF;
   src_par_t sp;
   sp.phase_change = c->phase_change;
   sp.freezing = c->freezing;
   sp.n_soot_ref = c->n_soot;
   sp.tables = c->tables;
   sp.equilibrium = c->equilibrium;
+  sp.bimodal = c->bimodal;
   build_tables();
   double ls = log(c->soot_sigma > 0.0 ? c->soot_sigma : 1.0);
   sp.rp2 = c->soot_rm * c->soot_rm * exp(2.0 * ls * ls);
   for (int m = 0; m < n; ++m) {
     prim_t w;
-    cons_to_prim(U + (size_t)m * NF, &w);
-    phase_source(&w, NULL, dt, &sp, Q + (size_t)m * NF, aux + (size_t)m * 11);
+    cons_to_prim(U + (size_t)m * nf, c->bimodal, &w);
+    phase_source(&w, NULL, dt, &sp, Q + (size_t)m * nf, aux + (size_t)m * 11);
   }
 }
 
@@ -1336,7 +1443,7 @@ void or_prim_to_cons_batch(const double *P, int n, double *U) {
 void or_cons_to_prim_batch(const double *U, int n, double *P) {
   for (int m = 0; m < n; ++m) {
     prim_t w;
-    cons_to_prim(U + (size_t)m * NF, &w);
+    cons_to_prim(U + (size_t)m * NF, 0, &w);
     double *o = P + (size_t)m * 9;
     o[0] = w.rho; o[1] = w.u; o[2] = w.v; o[3] = w.p; o[4] = w.T;
     o[5] = w.Yv; o[6] = w.Yl; o[7] = w.Ys; o[8] = w.c2;
@@ -1345,16 +1452,16 @@ void or_cons_to_prim_batch(const double *U, int n, double *P) {
 
 /* Inflow and ambient states as built by the oracle (for BC tests). */
 void or_boundary_states(or_ctx *g, double *inflow, double *amb) {
-  if (inflow) memcpy(inflow, g->inflow, sizeof(double) * NF * g->nr);
-  if (amb) memcpy(amb, g->amb, sizeof(double) * NF);
+  if (inflow) memcpy(inflow, g->inflow, sizeof(double) * g->nf * g->nr);
+  if (amb) memcpy(amb, g->amb, sizeof(double) * g->nf);
 }
 
-/* One residual evaluation (no time update) of state U, for pins: L out (NF x N),
+/* One residual evaluation (no time update) of state U, for pins: L out (nf x N),
  * bflux out (3). */
 void or_residual(or_ctx *g, const double *U, double dt, double *L, double *bflux) {
   size_t N = (size_t)g->nx * g->nr;
   residual(g, U, dt);
-  memcpy(L, g->L, sizeof(double) * NF * N);
+  memcpy(L, g->L, sizeof(double) * g->nf * N);
   if (bflux) memcpy(bflux, g->bflux, sizeof(double) * 3);
 }
 

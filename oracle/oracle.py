@@ -21,6 +21,7 @@ sys.path.insert(0, os.path.dirname(_HERE))
 from synth.cases import CASE_KEYS  # noqa: E402
 
 NF = 14
+NF_BI = 18        # fields of a state with the bimodal liquid
 NDIAG = 32
 AUX_NAMES = ("lnS_l", "lnS_i", "lnJ_hom", "lnJ_het", "active", "r_crit", "phi", "G_l", "G_s",
              "koop_log10J", "omega")
@@ -42,7 +43,14 @@ class OrCase(C.Structure):
     _fields_ = [(k, C.c_int32 if t == "i" else C.c_double) for k, t in CASE_KEYS]
 
 
+def nfields(c: dict) -> int:
+    """Fields of a case's state: 14, or 18 with the bimodal liquid."""
+    return NF_BI if int(c.get("bimodal", 0)) else NF
+
+
 def _case(c: dict) -> OrCase:
+    if int(c.get("bimodal", 0)) and int(c.get("equilibrium", 0)):
+        raise ValueError("the equilibrium model carries one condensate: not with the bimodal liquid")
     s = OrCase()
     for k, t in CASE_KEYS:
         setattr(s, k, int(c[k]) if t == "i" else float(c[k]))
@@ -89,6 +97,8 @@ def _L():
         lib.or_dv_mol.restype = d
         lib.or_dv_mol.argtypes = [d, d]
         lib.or_diffusive_flux.argtypes = [_dp, _dp, d, d, _dp]
+        lib.or_diffusive_flux_n.argtypes = [_dp, _dp, d, d, C.c_int, _dp]
+        lib.or_roe_flux_n.argtypes = [_dp, _dp, C.c_int, C.c_int, _dp]
         _lib = lib
     return _lib
 
@@ -144,24 +154,26 @@ def diffusive_flux(qa, qb, h: float, nu_t: float) -> np.ndarray:
     """Viscous/diffusive face flux G between primitive vectors qa (minus side), qb."""
     qa = np.ascontiguousarray(qa, dtype=np.float64)
     qb = np.ascontiguousarray(qb, dtype=np.float64)
-    G = np.zeros(NF)
-    _L().or_diffusive_flux(_ptr(qa), _ptr(qb), h, nu_t, _ptr(G))
+    G = np.zeros(len(qa))
+    _L().or_diffusive_flux_n(_ptr(qa), _ptr(qb), h, nu_t, len(qa), _ptr(G))
     return G
 
 
 def roe_flux(qL, qR, direction: int) -> np.ndarray:
     qL = np.ascontiguousarray(qL, dtype=np.float64)
     qR = np.ascontiguousarray(qR, dtype=np.float64)
-    F = np.zeros(NF)
-    _L().or_roe_flux(_ptr(qL), _ptr(qR), direction, _ptr(F))
+    F = np.zeros(len(qL))
+    _L().or_roe_flux_n(_ptr(qL), _ptr(qR), direction, len(qL), _ptr(F))
     return F
 
 
 def source_batch(case: dict, U: np.ndarray, dt: float):
-    """Q (n x 14) and aux (n x 11) of conserved states U (n x 14)."""
-    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1, NF)
+    """Q (n x nf) and aux (n x 11) of conserved states U (n x nf; nf = 18 for the bimodal
+    liquid, else 14)."""
+    nf = nfields(case)
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1, nf)
     n = U.shape[0]
-    Q = np.zeros((n, NF))
+    Q = np.zeros((n, nf))
     aux = np.zeros((n, 11))
     cs = _case(case)
     _L().or_source_batch(C.byref(cs), _ptr(U), n, dt, _ptr(Q), _ptr(aux))
@@ -185,12 +197,14 @@ def cons_to_prim_batch(U: np.ndarray) -> np.ndarray:
 
 
 class Oracle:
-    """One case on the CPU.  State arrays are (14, nr, nx) float64, x fastest."""
+    """One case on the CPU.  State arrays are (nf, nr, nx) float64, x fastest (nf = 14, or 18
+    with the bimodal liquid)."""
 
     def __init__(self, case: dict, ufac_rows=None):
         self.case = dict(case)
         self.nx = int(case["nx"])
         self.nr = int(case["nr"]) if case["geom"] == 1 else 1
+        self.nf = nfields(case)
         self._cs = _case(case)
         if ufac_rows is None:
             ufac_rows = np.ones(self.nr)
@@ -204,7 +218,7 @@ class Oracle:
 
     @property
     def shape(self):
-        return (NF, self.nr, self.nx)
+        return (self.nf, self.nr, self.nx)
 
     def init_state(self) -> np.ndarray:
         U = np.zeros(self.shape)
@@ -233,7 +247,7 @@ class Oracle:
         return L, b
 
     def boundary_states(self):
-        inflow = np.zeros((self.nr, NF))
-        amb = np.zeros(NF)
+        inflow = np.zeros((self.nr, self.nf))
+        amb = np.zeros(self.nf)
         _L().or_boundary_states(self._h, _ptr(inflow), _ptr(amb))
         return inflow, amb

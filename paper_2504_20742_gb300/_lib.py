@@ -26,7 +26,7 @@ _CASE_FIELDS = (
     ("Yv_core", "d"), ("T_byp", "d"), ("u_byp", "d"), ("n_soot", "d"), ("soot_rm", "d"),
     ("soot_sigma", "d"), ("p0", "d"), ("T0", "d"), ("Yv_inlet", "d"), ("seed_l_n", "d"),
     ("seed_l_r", "d"), ("seed_s_n", "d"), ("seed_s_r", "d"), ("mix_width", "d"), ("nu_t", "d"),
-    ("viscous", "i"), ("tables", "i"), ("equilibrium", "i"), ("pad_", "i"),
+    ("viscous", "i"), ("tables", "i"), ("equilibrium", "i"), ("bimodal", "i"),
 )
 
 

@@ -196,6 +196,22 @@ __global__ void k_derived(DevCase dc, const T* __restrict__ U, int which, double
     cons_to_prim<T>(u14, w);
     if (which == 0) { out[n] = double(w.Tg); continue; }
     if (which == 1) { out[n] = double(w.p); continue; }
+    if (which >= 13) {
+      // lognormal spectrum through mu0, mu1, mu2: median radius (um) and geometric width
+      const T* m = which <= 14 ? w.ml : w.ms;
+      double v = 0.0;
+      if (double(m[0]) > k::MU_MIN && m[1] > T(0) && m[2] > T(0)) {
+        const double m0 = m[0], m1 = m[1], m2 = m[2];
+        if (which == 13 || which == 15) {
+          v = exp(2.0 * log(m1 / m0) - 0.5 * log(m2 / m0));
+        } else {
+          const double s2 = log(m0 * m2 / (m1 * m1));
+          v = exp(sqrt(s2 > 0.0 ? s2 : 0.0));
+        }
+      }
+      out[n] = v;
+      continue;
+    }
     double aux[NAUX], lnJ2[2];
     phase_source<T>(w, u14, nullptr, T(dt), dc.sc, Q, lnJ2, aux);
     double v;
@@ -684,7 +700,7 @@ ct_status ct_derived(const ct_case* c, int precision, const void* U, int which, 
   ct_status s = validate(c, precision);
   if (s != CT_OK) return s;
   if (!U || !out) return fail(CT_ERR_ARG, "null buffer");
-  if (which < 0 || which > 12) return fail(CT_ERR_ARG, "which out of range [0, 12]");
+  if (which < 0 || which > 16) return fail(CT_ERR_ARG, "which out of range [0, 16]");
   if (!(dt > 0.0)) return fail(CT_ERR_ARG, "dt must be > 0");
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, nullptr);

@@ -32,7 +32,7 @@ CASE_KEYS = (
     ("n_soot", "d"), ("soot_rm", "d"), ("soot_sigma", "d"),
     ("p0", "d"), ("T0", "d"), ("Yv_inlet", "d"),
     ("seed_l_n", "d"), ("seed_l_r", "d"), ("seed_s_n", "d"), ("seed_s_r", "d"),
-    ("mix_width", "d"), ("nu_t", "d"), ("viscous", "i"), ("tables", "i"), ("equilibrium", "i"), ("pad_", "i"),
+    ("mix_width", "d"), ("nu_t", "d"), ("viscous", "i"), ("tables", "i"), ("equilibrium", "i"), ("bimodal", "i"),
 )
 
 _MASK = (1 << 64) - 1

@@ -149,3 +149,20 @@ def test_full_size_sweep_samples(P, blob):
         assert db[k, 0] == d[0]
     print("active cells per case (min, max):", db[:, 7].min(), db[:, 7].max(),
           "fallbacks:", db[:, 26].sum())
+
+
+def test_batch_with_optional_model_parts_matches_single_cases(P):
+    """Viscous fluxes, property tables and the equilibrium model travel with each case's
+    descriptor: a batch mixing them reproduces the single-case steps bit for bit (FP32)."""
+    bc = _small_batch(3)
+    extra = ({"viscous": 1, "nu_t": 0.2}, {"tables": 1}, {"equilibrium": 1}, {"viscous": 1, "nu_t": 0.05, "tables": 1})
+    bc = [(dict(c, **e), uf) for (c, uf), e in zip(bc, extra)]
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32)
+    b.init_state(0.5)
+    b.step(5, 0.5)
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0)
+    for k, (c, uf) in enumerate(bc):
+        ref, d = _single(P, c, uf, P.CT_FP32, 5)
+        assert torch.equal(b.state(k), ref), (k, c.get("viscous"), c.get("tables"), c.get("equilibrium"))
+        assert db[k, 0] == d[0]

@@ -261,6 +261,22 @@ def test_derived_fields_parity(P):
         assert np.allclose(g[fin], r[fin], rtol=1e-8, atol=1e-8), which
 
 
+def test_lognormal_spectra_parity(P):
+    """Derived 13-16 (lognormal liquid and ice spectra from mu0, mu1, mu2) on the oracle's
+    own state after 30 steps of the seeded mixing layer."""
+    c, uf = cases.mixing_layer_case()
+    o = O.Oracle(c, uf)
+    Uo = o.init_state()
+    o.step(Uo, 30, 0.5)
+    s = P.Solver(c, uf)
+    s.load_state(torch.tensor(Uo), 0.5)
+    for which in (13, 14, 15, 16):
+        g = s.derived(which, 1e-5).cpu().numpy()
+        r = o.derived(Uo, which, 1e-5)
+        assert np.count_nonzero(r) > 100, which
+        assert np.allclose(g, r, rtol=1e-12, atol=0.0), which
+
+
 def test_checkpoint_resume_is_bitwise(P):
     c, uf = cases.mixing_layer_case(nx=64, nr=32)
     a = P.Solver(c, uf)

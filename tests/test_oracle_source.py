@@ -300,3 +300,19 @@ def test_growth_limiter_reduces_to_explicit_rate_for_short_stages():
     _, a1 = O.source_batch(c, U, 1e-14)
     _, a2 = O.source_batch(c, U, 1e-13)
     assert a1[0, 7] == pytest.approx(a2[0, 7], rel=1e-9)
+
+
+def test_lognormal_spectrum_from_moments_is_exact():
+    """Derived quantities 13-16: a lognormal population (N, r_m, sigma_g) has moments
+    mu_k = N r_m^k exp(k^2 ln^2 sigma_g / 2); the reconstruction returns r_m and sigma_g."""
+    c, uf = cases.closed_box_case(nx=4, nr=2)
+    o = O.Oracle(c, uf)
+    U = o.init_state()
+    for rm, sg, rmi, sgi in ((0.2, 1.6, 1.5, 1.3), (0.015, 1.1, 3.0, 2.0)):
+        s2, s2i = np.log(sg) ** 2, np.log(sgi) ** 2
+        U2 = U.copy()
+        for k in range(4):
+            U2[5 + k] = U2[0] * 1e10 * rm ** k * np.exp(k * k * s2 / 2)
+            U2[9 + k] = U2[0] * 1e8 * rmi ** k * np.exp(k * k * s2i / 2)
+        got = [o.derived(U2, w)[0, 0] for w in (13, 14, 15, 16)]
+        assert np.allclose(got, [rm, sg, rmi, sgi], rtol=1e-12), got
