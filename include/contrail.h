@@ -22,7 +22,9 @@
  *     nozzle), 14 fields f:
  *        0 rho, 1 rho*u, 2 rho*v, 3 rho*E, 4 rho*Y_v,
  *        5..8  rho*mu_k(liquid)/(1 um)^k, 9..12 rho*mu_k(ice)/(1 um)^k, 13 rho*n_soot
- *     in SI units; mu_k are specific moments (per kg of mixture, Eq. (26)).
+ *     in SI units; mu_k are specific moments (per kg of mixture, Eq. (26)).  A case with
+ *     the bimodal liquid (ct_case.bimodal = 1) has 18 fields: 5..8 then hold the droplets
+ *     of homogeneous origin and 14..17 rho*mu_k/(1 um)^k of those of heterogeneous origin.
  *     Element type: double for CT_FP64, float for CT_FP32 and CT_FP32_MLP.
  */
 #ifndef CONTRAIL_H
@@ -36,6 +38,7 @@ extern "C" {
 #endif
 
 #define CT_NFIELDS 14
+#define CT_NFIELDS_BIMODAL 18
 #define CT_NDIAG 32
 #define CT_NAUX 11
 #define CT_MLP_IN 16       /* surrogate inputs */
@@ -81,7 +84,7 @@ typedef struct {
   int32_t viscous;                         /* 1: viscous and diffusive fluxes, Eqs. (25)-(26) */
   int32_t tables;                          /* 1: water properties from tables, 2nd-order Taylor */
   int32_t equilibrium;                     /* 1: equilibrium phase change (not with CT_FP32_MLP) */
-  int32_t pad_;                            /* unused, 0 */
+  int32_t bimodal;                         /* 1: two liquid moment sets, 18-field state (see below) */
 } ct_case;
 
 /* Optional parts of the model, each off by default:
@@ -97,14 +100,23 @@ typedef struct {
  *                    any stream capture.
  *   equilibrium = 1  equilibrium phase change instead of the kinetic model (the comparison
  *                    of Sec. 4.3): every stage leaves each cell's water at saturation over
- *                    its condensate (liquid above 235.15 K, ice below, 1 um monodisperse). */
+ *                    its condensate (liquid above 235.15 K, ice below, 1 um monodisperse).
+ *   bimodal = 1      the bimodal liquid of Sec. 2.2: one moment set per nucleation
+ *                    mechanism, so that spontaneously nucleated and soot-activated droplets
+ *                    keep their own size histories (the two-peaked spectrum of Sec. 4.3).
+ *                    Homogeneous nucleation feeds fields 5..8, heterogeneous nucleation the
+ *                    extra fields 14..17; each set grows at its own r20; only droplets of
+ *                    heterogeneous origin freeze by immersion (they hold the soot).  Every
+ *                    state buffer then has CT_NFIELDS_BIMODAL planes.  Not with CT_FP32_MLP
+ *                    (the surrogate was trained on one set) nor with equilibrium = 1. */
 
 /* Diagnostics record of the last completed step (CT_NDIAG doubles):
  *   0 dt of the step, 1 total mass, 2 total water (vapour + liquid + ice), 3 total energy
  *   (volume integrals per radian for geom 1, per unit throat area for geom 0),
  *   4..6 mass, water and energy that entered through the boundary during the step
  *   (RK2 rule), 7 active cells in stage 2, 8 non-finite values, 9..22 max-norm of
- *   (U^{n+1}-U^n)/dt per field, 23 max log10 J_hom, 24 max log10 J_het (m^-3 s^-1),
+ *   (U^{n+1}-U^n)/dt per field (bimodal: fields 14..17 share the slots of 5..8, the larger
+ *   of the two), 23 max log10 J_hom, 24 max log10 J_het (m^-3 s^-1),
  *   25 dt of the next step, 26 surrogate fallback cells (CT_FP32_MLP), 27 steps taken,
  *   28 tensor-core waits that gave up in either stage (CT_FP32_MLP; ct_diagnostics then
  *   returns CT_ERR_TIMEOUT). */
@@ -155,13 +167,16 @@ ct_status ct_diagnostics(const void *work, double *host_out, int nout, void *str
  * 7 r_crit, 8 Kantrowitz phi, 9 G_l(r20), 10 G_s(r20), 11 Koop log10 J_s (cm^-3 s^-1),
  * 12 per-droplet freezing rate omega, 13/14 median radius (um) and geometric standard
  * deviation of the lognormal liquid spectrum with the cell's mu0, mu1, mu2 (the droplet
- * spectra of Sec. 4.3), 15/16 the same for ice.  Non-applicable values are -inf (logs) or 0.
+ * spectra of Sec. 4.3), 15/16 the same for ice, 17/18 the same for the droplets of
+ * heterogeneous origin (bimodal cases; 0 otherwise).  With the bimodal liquid, 9 and 12 and
+ * 13/14 describe the droplets of homogeneous origin.  Non-applicable values are -inf (logs) or 0.
  * dt enters only the limiters. */
 ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, double dt,
                      double *out, void *stream);
 
-/* Phase-change source (Sec. 2.2) of n independent cells: U (device, n x CT_NFIELDS
- * doubles, row-major conserved states) -> Q (device, n x CT_NFIELDS) and aux (device,
+/* Phase-change source (Sec. 2.2) of n independent cells: U (device, n x nf doubles,
+ * row-major conserved states, nf = CT_NFIELDS_BIMODAL for a bimodal case, else CT_NFIELDS)
+ * -> Q (device, n x nf) and aux (device,
  * n x CT_NAUX: ln S_l, ln S_i, ln J_hom, ln J_het,eff, active, r_crit, phi, G_l, G_s,
  * Koop log10 J_s, omega), evaluated at the given precision with limiters of step dt. */
 ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int n, double dt,
@@ -288,14 +303,15 @@ ct_status ct_autotune(const ct_case *c, int precision, const void *U, void *U1, 
  * conditions together.  Each step is two launches of a persistent kernel whose CTAs take
  * the tiles of all cases from one work list; every case keeps its own CFL time step and
  * diagnostics.  Batch state layout: the cases' states (each in the single-case layout)
- * one after another, case k starting at element 14 * sum_{k' < k} nx_k' nr_k'.
- * FP32 and FP32_MLP only. */
+ * one after another, case k starting at element nf * sum_{k' < k} nx_k' nr_k' (nf = 14, or
+ * 18 when the cases are bimodal: all cases of a batch share the flag).  FP32 and FP32_MLP
+ * only. */
 typedef struct ct_batch ct_batch;   /* host object: case table, tile shape, captured graph */
 
 /* Device workspace bytes of a batch (0 for invalid cases). */
 size_t ct_batch_workspace_bytes(const ct_case *cases, int ncases);
 
-/* Elements of one batch state (sum over cases of 14 nx nr). */
+/* Elements of one batch state (sum over cases of nf nx nr). */
 size_t ct_batch_state_elems(const ct_case *cases, int ncases);
 
 /* Validate 1..96 cases, set up every case's part of `work` (device, 256-byte aligned,

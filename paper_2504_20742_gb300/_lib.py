@@ -15,6 +15,12 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libcontrail.so")
 
 CT_FP64, CT_FP32, CT_FP32_MLP = 0, 1, 2
 NF, NDIAG, NAUX = 14, 32, 11
+NF_BI = 18   # fields of a state with the bimodal liquid
+
+
+def nfields(case) -> int:
+    """Fields of a case's state: 14, or 18 with the bimodal liquid."""
+    return NF_BI if int(case.get("bimodal", 0)) else NF
 CT_MLP_IN, CT_MLP_HIDDEN, CT_MLP_OUT = 16, 128, 10
 
 # ct_case fields, in the order of include/contrail.h

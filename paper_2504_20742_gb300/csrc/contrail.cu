@@ -20,8 +20,9 @@ namespace ct {
 
 
 // ---- time step of a given state (initial step / after a load) --------------------------
-template <class T>
+template <class T, bool BI = false>
 __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__ U) {
+  constexpr int NFX = nf_of<BI>();
   constexpr int NT = NT_AUX;
   __shared__ double red[NT / 32][NPART];
   __shared__ double fin[NPART];
@@ -29,11 +30,11 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
   const size_t N = (size_t)nx * nr;
   T dtmin = T(INFINITY);
   for (size_t n = (size_t)blockIdx.x * NT + threadIdx.x; n < N; n += (size_t)gridDim.x * NT) {
-    T u14[NF];
+    T u14[NFX];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     Prim<T> w;
-    cons_to_prim<T>(u14, w);
+    cons_to_prim<T, BI>(u14, w);
     const T c = m_sqrt(w.c2);
     T rate = (m_fabs(w.u) + c) * T(dc.idx);
     if (dc.geom == 1) rate += (m_fabs(w.v) + c) * T(dc.idr);
@@ -127,10 +128,18 @@ __device__ void inflow_cons(const ct_case& c, double r, double ufac, double* u14
   }
 }
 
-__global__ void k_setup(ct_case c, const double* __restrict__ ufac, double* inflow, double* amb, int nr, double dr) {
-  for (int j = threadIdx.x; j < nr; j += blockDim.x)
-    inflow_cons(c, (j + 0.5) * dr, ufac ? ufac[j] : 1.0, inflow + (size_t)j * NF);
-  if (threadIdx.x == 0) ambient_cons(c, 1.0, amb);
+// nf fields per state (18 with the bimodal liquid: the second set enters empty)
+__global__ void k_setup(ct_case c, const double* __restrict__ ufac, double* inflow, double* amb, int nr, double dr,
+                        int nf) {
+  for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+    double* row = inflow + (size_t)j * nf;
+    inflow_cons(c, (j + 0.5) * dr, ufac ? ufac[j] : 1.0, row);
+    for (int f = NF; f < nf; ++f) row[f] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    ambient_cons(c, 1.0, amb);
+    for (int f = NF; f < nf; ++f) amb[f] = 0.0;
+  }
 }
 
 // ---- initial state -----------------------------------------------------------------------
@@ -138,13 +147,15 @@ __device__ double area_mach(double M, double g) {
   return 1.0 / M * pow(2.0 / (g + 1.0) * (1.0 + 0.5 * (g - 1.0) * M * M), 0.5 * (g + 1.0) / (g - 1.0));
 }
 
-template <class T>
+template <class T, bool BI = false>
 __global__ void k_init(ct_case c, DevCase dc, T* __restrict__ U) {
+  constexpr int NFX = nf_of<BI>();
   const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
   const size_t N = (size_t)nx * nr;
   for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int i = int(n % nx), j = int(n / nx);
-    double u14[NF];
+    double u14[NFX];
+    for (int f = NF; f < NFX; ++f) u14[f] = 0.0;   // the second liquid set starts empty
     if (dc.geom == 0) {
       const double z[4] = {0, 0, 0, 0};
       const double g = dc.gam0, Rg = (1.0 - dc.Yv0) * k::RA + dc.Yv0 * k::RV;
@@ -162,7 +173,7 @@ __global__ void k_init(ct_case c, DevCase dc, T* __restrict__ U) {
       const double p = dc.p0 * pow(Tg / dc.T0, g / (g - 1.0));
       prim_to_cons<double>(p, Tg, M * sqrt(g * Rg * Tg), 0.0, dc.Yv0, z, z, 0.0, u14);
     } else {
-      for (int f = 0; f < NF; ++f) u14[f] = dc.inflow[(size_t)j * NF + f];
+      for (int f = 0; f < NFX; ++f) u14[f] = dc.inflow[(size_t)j * NFX + f];
       const double r = (j + 0.5) * dc.dr;
       if (r < 0.5 * c.d_core && (c.seed_l_n > 0.0 || c.seed_s_n > 0.0)) {
         Prim<double> w;
@@ -179,30 +190,32 @@ __global__ void k_init(ct_case c, DevCase dc, T* __restrict__ U) {
         prim_to_cons<double>(w.p, w.Tg, w.u, w.v, Yv, ml, ms, w.ns, u14);
       }
     }
-    for (int f = 0; f < NF; ++f) U[f * N + n] = T(u14[f]);
+    for (int f = 0; f < NFX; ++f) U[f * N + n] = T(u14[f]);
   }
 }
 
 // ---- derived per-cell quantities and pointwise sources ------------------------------------
-template <class T>
+template <class T, bool BI = false>
 __global__ void k_derived(DevCase dc, const T* __restrict__ U, int which, double dt, double* __restrict__ out) {
+  constexpr int NFX = nf_of<BI>();
   const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
   const size_t N = (size_t)nx * nr;
   for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-    T u14[NF], Q[NF];
+    T u14[NFX], Q[NFX];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     Prim<T> w;
-    cons_to_prim<T>(u14, w);
+    cons_to_prim<T, BI>(u14, w);
     if (which == 0) { out[n] = double(w.Tg); continue; }
     if (which == 1) { out[n] = double(w.p); continue; }
     if (which >= 13) {
       // lognormal spectrum through mu0, mu1, mu2: median radius (um) and geometric width
-      const T* m = which <= 14 ? w.ml : w.ms;
+      if (which >= 17 && !BI) { out[n] = 0.0; continue; }
+      const T* m = which <= 14 ? w.ml : (which <= 16 ? w.ms : w.mh);
       double v = 0.0;
       if (double(m[0]) > k::MU_MIN && m[1] > T(0) && m[2] > T(0)) {
         const double m0 = m[0], m1 = m[1], m2 = m[2];
-        if (which == 13 || which == 15) {
+        if (which == 13 || which == 15 || which == 17) {
           v = exp(2.0 * log(m1 / m0) - 0.5 * log(m2 / m0));
         } else {
           const double s2 = log(m0 * m2 / (m1 * m1));
@@ -213,7 +226,7 @@ __global__ void k_derived(DevCase dc, const T* __restrict__ U, int which, double
       continue;
     }
     double aux[NAUX], lnJ2[2];
-    phase_source<T>(w, u14, nullptr, T(dt), dc.sc, Q, lnJ2, aux);
+    phase_source<T, BI>(w, u14, nullptr, T(dt), dc.sc, Q, lnJ2, aux);
     double v;
     switch (which) {
       case 2: v = aux[0]; break;
@@ -226,17 +239,18 @@ __global__ void k_derived(DevCase dc, const T* __restrict__ U, int which, double
   }
 }
 
-template <class T>
+template <class T, bool BI = false>
 __global__ void k_source_batch(SrcCase sc, const double* __restrict__ U, int n, double dt, double* __restrict__ Qo,
                                double* __restrict__ auxo) {
+  constexpr int NFX = nf_of<BI>();
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-    T u14[NF], Q[NF];
-    for (int f = 0; f < NF; ++f) u14[f] = T(U[(size_t)m * NF + f]);
+    T u14[NFX], Q[NFX];
+    for (int f = 0; f < NFX; ++f) u14[f] = T(U[(size_t)m * NFX + f]);
     Prim<T> w;
-    cons_to_prim<T>(u14, w);
+    cons_to_prim<T, BI>(u14, w);
     double aux[NAUX], lnJ2[2];
-    phase_source<T>(w, u14, nullptr, T(dt), sc, Q, lnJ2, aux);
-    for (int f = 0; f < NF; ++f) Qo[(size_t)m * NF + f] = (f >= 4 && f <= 12) ? double(Q[f]) : 0.0;
+    phase_source<T, BI>(w, u14, nullptr, T(dt), sc, Q, lnJ2, aux);
+    for (int f = 0; f < NFX; ++f) Qo[(size_t)m * NFX + f] = ((f >= 4 && f <= 12) || f >= NF) ? double(Q[f]) : 0.0;
     for (int a = 0; a < NAUX; ++a) auxo[(size_t)m * NAUX + a] = aux[a];
   }
 }
@@ -303,6 +317,8 @@ static ct_status cuda_check(const char* where) {
 }
 
 static int case_nr(const ct_case* c) { return c->geom == 1 ? c->nr : 1; }
+// fields of a case's state: 14, or 18 with the bimodal liquid
+static int case_nf(const ct_case* c) { return c->bimodal ? NF_BI : NF; }
 
 // ---- tile shapes ------------------------------------------------------------------------
 namespace ct {
@@ -320,7 +336,11 @@ const StageSet* stage_set(int shape) {
 }
 }  // namespace ct
 
-static int prec_index(int precision) { return precision == CT_FP64 ? 0 : (precision == CT_FP32 ? 1 : 2); }
+// kernel variant of a case at a precision (the index into StageSet)
+static int variant_of(const ct_case* c, int precision) {
+  if (precision == CT_FP32_MLP) return 2;
+  return (precision == CT_FP64 ? 0 : 1) + (c->bimodal ? 3 : 0);
+}
 static int tiles_x(const ct_case* c, int shape) {
   const int tx = stage_set(shape)->tx;
   return (c->nx + tx - 1) / tx;
@@ -347,15 +367,15 @@ static int max_rows(const ct_case* c) {
 static std::mutex g_shape_mu;
 static std::map<std::tuple<int, int, int, int>, int> g_shape;
 static std::tuple<int, int, int, int> shape_key(const ct_case* c, int precision) {
-  return std::make_tuple(c->geom, c->nx, case_nr(c), prec_index(precision));
+  return std::make_tuple(c->geom, c->nx, case_nr(c), variant_of(c, precision));
 }
 static int shape_for(const ct_case* c, int precision) {
   std::lock_guard<std::mutex> lk(g_shape_mu);
   auto it = g_shape.find(shape_key(c, precision));
   return it == g_shape.end() ? 0 : it->second;
 }
-static bool shape_usable(int shape, int precision) {
-  return shape >= 0 && shape < NSHAPES && stage_set(shape)->stage[prec_index(precision)][0] != nullptr;
+static bool shape_usable(int shape, int variant) {
+  return shape >= 0 && shape < NSHAPES && stage_set(shape)->stage[variant][0] != nullptr;
 }
 
 static ct_status validate(const ct_case* c, int precision) {
@@ -377,6 +397,11 @@ static ct_status validate(const ct_case* c, int precision) {
   if (c->equilibrium != 0 && c->equilibrium != 1) return fail(CT_ERR_ARG, "equilibrium must be 0 or 1");
   if (c->equilibrium && precision == CT_FP32_MLP)
     return fail(CT_ERR_ARG, "the surrogate stands in for the kinetic source: no equilibrium with CT_FP32_MLP");
+  if (c->bimodal != 0 && c->bimodal != 1) return fail(CT_ERR_ARG, "bimodal must be 0 or 1");
+  if (c->bimodal && precision == CT_FP32_MLP)
+    return fail(CT_ERR_ARG, "the surrogate was trained on one liquid set: no bimodal liquid with CT_FP32_MLP");
+  if (c->bimodal && c->equilibrium)
+    return fail(CT_ERR_ARG, "the equilibrium model carries one condensate: not with the bimodal liquid");
   if (!(c->nu_t >= 0.0) || c->nu_t > 1.0e3) return fail(CT_ERR_ARG, "nu_t out of range [0, 1e3]");
   return CT_OK;
 }
@@ -386,8 +411,8 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 static size_t ws_bytes(const ct_case* c) {
   const size_t nr = (size_t)case_nr(c);
   size_t b = HDR_BYTES;
-  b += align256(nr * NF * sizeof(double));
-  b += align256(NF * sizeof(double));
+  b += align256(nr * case_nf(c) * sizeof(double));
+  b += align256(case_nf(c) * sizeof(double));
   b += align256((size_t)max_blocks(c) * NPART * sizeof(double));
   b += align256((size_t)max_rows(c) * sizeof(unsigned int));
   b += align256((size_t)max_rows(c) * NPART * sizeof(double));
@@ -466,9 +491,9 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.hdr = (WsHeader*)base;
   size_t off = HDR_BYTES;
   d.inflow = (const double*)(base + off);
-  off += align256((size_t)d.nr * NF * sizeof(double));
+  off += align256((size_t)d.nr * case_nf(c) * sizeof(double));
   d.amb = (const double*)(base + off);
-  off += align256(NF * sizeof(double));
+  off += align256(case_nf(c) * sizeof(double));
   d.partials = (double*)(base + off);
   off += align256((size_t)max_blocks(c) * NPART * sizeof(double));
   d.row_count = (unsigned int*)(base + off);
@@ -535,7 +560,7 @@ ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host
   if (cudaMemcpyAsync(work, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) return cuda_check("ct_setup header");
   if (cudaMemsetAsync(d.row_count, 0, (size_t)max_rows(c) * sizeof(unsigned int), st) != cudaSuccess)
     return cuda_check("ct_setup row tickets");
-  if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr);
+  if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr, case_nf(c));
   // the header copy and the profile kernel read host memory that must outlive them
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_setup sync");
   return cuda_check("ct_setup");
@@ -555,8 +580,13 @@ static ct_status launch_dt(const ct_case* c, int precision, void* work, const vo
   // a grid-stride kernel: a few hundred CTAs keep its one-level reduction short
   int grid = (int)std::min<size_t>(std::min<size_t>((N + NT_AUX - 1) / NT_AUX, (size_t)d.nblocks), (size_t)512);
   d.nblocks = grid;
-  if (precision == CT_FP64) k_dt<double><<<grid, NT_AUX, 0, st>>>(d, (const double*)U);
-  else k_dt<float><<<grid, NT_AUX, 0, st>>>(d, (const float*)U);
+  if (precision == CT_FP64) {
+    if (c->bimodal) k_dt<double, true><<<grid, NT_AUX, 0, st>>>(d, (const double*)U);
+    else k_dt<double><<<grid, NT_AUX, 0, st>>>(d, (const double*)U);
+  } else {
+    if (c->bimodal) k_dt<float, true><<<grid, NT_AUX, 0, st>>>(d, (const float*)U);
+    else k_dt<float><<<grid, NT_AUX, 0, st>>>(d, (const float*)U);
+  }
   return cuda_check("k_dt");
 }
 
@@ -570,8 +600,13 @@ ct_status ct_init_state(const ct_case* c, int precision, void* work, void* U, do
   DevCase d = make_dev(c, work);
   const size_t N = (size_t)c->nx * case_nr(c);
   int grid = (int)std::min<size_t>((N + 255) / 256, 4096);
-  if (precision == CT_FP64) k_init<double><<<grid, 256, 0, st>>>(*c, d, (double*)U);
-  else k_init<float><<<grid, 256, 0, st>>>(*c, d, (float*)U);
+  if (precision == CT_FP64) {
+    if (c->bimodal) k_init<double, true><<<grid, 256, 0, st>>>(*c, d, (double*)U);
+    else k_init<double><<<grid, 256, 0, st>>>(*c, d, (double*)U);
+  } else {
+    if (c->bimodal) k_init<float, true><<<grid, 256, 0, st>>>(*c, d, (float*)U);
+    else k_init<float><<<grid, 256, 0, st>>>(*c, d, (float*)U);
+  }
   if ((s = cuda_check("k_init")) != CT_OK) return s;
   return launch_dt(c, precision, work, U, cfl, st);
 }
@@ -584,18 +619,17 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t N = (size_t)c->nx * case_nr(c);
-  const size_t bytes = N * NF * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
+  const size_t bytes = N * case_nf(c) * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
   if (U_src != U && cudaMemcpyAsync(U, U_src, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return cuda_check("ct_load_state copy");
   return launch_dt(c, precision, work, U, cfl, st);
 }
 
 static std::mutex g_attr_mu;
-static bool g_attr_done[NSHAPES][3];
+static bool g_attr_done[NSHAPES][NVARIANT];
 
-// Opt the kernels of one (shape, precision) into their dynamic shared memory, once.
-static ct_status set_stage_attrs(int shape, int precision) {
-  const int p = prec_index(precision);
+// Opt the kernels of one (shape, kernel variant) into their dynamic shared memory, once.
+static ct_status set_stage_attrs(int shape, int p) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (g_attr_done[shape][p]) return CT_OK;
   const StageSet* ss = stage_set(shape);
@@ -625,12 +659,12 @@ static void launch_stage(const StageSet* ss, int p, int stage, const DevCase& d,
 
 static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
                                cudaStream_t st, const void* blob = nullptr, int shape = -1) {
+  const int p = variant_of(c, precision);
   if (shape < 0) shape = shape_for(c, precision);
-  if (!shape_usable(shape, precision)) shape = 0;
-  ct_status s = set_stage_attrs(shape, precision);
+  if (!shape_usable(shape, p)) shape = 0;
+  ct_status s = set_stage_attrs(shape, p);
   if (s != CT_OK) return s;
   const StageSet* ss = stage_set(shape);
-  const int p = prec_index(precision);
   DevCase d = make_dev(c, work, shape);
   d.cfl = cfl;
   dim3 grid(tiles_x(c, shape), tiles_y(c, shape));
@@ -672,7 +706,7 @@ ct_status ct_step_host(const ct_case* c, int precision, const void* U_host_in, v
   if (!U_host_in || !U_host_out) return fail(CT_ERR_ARG, "null host buffer");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t N = (size_t)c->nx * case_nr(c);
-  const size_t bytes = N * NF * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
+  const size_t bytes = N * case_nf(c) * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
   if (cudaMemcpyAsync(U, U_host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return cuda_check("h2d");
   if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
   if ((s = ct_step(c, precision, U, U1, work, nsteps, cfl, stream)) != CT_OK) return s;
@@ -700,14 +734,19 @@ ct_status ct_derived(const ct_case* c, int precision, const void* U, int which, 
   ct_status s = validate(c, precision);
   if (s != CT_OK) return s;
   if (!U || !out) return fail(CT_ERR_ARG, "null buffer");
-  if (which < 0 || which > 16) return fail(CT_ERR_ARG, "which out of range [0, 16]");
+  if (which < 0 || which > 18) return fail(CT_ERR_ARG, "which out of range [0, 18]");
   if (!(dt > 0.0)) return fail(CT_ERR_ARG, "dt must be > 0");
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, nullptr);
   const size_t N = (size_t)c->nx * case_nr(c);
   int grid = (int)std::min<size_t>((N + 255) / 256, 8192);
-  if (precision == CT_FP64) k_derived<double><<<grid, 256, 0, st>>>(d, (const double*)U, which, dt, out);
-  else k_derived<float><<<grid, 256, 0, st>>>(d, (const float*)U, which, dt, out);
+  if (precision == CT_FP64) {
+    if (c->bimodal) k_derived<double, true><<<grid, 256, 0, st>>>(d, (const double*)U, which, dt, out);
+    else k_derived<double><<<grid, 256, 0, st>>>(d, (const double*)U, which, dt, out);
+  } else {
+    if (c->bimodal) k_derived<float, true><<<grid, 256, 0, st>>>(d, (const float*)U, which, dt, out);
+    else k_derived<float><<<grid, 256, 0, st>>>(d, (const float*)U, which, dt, out);
+  }
   return cuda_check("k_derived");
 }
 
@@ -722,8 +761,13 @@ ct_status ct_source_batch(const ct_case* c, int precision, const double* U, int 
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, nullptr);
   int grid = std::min((n + 255) / 256, 8192);
-  if (precision == CT_FP64) k_source_batch<double><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
-  else k_source_batch<float><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
+  if (precision == CT_FP64) {
+    if (c->bimodal) k_source_batch<double, true><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
+    else k_source_batch<double><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
+  } else {
+    if (c->bimodal) k_source_batch<float, true><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
+    else k_source_batch<float><<<grid, 256, 0, st>>>(d.sc, U, n, dt, Q, aux);
+  }
   return cuda_check("k_source_batch");
 }
 
@@ -792,7 +836,8 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, work);
   k_scratch_reset<<<1, 256, 0, st>>>(d.nblocks, d.row_count, max_rows(c));
-  if (c->geom == 1) k_setup<<<1, 256, 0, st>>>(*c, ufac_rows_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr);
+  if (c->geom == 1)
+    k_setup<<<1, 256, 0, st>>>(*c, ufac_rows_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr, case_nf(c));
   if ((s = cuda_check("ct_step_static setup")) != CT_OK) return s;
   if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
   return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st);
@@ -816,7 +861,7 @@ ct_status ct_set_tile_shape(const ct_case* c, int precision, int shape) {
     g_shape.erase(shape_key(c, precision));
     return CT_OK;
   }
-  if (!shape_usable(shape, precision)) return fail(CT_ERR_ARG, "tile shape not available for this precision");
+  if (!shape_usable(shape, variant_of(c, precision))) return fail(CT_ERR_ARG, "tile shape not available for this precision");
   g_shape[shape_key(c, precision)] = shape;
   return CT_OK;
 }
@@ -829,13 +874,13 @@ ct_status ct_autotune(const ct_case* c, int precision, const void* U, void* U1, 
   if (precision == CT_FP32_MLP && (!blob || ((uintptr_t)blob & 15) != 0)) return fail(CT_ERR_ARG, "ct_autotune: blob");
   if (reps < 1) return fail(CT_ERR_ARG, "ct_autotune: reps < 1");
   cudaStream_t st = (cudaStream_t)stream;
-  const int p = prec_index(precision);
+  const int p = variant_of(c, precision);
   int best = -1;
   float best_ms = 0.0f;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     float ms = -1.0f;
-    if (shape_usable(sh, precision)) {
-      if ((s = set_stage_attrs(sh, precision)) != CT_OK) return s;
+    if (shape_usable(sh, p)) {
+      if ((s = set_stage_attrs(sh, p)) != CT_OK) return s;
       const StageSet* ss = stage_set(sh);
       DevCase d = make_dev(c, work, sh);
       const dim3 grid(tiles_x(c, sh), tiles_y(c, sh));
@@ -892,6 +937,8 @@ static ct_status batch_validate(const ct_case* cases, int ncases, int precision)
     ct_status s = validate(&cases[k], precision);
     if (s != CT_OK) return s;
     if (cases[k].geom != 1) return fail(CT_ERR_ARG, "batched cases must be axisymmetric plumes (geom 1)");
+    if (cases[k].bimodal != cases[0].bimodal)
+      return fail(CT_ERR_ARG, "the cases of a batch share one state layout: all bimodal or none");
   }
   return CT_OK;
 }
@@ -924,17 +971,18 @@ static ct_status batch_upload(ct_batch* b) {
     h.cases[k] = make_dev(&b->cases[k], b->work + b->case_off[k], b->shape);
   }
   // persistent grid: every SM full, never more CTAs than tiles
-  ct_status s = set_stage_attrs(b->shape, b->precision);
+  const int p = variant_of(&b->cases[0], b->precision);
+  ct_status s = set_stage_attrs(b->shape, p);
   if (s != CT_OK) return s;
   const StageSet* ss = stage_set(b->shape);
-  const int p = prec_index(b->precision);
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // The runtime's occupancy calculator assumes one CTA per SM for kernels that use TMEM;
   // every CTA here gives up its allocation permit at once, so take the register and
   // shared-memory limit of the plain FP32 kernel (same registers) at this shared memory.
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ss->batch[1][0], ss->nt, ss->smem[p]) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ss->batch[p == 2 ? 1 : p][0], ss->nt, ss->smem[p]) !=
+      cudaSuccess)
     return cuda_check("occupancy");
   per_sm = std::max(1, per_sm);
   if (b->precision == CT_FP32_MLP) {
@@ -951,7 +999,7 @@ static ct_status batch_upload(ct_batch* b) {
 static void batch_launch(ct_batch* b, int stage, const void* Uin, const void* Un, void* Uout, const void* blob,
                          double cfl, cudaStream_t st) {
   const StageSet* ss = stage_set(b->shape);
-  const int p = prec_index(b->precision);
+  const int p = variant_of(&b->cases[0], b->precision);
   BatchCounters* ctr = b->ctr;
   const void* a1 = Uin;
   const void* a2 = Un;
@@ -980,7 +1028,7 @@ size_t ct_batch_workspace_bytes(const ct_case* cases, int ncases) {
 size_t ct_batch_state_elems(const ct_case* cases, int ncases) {
   if (batch_validate(cases, ncases, CT_FP32) != CT_OK) return 0;
   size_t n = 0;
-  for (int k = 0; k < ncases; ++k) n += (size_t)NF * cases[k].nx * case_nr(&cases[k]);
+  for (int k = 0; k < ncases; ++k) n += (size_t)case_nf(&cases[k]) * cases[k].nx * case_nr(&cases[k]);
   return n;
 }
 
@@ -1005,7 +1053,7 @@ ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const
     b->case_off.push_back(off);
     b->state_off.push_back(so);
     off += align256(ws_bytes(&cases[k]));
-    so += (long long)NF * cases[k].nx * case_nr(&cases[k]);
+    so += (long long)case_nf(&cases[k]) * cases[k].nx * case_nr(&cases[k]);
   }
   // per-case workspace: header, inflow profile and ambient state
   for (int k = 0; k < ncases && s == CT_OK; ++k) {
@@ -1057,7 +1105,7 @@ ct_status ct_batch_load_state(ct_batch* b, const void* U_src, void* U, double cf
 
 ct_status ct_batch_set_tile_shape(ct_batch* b, int shape) {
   if (!b) return fail(CT_ERR_ARG, "null batch");
-  if (shape < 0 || shape >= NSHAPES || !stage_set(shape)->batch[prec_index(b->precision)][0])
+  if (shape < 0 || shape >= NSHAPES || !stage_set(shape)->batch[variant_of(&b->cases[0], b->precision)][0])
     return fail(CT_ERR_ARG, "tile shape not available");
   if (shape == b->shape) return CT_OK;
   const int old = b->shape;
@@ -1080,7 +1128,7 @@ ct_status ct_batch_autotune(ct_batch* b, const void* U, void* U1, const void* bl
   ct_status s = CT_OK;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     float ms = -1.0f;
-    if (stage_set(sh)->batch[prec_index(b->precision)][0]) {
+    if (stage_set(sh)->batch[variant_of(&b->cases[0], b->precision)][0]) {
       if ((s = ct_batch_set_tile_shape(b, sh)) != CT_OK) return s;
       // stage 1 only: it reads U and writes the scratch state U1
       auto launch = [&]() { batch_launch(b, 1, U, nullptr, U1, blob, 0.5, b->stream); };
@@ -1155,6 +1203,7 @@ ct_status ct_batch_diagnostics(ct_batch* b, double* host_out) {
 ct_status ct_mlp_dataset(const ct_case* c, const double* U, int n, float* X, float* Y, float* M, void* stream) {
   ct_status s = validate(c, CT_FP64);
   if (s != CT_OK) return s;
+  if (c->bimodal) return fail(CT_ERR_ARG, "the surrogate's training data use one liquid set (bimodal = 0)");
   if (n < 0) return fail(CT_ERR_ARG, "n < 0");
   if (n == 0) return CT_OK;
   if (!U || !X || !Y || !M) return fail(CT_ERR_ARG, "null buffer");

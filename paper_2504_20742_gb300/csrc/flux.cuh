@@ -24,9 +24,9 @@ template <class T>
 struct FaceThermo {
   T g, H, ef, c2;
 };
-template <class T>
+template <class T, bool BI = false>
 __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
-  const T Yl = T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
+  const T Yl = BI ? T(k::YL3) * (q[8] + q[17]) : T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
   const T Ya = T(1) - q[4] - Yl - Ys;
   const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
   const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
@@ -41,11 +41,13 @@ __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
   return t;
 }
 
-// Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns.
-// Roe flux in direction DIR (0: normal velocity u, 1: normal velocity v) -> F[14].
-template <class T, int DIR>
+// Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns
+// (bimodal: 14..17 the second liquid set).  Roe flux in direction DIR (0: normal velocity u,
+// 1: normal velocity v) -> F[NFX].
+template <class T, int DIR, int NFX = NF>
 __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
-  const FaceThermo<T> tL = face_thermo(qL), tR = face_thermo(qR);
+  constexpr bool BI = NFX == NF_BI;
+  const FaceThermo<T> tL = face_thermo<T, BI>(qL), tR = face_thermo<T, BI>(qR);
   const T gL = tL.g, gR = tR.g, HL = tL.H, HR = tR.H, efL = tL.ef, efR = tR.ef, c2L = tL.c2, c2R = tR.c2;
   const T unL = DIR == 0 ? qL[1] : qL[2], utL = DIR == 0 ? qL[2] : qL[1];
   const T unR = DIR == 0 ? qR[1] : qR[2], utR = DIR == 0 ? qR[2] : qR[1];
@@ -93,7 +95,7 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   F[3] = fe;
   const T* qu = fm >= T(0) ? qL : qR;
 #pragma unroll
-  for (int f = 4; f < NF; ++f) F[f] = fm * qu[f];
+  for (int f = 4; f < NFX; ++f) F[f] = fm * qu[f];
 }
 
 // ---- viscous and diffusive face fluxes (Sec. 3.1 Eqs. (25)-(26), central differences) ----
@@ -132,14 +134,15 @@ __device__ __forceinline__ void cell_T_cp(T rho, T p, T Yv, T ml3, T ms3, T& Tg,
 
 // G (along +n) between the cells on the minus side (a) and the plus side (b), centres 1/ih
 // apart; q(f, side) returns primitive f (0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..12 moments,
-// 13 soot).  The face's total flux is the Roe flux minus G.  The energy flux carries
-// conduction, the work mu_e grad(|u|^2/2) and the enthalpy of the diffusing water
-// (against dry air).
-template <class T, class Q>
+// 13 soot, bimodal 14..17 the second liquid set).  The face's total flux is the Roe flux
+// minus G.  The energy flux carries conduction, the work mu_e grad(|u|^2/2) and the
+// enthalpy of the diffusing water (against dry air).
+template <class T, int NFX = NF, class Q>
 __device__ __forceinline__ void sub_diffusive_flux(const Q& q, T ih, T nu_t, T* F) {
+  constexpr bool BI = NFX == NF_BI;
   T Ta, cpa_, Tb, cpb;
-  cell_T_cp(q(0, 0), q(3, 0), q(4, 0), q(8, 0), q(12, 0), Ta, cpa_);
-  cell_T_cp(q(0, 1), q(3, 1), q(4, 1), q(8, 1), q(12, 1), Tb, cpb);
+  cell_T_cp(q(0, 0), q(3, 0), q(4, 0), BI ? q(8, 0) + q(17, 0) : q(8, 0), q(12, 0), Ta, cpa_);
+  cell_T_cp(q(0, 1), q(3, 1), q(4, 1), BI ? q(8, 1) + q(17, 1) : q(8, 1), q(12, 1), Tb, cpb);
   const T rho = T(0.5) * (q(0, 0) + q(0, 1)), Tf = T(0.5) * (Ta + Tb), pf = T(0.5) * (q(3, 0) + q(3, 1));
   const Transport<T> tr = transport(rho, Tf, pf, T(0.5) * (cpa_ + cpb), nu_t);
   const T ua = q(1, 0), ub = q(1, 1), va = q(2, 0), vb = q(2, 1);
@@ -149,12 +152,13 @@ __device__ __forceinline__ void sub_diffusive_flux(const Q& q, T ih, T nu_t, T* 
   F[1] -= Gu;
   F[2] -= Gv;
   F[4] -= Gy;
-  T Gl = T(0), Gs = T(0);
+  T Gl = T(0), Gs = T(0), gl3 = T(0);
 #pragma unroll
-  for (int f = 5; f < 14; ++f) {
+  for (int f = 5; f < NFX; ++f) {
     const T g = rDp * (q(f, 1) - q(f, 0));
-    if (f == 8) Gl = T(k::YL3) * g;
+    if (f == 8) { Gl = T(k::YL3) * g; gl3 = g; }
     if (f == 12) Gs = T(k::YS3) * g;
+    if (f == 17) Gl = T(k::YL3) * (gl3 + g);
     F[f] -= g;
   }
   const T ka = T(0.5) * (ua * ua + va * va), kb = T(0.5) * (ub * ub + vb * vb);

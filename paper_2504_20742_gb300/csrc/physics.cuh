@@ -13,6 +13,11 @@
 namespace ct {
 
 constexpr int NF = 14;
+// Bimodal liquid (Sec. 2.2: one moment set per nucleation mechanism): fields 14..17 hold
+// the droplets of heterogeneous origin, 5..8 those of homogeneous origin.
+constexpr int NF_BI = 18;
+template <bool BI>
+constexpr int nf_of() { return BI ? NF_BI : NF; }
 constexpr int NAUX = 11;
 
 // ---- constants (SI) ------------------------------------------------------------------
@@ -143,14 +148,16 @@ __device__ __forceinline__ R koop_log10(R daw) {
 template <class T>
 struct Prim {
   T rho, u, v, p, Tg, Yv, Yl, Ys, ml[4], ms[4], ns, cv, Rg, c2;
+  T mh[4];   // bimodal liquid: droplets of heterogeneous origin (set only when BI)
 };
 
-template <class T>
+// BI: the state has the 18 fields of the bimodal liquid; Y_l is the sum of both sets.
+template <class T, bool BI = false>
 __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   const T rho = U[0];
   // rho c_v straight from the conserved partial densities, then one reciprocal serves
   // 1/rho = (rho c_v) X and 1/c_v = rho^2 X, X = 1/(rho rho c_v)
-  const T rYl = T(k::YL3) * U[8], rYs = T(k::YS3) * U[12];
+  const T rYl = BI ? T(k::YL3) * (U[8] + U[17]) : T(k::YL3) * U[8], rYs = T(k::YS3) * U[12];
   const T rcv = (rho - U[4] - rYl - rYs) * T(k::CVA) + U[4] * T(k::CVV) + rYl * T(k::CL) + rYs * T(k::CS);
   const T X = trcp(rho * rcv);
   const T ir = rcv * X;
@@ -164,7 +171,13 @@ __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
     w.ms[q] = U[9 + q] * ir;
   }
   w.ns = U[13] * ir;
-  w.Yl = T(k::YL3) * w.ml[3];
+  if constexpr (BI) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w.mh[q] = U[14 + q] * ir;
+    w.Yl = T(k::YL3) * (w.ml[3] + w.mh[3]);
+  } else {
+    w.Yl = T(k::YL3) * w.ml[3];
+  }
   w.Ys = T(k::YS3) * w.ms[3];
   const T Ya = T(1) - w.Yv - w.Yl - w.Ys;
   const T e = U[3] * ir - T(0.5) * (w.u * w.u + w.v * w.v);
@@ -289,30 +302,34 @@ __device__ __forceinline__ T relax_slope(T Tsat, T Tg, T h, T Yv, T cv) {
 template <class T>
 struct Rates {
   T Jeff, rc_um, Gl, Gs, xl, xs;
+  T Jh, Gh, xh;   // bimodal: heterogeneous nucleation, growth and relaxation of the second set
 };
 
 // Cheap part of the source, shared by the plain and the surrogate paths: relaxation
 // limiter, freezing, moment assembly (Eq. 21), vapour sink (Eqs. 18, 25) and the
 // flux-aware limiters of reading J.  U: conserved stage input of the cell; acc (may be
-// null): its flux-only residual, so that the limiters act on A = U + dt acc.
-template <class T>
+// null): its flux-only residual, so that the limiters act on A = U + dt acc.  BI: the
+// bimodal liquid, whose second set (fields 14..17) takes the heterogeneous nucleation
+// r.Jh, grows at r.Gh and alone freezes by immersion.
+template <class T, bool BI = false>
 __device__ __forceinline__ void source_tail(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
                                             bool pres_l, bool pres_s, double lnSl, double lnSi, Rates<T> r, T* Q,
-                                            double* aux) {
+                                            double* aux, bool pres_h = false) {
   const T Tg = w.Tg, rho = w.rho;
   // growth over the stage: the exponential solution of the linearised exchange
-  const T xsum = dt * (r.xl + r.xs);
+  const T xsum = BI ? dt * (r.xl + r.xh + r.xs) : dt * (r.xl + r.xs);
   if (xsum > T(0)) {
     const T theta = -m_expm1(-xsum) / xsum;
     r.Gl *= theta;
     r.Gs *= theta;
+    if (BI) r.Gh *= theta;
   }
   if (aux) { aux[7] = double(r.Gl) * 1e-6; aux[8] = double(r.Gs) * 1e-6; }
 
-  // freezing, Eqs. (12)-(15) (reading H)
-  T Nf = T(0), rv = T(0), rf = T(0);
-  if (sc.freezing && pres_l && Tg < T(k::TREF)) {
-    rv = m_cbrt(w.ml[3] / w.ml[0]);   // um
+  // freezing, Eqs. (12)-(15) (reading H); with the bimodal liquid only droplets of
+  // heterogeneous origin carry a soot particle for immersion freezing
+  T Nf = T(0), rv = T(0), rf = T(0), Nfh = T(0), rvh = T(0), rfh = T(0);
+  if (sc.freezing && (pres_l || (BI && pres_h)) && Tg < T(k::TREF)) {
     const T daw = T(1) - T(m_exp(lnSl - lnSi));   // 1 - p_sat,i / p_sat,l
     T Js = T(0);
     if (daw >= T(0.26)) {
@@ -320,27 +337,52 @@ __device__ __forceinline__ void source_tail(const Prim<T>& w, const T* U, const 
       Js = m_exp(l10 * T(2.302585092994045684)) * T(1e6);
       if (aux) aux[9] = double(l10);
     }
-    T chi = w.ns / w.ml[0];
-    chi = chi > T(1) ? T(1) : chi;
-    const T rvm = rv * T(1e-6);
-    const T omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
-    if (aux) aux[10] = double(omega);
-    Nf = w.ml[0] * (-m_expm1(-omega * dt) / dt);   // first-order decay over the stage
-    rf = rv * T(k::RHOL_OVER_RHOS_CBRT);
+    if (pres_l) {
+      rv = m_cbrt(w.ml[3] / w.ml[0]);   // um
+      const T rvm = rv * T(1e-6);
+      T omega;
+      if (BI) {   // droplets of homogeneous origin hold no soot
+        omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm;
+      } else {
+        T chi = w.ns / w.ml[0];
+        chi = chi > T(1) ? T(1) : chi;
+        omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
+      }
+      if (aux) aux[10] = double(omega);
+      Nf = w.ml[0] * (-m_expm1(-omega * dt) / dt);   // first-order decay over the stage
+      rf = rv * T(k::RHOL_OVER_RHOS_CBRT);
+    }
+    if (BI && pres_h) {
+      rvh = m_cbrt(w.mh[3] / w.mh[0]);
+      const T rvm = rvh * T(1e-6);
+      T chi = w.ns / w.mh[0];
+      chi = chi > T(1) ? T(1) : chi;
+      const T omega = Js * T(k::FOUR_PI_3) * rvm * rvm * rvm + T(k::K_IMM * k::NS_SITE * 4.0 * k::PI * sc.rp2) * chi;
+      Nfh = w.mh[0] * (-m_expm1(-omega * dt) / dt);
+      rfh = rvh * T(k::RHOL_OVER_RHOS_CBRT);
+    }
   }
 
   // moment sources (per kg, scaled units), Eq. (21)
   const T jr = r.Jeff / rho;
-  T dml[4], dms[4];
+  T dml[4], dms[4], dmh[4];
   {
-    T rck = T(1), rvk = T(1), rfk = T(1);
+    const T jrh = BI ? r.Jh / rho : T(0);
+    T rck = T(1), rvk = T(1), rfk = T(1), rvhk = T(1), rfhk = T(1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       dml[q] = (q ? T(q) * w.ml[q - 1] * r.Gl : T(0)) + jr * rck - Nf * rvk;
-      dms[q] = (q ? T(q) * w.ms[q - 1] * r.Gs : T(0)) + Nf * rfk;
+      if (BI) {
+        dmh[q] = (q ? T(q) * w.mh[q - 1] * r.Gh : T(0)) + jrh * rck - Nfh * rvhk;
+        dms[q] = (q ? T(q) * w.ms[q - 1] * r.Gs : T(0)) + Nf * rfk + Nfh * rfhk;
+      } else {
+        dms[q] = (q ? T(q) * w.ms[q - 1] * r.Gs : T(0)) + Nf * rfk;
+      }
       rck *= r.rc_um;
       rvk *= rv;
       rfk *= rf;
+      rvhk *= rvh;
+      rfhk *= rfh;
     }
   }
   // limiters on the flux-updated stage state (reading J)
@@ -351,16 +393,24 @@ __device__ __forceinline__ void source_tail(const Prim<T>& w, const T* U, const 
 #pragma unroll
     for (int q = 0; q < 4; ++q) dml[q] = -(A(5 + q) * ir) * idt;
   }
+  if (BI && A(17) * ir + dt * dmh[3] <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dmh[q] = -(A(14 + q) * ir) * idt;
+  }
   if (A(12) * ir + dt * dms[3] <= T(0)) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) dms[q] = -(A(9 + q) * ir) * idt;
   }
-  T dYv = -(T(k::YL3) * dml[3] + T(k::YS3) * dms[3]);
+  T dYv = BI ? -(T(k::YL3) * (dml[3] + dmh[3]) + T(k::YS3) * dms[3]) : -(T(k::YL3) * dml[3] + T(k::YS3) * dms[3]);
   const T av = A(4) * ir;
   if (av + dt * dYv < T(0)) {
     const T th = av > T(0) ? av / (-dt * dYv) : T(0);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { dml[q] *= th; dms[q] *= th; }
+    for (int q = 0; q < 4; ++q) {
+      dml[q] *= th;
+      dms[q] *= th;
+      if (BI) dmh[q] *= th;
+    }
     dYv *= th;
   }
   Q[4] = rho * dYv;
@@ -368,6 +418,7 @@ __device__ __forceinline__ void source_tail(const Prim<T>& w, const T* U, const 
   for (int q = 0; q < 4; ++q) {
     Q[5 + q] = rho * dml[q];
     Q[9 + q] = rho * dms[q];
+    if (BI) Q[14 + q] = rho * dmh[q];
   }
 }
 
@@ -376,6 +427,7 @@ template <class T>
 struct Sat {
   double lnSl, lnSi, lnpv;
   bool pres_l, pres_s, active;
+  bool pres_h;   // bimodal: second liquid set present
 };
 
 template <class T>
@@ -383,6 +435,10 @@ __device__ __forceinline__ bool populations(const Prim<T>& w, bool& pres_l, bool
   pres_l = w.ml[0] > T(k::MU_MIN) && w.ml[1] > T(0) && w.ml[2] > T(0) && w.ml[3] > T(0);
   pres_s = w.ms[0] > T(k::MU_MIN) && w.ms[1] > T(0) && w.ms[2] > T(0) && w.ms[3] > T(0);
   return pres_l || pres_s;
+}
+template <class T>
+__device__ __forceinline__ bool present_h(const Prim<T>& w) {
+  return w.mh[0] > T(k::MU_MIN) && w.mh[1] > T(0) && w.mh[2] > T(0) && w.mh[3] > T(0);
 }
 
 // FP32 screen: a cell clearly below liquid saturation with no population has an exactly
@@ -394,28 +450,29 @@ __device__ __forceinline__ bool clearly_inactive(const Prim<T>& w) {
   return logf(pvf) - ln_psat_liq<float>(float(w.Tg)) < -1e-3f;
 }
 
-template <class T>
+template <class T, bool BI = false>
 __device__ __forceinline__ Sat<T> saturation(const Prim<T>& w, const SrcCase& sc) {
   Sat<T> s;
   populations(w, s.pres_l, s.pres_s);
+  s.pres_h = BI && present_h(w);
   // Eq. (1) in FP64: ln S = ln p_v - ln p_sat(T)
   double pv = double(w.rho) * double(w.Yv) * k::RV * double(w.Tg);
   pv = pv < 1e-30 ? 1e-30 : pv;
   s.lnpv = m_log(pv);
   s.lnSl = s.lnpv - prop_lnpl<double>(sc, double(w.Tg));
   s.lnSi = s.lnpv - prop_lnpi<double>(sc, double(w.Tg));
-  s.active = s.lnSl > 0.0 || s.pres_l || s.pres_s;
+  s.active = s.lnSl > 0.0 || s.pres_l || s.pres_s || s.pres_h;
   return s;
 }
 
 // Plain rates, Sec. 2.2.  ext (optional, the surrogate's training targets): 0 ln Jeff,
 // 1 ln r_crit/um, 2 G_l raw (um/s), 3 G_s raw, 4 1/tau_l, 5 1/tau_s, 6 ln J_hom,
 // 7 ln J_het,eff, 8 ln(1+phi), 9 T_sat,l - T.
-template <class T>
+template <class T, bool BI = false>
 __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& st, const SrcCase& sc, double* lnJ2,
                                                 double* aux, double* ext) {
   const T Tg = w.Tg, rho = w.rho;
-  Rates<T> r = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  Rates<T> r = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   // gas-phase properties (reading G)
   const T Yg = T(1) - w.Yl - w.Ys;
   const T Ya = Yg - w.Yv;
@@ -446,12 +503,14 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
                        2.0 * m_log(rhov) - m_log(k::RHOL);
     const double lnJhom = lnA - dGkT;
     const double lnJhet = lnA - k::FTHETA * dGkT;
-    double Jsum = m_exp(lnJhom);
+    const double Jhom = m_exp(lnJhom);
+    double Jsum = Jhom, Jhet = 0.0;
     lnJ2[0] = lnJhom;
     const double nsv = double(rho) * double(w.ns);
     if (sc.n_soot_ref > 0.0 && nsv > 0.0) {
       const double gate = nsv / sc.n_soot_ref;
-      Jsum += m_exp(lnJhet) * gate;
+      Jhet = m_exp(lnJhet) * gate;
+      Jsum += Jhet;
       lnJ2[1] = lnJhet + m_log(gate);
     }
     // Eq. (5) with alpha_crit from Young's law at r_crit (reading F)
@@ -465,7 +524,12 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
     const T alpha_c = lam / (rcT * (T(1) + T(3.78) * (T(1) - nu) * Knc * T(1.0 / k::PR)));
     const T phi = T(k::QC) * T(rhov) / alpha_c * m_sqrt(T(k::RV) * Tg * T(1.0 / (2.0 * k::PI))) *
                   (hfg * hfg / (T(k::RV) * Tg * Tg) - hfg / Tg);
-    r.Jeff = T(Jsum) / (T(1) + phi);
+    if (BI) {   // one moment set per mechanism
+      r.Jeff = T(Jhom) / (T(1) + phi);
+      r.Jh = T(Jhet) / (T(1) + phi);
+    } else {
+      r.Jeff = T(Jsum) / (T(1) + phi);
+    }
     r.rc_um = T(rc * 1e6);
     if (aux) { aux[2] = lnJ2[0]; aux[3] = lnJ2[1]; aux[5] = rc; aux[6] = double(phi); }
     if (ext) {
@@ -484,6 +548,13 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
     const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), prop_sigma<T>(sc, Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
     r.Gl = g.cond * g.D * T(1e6);
     r.xl = T(4.0 * k::PI * k::RHOL * 1e-12) * w.ml[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
+  }
+  if (BI && st.pres_h) {
+    if (!have_tsat_l && !st.pres_l) Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
+    const T r20 = m_sqrt(w.mh[2] / w.mh[0]) * T(1e-6);
+    const Growth<T> g = young_growth<T>(r20, Tg, Tsat_l, T(lnSl), prop_sigma<T>(sc, Tg), T(k::RHOL), hfg, lam, lbar, gam_g, cp_g);
+    r.Gh = g.cond * g.D * T(1e6);
+    r.xh = T(4.0 * k::PI * k::RHOL * 1e-12) * w.mh[2] * g.cond * relax_slope(Tsat_l, Tg, hfg, w.Yv, w.cv);
   }
   if (st.pres_s) {
     const T Tsat_i = prop_tsat<T, true>(sc, lnpv_t);
@@ -624,11 +695,15 @@ __device__ __forceinline__ bool equilibrium_source(const T* U, const T* acc, T d
   return true;
 }
 
-template <class T>
+template <class T, bool BI = false>
 __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const T* acc, T dt, const SrcCase& sc,
                                              T* Q, double* lnJ2, double* aux, double* ext = nullptr) {
 #pragma unroll
   for (int f = 4; f < 13; ++f) Q[f] = T(0);
+  if (BI) {
+#pragma unroll
+    for (int f = 14; f < 18; ++f) Q[f] = T(0);
+  }
   if (aux) {
 #pragma unroll
     for (int a = 0; a < NAUX; ++a) aux[a] = 0.0;
@@ -636,18 +711,20 @@ __device__ __forceinline__ bool phase_source(const Prim<T>& w, const T* U, const
   }
   lnJ2[0] = lnJ2[1] = -INFINITY;
   if (!sc.phase_change) return false;
-  if (sc.equilibrium) return equilibrium_source<T>(U, acc, dt, sc, Q, aux);
+  if constexpr (!BI) {   // one condensate population: not with the bimodal liquid
+    if (sc.equilibrium) return equilibrium_source<T>(U, acc, dt, sc, Q, aux);
+  }
   if (!aux && !ext) {
     // the FP32 screen's margin (1e-3 in ln S_l) is far above its rounding error, so a
     // screened cell is inactive in FP64 too: both paths give the same (zero) source
     bool pl, ps;
-    if (!populations(w, pl, ps) && clearly_inactive(w)) return false;
+    if (!populations(w, pl, ps) && !(BI && present_h(w)) && clearly_inactive(w)) return false;
   }
-  const Sat<T> st = saturation(w, sc);
+  const Sat<T> st = saturation<T, BI>(w, sc);
   if (aux) { aux[0] = st.lnSl; aux[1] = st.lnSi; aux[4] = st.active ? 1.0 : 0.0; }
   if (!st.active) return false;
-  const Rates<T> r = plain_rates<T>(w, st, sc, lnJ2, aux, ext);
-  source_tail<T>(w, U, acc, dt, sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, aux);
+  const Rates<T> r = plain_rates<T, BI>(w, st, sc, lnJ2, aux, ext);
+  source_tail<T, BI>(w, U, acc, dt, sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, aux, st.pres_h);
   return true;
 }
 

@@ -59,8 +59,8 @@ struct DevCase {
   double p0, T0, Yv0, cp0, gam0;       // nozzle inlet mixture
   float fdx, fidx, fdr, fidr, fwall_len, farea_a, fixt;   // FP32 copies of the geometry
   SrcCase sc;
-  const double* inflow;   // nr x NF (plume)
-  const double* amb;      // NF
+  const double* inflow;   // nr x nf (plume; nf = 18 for the bimodal liquid, else 14)
+  const double* amb;      // nf
   WsHeader* hdr;
   double* partials;       // nblocks x NPART, tile by * tiles_x + bx
   unsigned int* row_count;  // tiles_y arrival tickets (zero between launches)
@@ -78,8 +78,8 @@ struct Tile {
   static constexpr int NT = (NFACE + 31) / 32 * 32;
   template <class T>
   static constexpr int minb() { return sizeof(T) == 4 && NT <= 320 ? 2 : 1; }
-  template <class T>
-  static constexpr size_t smem() { return sizeof(T) * (size_t)NF * (HX * HY + 3 * NFACE); }
+  template <class T, int NFX = NF>
+  static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + 3 * NFACE); }
 };
 // thread count of the auxiliary kernels (time step of a given state)
 constexpr int NT_AUX = 288;
@@ -100,7 +100,7 @@ __device__ __forceinline__ Geo<double> geo_of(const DevCase& d, double) {
 // Conserved state at (i, j), i in [-2, nx+1], j in [-2, nr+1], not both outside.
 // Out of line on purpose: keeps the nozzle inlet's FP64 arithmetic from being hoisted into
 // the interior path of the FP32 kernels.
-template <class T>
+template <class T, int NFX = NF>
 __device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__ U, size_t N, int i, int j,
                                         T* u14) {
   const int nx = dc.nx, nr = dc.nr;
@@ -108,7 +108,7 @@ __device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__
     if (dc.bc_xlo == 1) {   // wall: mirror
       const size_t n = (size_t)j * nx + (-i - 1);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+      for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
       u14[1] = -u14[1];
     } else if (dc.geom == 0) {   // total-condition subsonic inlet, interior velocity
       const size_t n = (size_t)j * nx;
@@ -118,9 +118,11 @@ __device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__
       const double p = dc.p0 * pow(Tg / dc.T0, dc.gam0 / (dc.gam0 - 1.0));
       const double z[4] = {0, 0, 0, 0};
       prim_to_cons<T>(p, Tg, u, 0.0, dc.Yv0, z, z, 0.0, u14);
+#pragma unroll
+      for (int f = NF; f < NFX; ++f) u14[f] = T(0);   // no liquid of heterogeneous origin
     } else {   // plume inflow profile
 #pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = T(dc.inflow[j * NF + f]);
+      for (int f = 0; f < NFX; ++f) u14[f] = T(dc.inflow[j * NFX + f]);
     }
     return;
   }
@@ -128,33 +130,33 @@ __device__ __noinline__ void load_ghost(const DevCase& dc, const T* __restrict__
     const int ii = dc.bc_xhi == 1 ? 2 * nx - 1 - i : nx - 1;
     const size_t n = (size_t)j * nx + ii;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     if (dc.bc_xhi == 1) u14[1] = -u14[1];
     return;
   }
   if (j < 0) {   // axis: mirror with rho*v negated
     const size_t n = (size_t)(-j - 1) * nx + i;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+    for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     u14[2] = -u14[2];
     return;
   }
   if (j >= nr) {
     if (dc.bc_rhi == 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = T(dc.amb[f]);
+      for (int f = 0; f < NFX; ++f) u14[f] = T(dc.amb[f]);
     } else {
       const int jj = dc.bc_rhi == 1 ? 2 * nr - 1 - j : nr - 1;
       const size_t n = (size_t)jj * nx + i;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+      for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
       if (dc.bc_rhi == 1) u14[2] = -u14[2];
     }
     return;
   }
   const size_t n = (size_t)j * nx + i;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) u14[f] = U[f * N + n];
+  for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
 }
 
 __device__ __forceinline__ double area_q1d(const DevCase& dc, double x) {
@@ -461,16 +463,17 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
 // records.  All threads of the CTA call this.  STAGE 1: Uout = Uin + dt L(Uin).
 // STAGE 2: Uout = (Un + Uin + dt L(Uin))/2 (Uout may be Un); the last tile of the case to
 // finish reduces the partials and publishes cfl * (stable step) as the next time step.
-template <class TL, class T, int STAGE, bool SURR>
+template <class TL, class T, int STAGE, bool SURR, bool BI = false>
 __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, int tile, const T* __restrict__ Uin,
                                            const T* Un, T* Uout, const unsigned char* __restrict__ blob,
                                            unsigned char* smem_raw, double cfl, TcCtx* tcx) {
   constexpr int TX = TL::TX, TY = TL::TY, HX = TL::HX, HY = TL::HY, NT = TL::NT, NCELL = TL::NCELL;
   constexpr int NFACE = TL::NFACE;
+  constexpr int NFX = nf_of<BI>();   // fields of the state (18 with the bimodal liquid)
   T (*qs)[HY][HX] = reinterpret_cast<T (*)[HY][HX]>(smem_raw);                      // primitives
-  T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NF * HX * HY);   // face fluxes
-  T (*fL)[NFACE] = fb + NF;        // reconstructed left state of each face
-  T (*fR)[NFACE] = fb + 2 * NF;    // reconstructed right state of each face
+  T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);   // face fluxes
+  T (*fL)[NFACE] = fb + NFX;       // reconstructed left state of each face
+  T (*fR)[NFACE] = fb + 2 * NFX;   // reconstructed right state of each face
   __shared__ double red[NT / 32][NPART];
   __shared__ double fin[NPART];
 
@@ -486,7 +489,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   // of them are issued before any is converted, so their latencies overlap.
   {
     constexpr int NA = (HX * HY + NT - 1) / NT;
-    T u14[NA][NF];
+    T u14[NA][NFX];
     int kind[NA];   // 0 skip, 1 interior, 2 ghost
 #pragma unroll
     for (int r = 0; r < NA; ++r) {
@@ -500,7 +503,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       if (kind[r] == 1) {
         const size_t n = (size_t)j * nx + i;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) u14[r][f] = Uin[f * N + n];
+        for (int f = 0; f < NFX; ++f) u14[r][f] = Uin[f * N + n];
       }
     }
 #pragma unroll
@@ -509,13 +512,13 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const int p = tid + r * NT;
       const int hi = p % HX, hj = p / HX;
       if (kind[r] == 2) {   // out of line, through its own array: u14 stays in registers
-        T g14[NF];
-        load_ghost<T>(dc, Uin, N, i0 + hi - 2, j0 + hj - 2, g14);
+        T g14[NFX];
+        load_ghost<T, NFX>(dc, Uin, N, i0 + hi - 2, j0 + hj - 2, g14);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) u14[r][f] = g14[f];
+        for (int f = 0; f < NFX; ++f) u14[r][f] = g14[f];
       }
       Prim<T> w;
-      cons_to_prim<T>(u14[r], w);
+      cons_to_prim<T, BI>(u14[r], w);
       qs[0][hj][hi] = w.rho;
       qs[1][hj][hi] = w.u;
       qs[2][hj][hi] = w.v;
@@ -527,6 +530,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         qs[9 + q][hj][hi] = w.ms[q];
       }
       qs[13][hj][hi] = w.ns;
+      if (BI) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) qs[14 + q][hj][hi] = w.mh[q];
+      }
     }
   }
   __syncthreads();
@@ -538,7 +545,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const int i = i0 + c, j = j0 + hj;
     if (i > nx || j >= nr) continue;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NFX; ++f) {
       const T am = qs[f][hj + 2][c + 1], a0 = qs[f][hj + 2][c + 2], a1 = qs[f][hj + 2][c + 3];
       const T hs = vl_half_slope(a0 - am, a1 - a0);
       if (c < TX) fL[f][hj * (TX + 1) + c + 1] = a0 + hs;
@@ -552,27 +559,32 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const int fx = p % (TX + 1), hj = p / (TX + 1);
     const int i = i0 + fx, j = j0 + hj;
     if (i > nx || j >= nr) continue;
-    T qL[NF], qR[NF], F[NF];
+    T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NFX; ++f) {
       qL[f] = fL[f][p];
       qR[f] = fR[f][p];
     }
-    roe_flux<T, 0>(qL, qR, F);
+    roe_flux<T, 0, NFX>(qL, qR, F);
     // walls are adiabatic, impermeable and slip: nothing diffuses through them
     if (dc.viscous && !((i == 0 && dc.bc_xlo == 1) || (i == nx && dc.bc_xhi == 1))) {
       const auto q = [&](int f, int side) -> T { return qs[f][hj + 2][fx + 1 + side]; };
-      sub_diffusive_flux<T>(q, g.idx, g.nu_t, F);
+      sub_diffusive_flux<T, NFX>(q, g.idx, g.nu_t, F);
     }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
+    for (int f = 0; f < NFX; ++f) fb[f][p] = F[f];
   }
   __syncthreads();
 
   const int ci = tid % TX, cj = tid / TX;
   const int i = i0 + ci, j = j0 + cj;
   const bool cell = tid < NCELL && i < nx && j < nr;
-  T acc[NF];
+  T acc[NFX];
+  // water carried by a face flux: vapour, liquid (both sets) and ice
+  const auto water_flux = [&](int f) -> T {
+    const T l3 = BI ? fb[8][f] + fb[17][f] : fb[8][f];
+    return fb[4][f] + T(k::YL3) * l3 + T(k::YS3) * fb[12][f];
+  };
   T bm = T(0), bw = T(0), be = T(0);   // boundary inflow rates of this cell's faces
   T area_w = T(0), area_e = T(0), vol = T(0);
   if (cell) {
@@ -594,15 +606,15 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       vol = area_w * g.dx;
     }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) acc[f] = cw * fb[f][w] - ce * fb[f][e];
+    for (int f = 0; f < NFX; ++f) acc[f] = cw * fb[f][w] - ce * fb[f][e];
     if (i == 0) {
       bm += area_w * fb[0][w];
-      bw += area_w * (fb[4][w] + T(k::YL3) * fb[8][w] + T(k::YS3) * fb[12][w]);
+      bw += area_w * water_flux(w);
       be += area_w * fb[3][w];
     }
     if (i == nx - 1) {
       bm -= area_e * fb[0][e];
-      bw -= area_e * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
+      bw -= area_e * water_flux(e);
       be -= area_e * fb[3][e];
     }
   }
@@ -615,7 +627,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const int ii = i0 + hi, jj = j0 + c;
       if (ii >= nx || jj > nr) continue;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NFX; ++f) {
         const T am = qs[f][c + 1][hi + 2], a0 = qs[f][c + 2][hi + 2], a1 = qs[f][c + 3][hi + 2];
         const T hs = vl_half_slope(a0 - am, a1 - a0);
         if (c < TY) fL[f][(c + 1) * TX + hi] = a0 + hs;
@@ -628,19 +640,19 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const int hi = p % TX, fy = p / TX;
       const int ii = i0 + hi, jj = j0 + fy;
       if (ii >= nx || jj > nr) continue;
-      T qL[NF], qR[NF], F[NF];
+      T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NFX; ++f) {
         qL[f] = fL[f][p];
         qR[f] = fR[f][p];
       }
-      roe_flux<T, 1>(qL, qR, F);
+      roe_flux<T, 1, NFX>(qL, qR, F);
       if (dc.viscous && !(jj == nr && dc.bc_rhi == 1)) {
         const auto q = [&](int f, int side) -> T { return qs[f][fy + 1 + side][hi + 2]; };
-        sub_diffusive_flux<T>(q, g.idr, g.nu_t, F);
+        sub_diffusive_flux<T, NFX>(q, g.idr, g.nu_t, F);
       }
 #pragma unroll
-      for (int f = 0; f < NF; ++f) fb[f][p] = F[f];
+      for (int f = 0; f < NFX; ++f) fb[f][p] = F[f];
     }
     __syncthreads();
   }
@@ -653,19 +665,19 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   for (int f = 0; f < NF; ++f) rmax[f] = T(0);
   T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
   int nactive = 0, nbad = 0, nfallback = 0, ntimeout = 0;
-  T u14[NF];
+  T u14[NFX];
   Prim<T> w;
   if (cell) {
     const size_t n = (size_t)j * nx + i;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-    cons_to_prim<T>(u14, w);
+    for (int f = 0; f < NFX; ++f) u14[f] = Uin[f * N + n];
+    cons_to_prim<T, BI>(u14, w);
     if (dc.geom == 1) {
       const T ijh = trcp(T(j) + T(0.5));
       const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
       const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NFX; ++f) {
         T Fs = fb[f][cj * TX + ci], Fn = fb[f][(cj + 1) * TX + ci];
         if (wall && j == dc.jw - 1) Fn = f == 2 ? w.p : T(0);
         if (wall && j == dc.jw) Fs = f == 2 ? w.p : T(0);
@@ -681,22 +693,26 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         const T An = T(nr) * g.dr * g.dx;
         const int e = (cj + 1) * TX + ci;
         bm -= An * fb[0][e];
-        bw -= An * (fb[4][e] + T(k::YL3) * fb[8][e] + T(k::YS3) * fb[12][e]);
+        bw -= An * water_flux(e);
         be -= An * fb[3][e];
       }
     } else {
       acc[1] += w.p * tdiv(area_e - area_w, vol);
     }
     // phase-change source limited on the flux-updated state
-    T Q[NF];
+    T Q[NFX];
     double lnJ2[2];
     if (!SURR) {
-      const bool act = phase_source<T>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
+      const bool act = phase_source<T, BI>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
       nactive = act ? 1 : 0;
       lnJh = T(lnJ2[0]);
       lnJt = T(lnJ2[1]);
 #pragma unroll
       for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+      if (BI) {
+#pragma unroll
+        for (int f = 14; f < 18; ++f) acc[f] += Q[f];
+      }
     }
   }
   if (SURR)
@@ -705,27 +721,32 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   if (cell) {
     const size_t n = (size_t)j * nx + i;
     // RK combine
-    T out[NF];
+    T out[NFX];
     if (STAGE == 1) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) out[f] = u14[f] + dt * acc[f];
+      for (int f = 0; f < NFX; ++f) out[f] = u14[f] + dt * acc[f];
     } else {
       const T idt = trcp(dt);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NFX; ++f) {
         const T un = Un[f * N + n];
         out[f] = T(0.5) * un + T(0.5) * (u14[f] + dt * acc[f]);
-        rmax[f] = m_fabs(out[f] - un) * idt;
+        const T rf = m_fabs(out[f] - un) * idt;
+        if (f < NF) {
+          rmax[f] = rf;
+        } else {   // the second liquid set shares the residual slots of the first
+          rmax[f - 9] = rf > rmax[f - 9] ? rf : rmax[f - 9];
+        }
       }
     }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NFX; ++f) {
       Uout[f * N + n] = out[f];
       nbad += finite_bits(out[f]) ? 0 : 1;
     }
     if (STAGE == 2) {
       Prim<T> wn;
-      cons_to_prim<T>(out, wn);
+      cons_to_prim<T, BI>(out, wn);
       const T c = m_sqrt(wn.c2);
       T rate = (m_fabs(wn.u) + c) * g.idx;
       if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
@@ -735,7 +756,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       }
       dtmin = trcp(rate);   // times cfl at the end
       pM = vol * out[0];
-      pW = vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]);
+      pW = vol * (out[4] + T(k::YL3) * (BI ? out[8] + out[17] : out[8]) + T(k::YS3) * out[12]);
       pE = vol * out[3];
     }
   }
@@ -821,7 +842,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 // Register budget from __launch_bounds__: the register file is split between the SM's four
 // schedulers, so 18 warps (two CTAs of 288 threads) leave 96 registers per thread and 9
 // warps (one FP64 CTA) 168; a larger cap fails at launch.
-template <class TL, class T, int STAGE, bool SURR>
+template <class TL, class T, int STAGE, bool SURR, bool BI = false>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -836,7 +857,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     tcx.wphase = 0;
     tcx.ready = true;
   }
-  stage_tile<TL, T, STAGE, SURR>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
+  stage_tile<TL, T, STAGE, SURR, BI>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
                                  smem_raw, dc.cfl, &tcx);
   if (SURR) tc_release(tcx.tmem);
 }
@@ -868,7 +889,7 @@ struct BatchCounters {
   unsigned int exited;
 };
 
-template <class TL, class T, int STAGE, bool SURR>
+template <class TL, class T, int STAGE, bool SURR, bool BI = false>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     k_batch_stage(const __grid_constant__ BatchTable bt, BatchCounters* __restrict__ ctr, const T* __restrict__ Uin,
                   const T* Un, T* Uout, const unsigned char* __restrict__ blob, double cfl, int max_tiles) {
@@ -901,7 +922,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     const int k = bt.case_of[slot];
     const int lt = t - bt.tile_start[slot], tx = bt.tiles_x[k];
     const long long off = bt.state_off[k];
-    stage_tile<TL, T, STAGE, SURR>(bt.cases[k], lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off,
+    stage_tile<TL, T, STAGE, SURR, BI>(bt.cases[k], lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off,
                                    blob, smem_raw, cfl, &tcx);
     __syncthreads();
   }
@@ -917,14 +938,16 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
 }
 
 // ---- kernels of one tile shape, as seen by the host ---------------------------------------
-// Precision index p: 0 FP64, 1 FP32, 2 FP32 + surrogate.  A null entry: that combination
-// does not fit the shared memory of an SM.
+// Kernel variant index p: 0 FP64, 1 FP32, 2 FP32 + surrogate, 3 FP64 with the bimodal
+// liquid, 4 FP32 with the bimodal liquid.  A null entry: that combination does not fit the
+// shared memory of an SM.
+constexpr int NVARIANT = 5;
 struct StageSet {
   int tx, ty, nt;
-  size_t smem[3];
-  int minb[3];
-  const void* stage[3][2];   // k_stage, stages 1 and 2
-  const void* batch[3][2];   // k_batch_stage (FP32 and FP32 + surrogate only)
+  size_t smem[NVARIANT];
+  int minb[NVARIANT];
+  const void* stage[NVARIANT][2];   // k_stage, stages 1 and 2
+  const void* batch[NVARIANT][2];   // k_batch_stage (FP32 variants only)
 };
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
 
@@ -953,6 +976,25 @@ StageSet make_stage_set() {
   s.batch[2][0] = (const void*)k_batch_stage<TL, float, 1, true>;
   s.batch[2][1] = (const void*)k_batch_stage<TL, float, 2, true>;
   return s;
+}
+
+// The bimodal variants (3, 4) of a shape, instantiated in a translation unit of their own.
+template <class TL>
+void add_bimodal_variants(StageSet& s) {
+  s.smem[3] = TL::template smem<double, NF_BI>();
+  s.smem[4] = TL::template smem<float, NF_BI>();
+  s.minb[3] = TL::template minb<double>();
+  s.minb[4] = TL::template minb<float>();
+  if constexpr (TL::template smem<double, NF_BI>() <= SMEM_LIMIT) {
+    s.stage[3][0] = (const void*)k_stage<TL, double, 1, false, true>;
+    s.stage[3][1] = (const void*)k_stage<TL, double, 2, false, true>;
+  }
+  if constexpr (TL::template smem<float, NF_BI>() <= SMEM_LIMIT) {
+    s.stage[4][0] = (const void*)k_stage<TL, float, 1, false, true>;
+    s.stage[4][1] = (const void*)k_stage<TL, float, 2, false, true>;
+    s.batch[4][0] = (const void*)k_batch_stage<TL, float, 1, false, true>;
+    s.batch[4][1] = (const void*)k_batch_stage<TL, float, 2, false, true>;
+  }
 }
 
 // the tile shapes the library is built with (one translation unit each)

@@ -8,7 +8,8 @@ from . import _lib as L
 
 
 class Solver:
-    """One case on one GPU.  State tensors are (14, nr, nx), float64 (CT_FP64) or float32."""
+    """One case on one GPU.  State tensors are (nf, nr, nx), float64 (CT_FP64) or float32;
+    nf = 14, or 18 with the bimodal liquid."""
 
     def __init__(self, case: dict, ufac_rows=None, precision: int = L.CT_FP64, device="cuda:0",
                  stream: torch.cuda.Stream | None = None):
@@ -19,7 +20,8 @@ class Solver:
         self.nr = int(case["nr"]) if int(case["geom"]) == 1 else 1
         self.dtype = torch.float64 if precision == L.CT_FP64 else torch.float32
         self.stream = stream or torch.cuda.current_stream(self.device)
-        self.U = torch.zeros((L.NF, self.nr, self.nx), dtype=self.dtype, device=self.device)
+        self.nf = L.nfields(self.case)
+        self.U = torch.zeros((self.nf, self.nr, self.nx), dtype=self.dtype, device=self.device)
         self.U1 = torch.zeros_like(self.U)
         nbytes = L.ct_workspace_bytes(self.case, precision)
         if nbytes == 0:
@@ -66,7 +68,7 @@ class Solver:
 
 class Batch:
     """Many axisymmetric cases stepped together by the persistent, graph-captured kernel.
-    The batch state is one float32 tensor; `state(k)` views case k as (14, nr, nx)."""
+    The batch state is one float32 tensor; `state(k)` views case k as (nf, nr, nx)."""
 
     def __init__(self, cases: list, ufac_rows: list | None = None, precision: int = L.CT_FP32_MLP,
                  device="cuda:0", stream: torch.cuda.Stream | None = None, blob: torch.Tensor | None = None):
@@ -90,7 +92,7 @@ class Batch:
         off = 0
         for c in self.cases:
             self.offsets.append(off)
-            off += L.NF * int(c["nx"]) * int(c["nr"])
+            off += L.nfields(c) * int(c["nx"]) * int(c["nr"])
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -101,7 +103,8 @@ class Batch:
     def state(self, k: int) -> torch.Tensor:
         c = self.cases[k]
         nx, nr = int(c["nx"]), int(c["nr"])
-        return self.U[self.offsets[k]:self.offsets[k] + L.NF * nx * nr].view(L.NF, nr, nx)
+        nf = L.nfields(c)
+        return self.U[self.offsets[k]:self.offsets[k] + nf * nx * nr].view(nf, nr, nx)
 
     def init_state(self, cfl: float = 0.5):
         L.ct_batch_init_state(self.handle, self.U, cfl)

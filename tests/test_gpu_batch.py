@@ -54,10 +54,11 @@ def _single(P, c, uf, prec, nsteps, blob=None, shape=-1):
     return s.U.clone(), d
 
 
-@pytest.mark.parametrize("prec,viscous", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
-def test_every_tile_shape_gives_the_same_state(P, blob, prec, viscous):
+@pytest.mark.parametrize("prec,viscous,bimodal", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 1, 0), (1, 1, 0),
+                                                  (0, 0, 1), (1, 1, 1)])
+def test_every_tile_shape_gives_the_same_state(P, blob, prec, viscous, bimodal):
     c, uf = cases.mixing_layer_case(nx=100, nr=44)
-    c = dict(c, viscous=viscous, nu_t=0.05)
+    c = dict(c, viscous=viscous, nu_t=0.05, bimodal=bimodal)
     ref, d0 = _single(P, c, uf, prec, 12, blob, 0)
     assert d0[8] == 0 and d0[7] > 0
     for shape in range(1, P.ct_tile_shape_count()):
@@ -166,3 +167,22 @@ def test_batch_with_optional_model_parts_matches_single_cases(P):
         ref, d = _single(P, c, uf, P.CT_FP32, 5)
         assert torch.equal(b.state(k), ref), (k, c.get("viscous"), c.get("tables"), c.get("equilibrium"))
         assert db[k, 0] == d[0]
+
+
+def test_bimodal_batch_matches_single_cases(P):
+    """A batch of bimodal cases (18-field states) steps each case as the single-case kernel
+    does; a batch may not mix layouts."""
+    bc = [(dict(c, bimodal=1), uf) for c, uf in _small_batch(3)]
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32)
+    b.init_state(0.5)
+    b.step(5, 0.5)
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0)
+    for k, (c, uf) in enumerate(bc):
+        assert b.state(k).shape[0] == 18
+        ref, d = _single(P, c, uf, P.CT_FP32, 5)
+        assert torch.equal(b.state(k), ref), k
+        assert db[k, 0] == d[0]
+    mixed = [bc[0][0], dict(bc[1][0], bimodal=0)]
+    with pytest.raises(P.ContrailError):
+        P.Batch(mixed, [bc[0][1], bc[1][1]], precision=P.CT_FP32)

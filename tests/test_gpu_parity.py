@@ -52,6 +52,11 @@ def _equilibrium(cu):
     return dict(c, equilibrium=1), uf
 
 
+def _bimodal(cu):
+    c, uf = cu
+    return dict(c, bimodal=1), uf
+
+
 # Well-conditioned cases: 100 steps at 1e-9.  The nucleating mixing layers amplify a
 # rounding-level perturbation of the oracle's own input to O(1) within about 50 steps
 # (pinned in test_oracle_solver.py); they are checked by shadowing in
@@ -74,6 +79,12 @@ CASES = {
     "freezing96x40_equilibrium": (lambda: _equilibrium(cases.freezing_case()), 100),
     "mixing96x40_equilibrium": (lambda: _equilibrium(cases.mixing_layer_case()), 100),
     "nozzle400_equilibrium": (lambda: (dict(cases.nozzle_case(nx=400), equilibrium=1), None), 100),
+    # bimodal liquid (Sec. 2.2: one moment set per nucleation mechanism)
+    "freezing96x40_bimodal": (lambda: _bimodal(cases.freezing_case()), 100),
+    "plume256x64_bimodal": (lambda: _bimodal(cases.plume_case(nx=256, nr=64)), 100),
+    "freezing_ragged_77x29_bimodal_viscous": (lambda: _bimodal(_viscous(cases.freezing_case(nx=77, nr=29), 0.05)), 100),
+    "mixing96x40_bimodal_2steps": (lambda: _bimodal(cases.mixing_layer_case()), 2),
+    "closed_box_bimodal_2steps": (lambda: _bimodal(cases.closed_box_case()), 2),
 }
 
 CHAOTIC = {
@@ -81,6 +92,8 @@ CHAOTIC = {
     "mixing96x40_viscous": lambda: _viscous(cases.mixing_layer_case(), 0.05),
     "mixing_ragged_77x29": lambda: cases.mixing_layer_case(nx=77, nr=29),
     "closed_box": lambda: cases.closed_box_case(),
+    "mixing96x40_bimodal": lambda: _bimodal(cases.mixing_layer_case()),
+    "closed_box_bimodal": lambda: _bimodal(cases.closed_box_case()),
 }
 
 
@@ -318,3 +331,111 @@ def test_step_host_end_to_end(P):
     ref.init_state(0.5)
     ref.step(10, 0.5)
     assert np.array_equal(hout.numpy(), ref.state64())
+
+
+def _split_liquid(U14, frac=0.5):
+    """18-field state: a fraction of each cell's droplets moved into the second set (the
+    flow sees only the total liquid, so the state is otherwise the same)."""
+    U = np.zeros((18,) + U14.shape[1:])
+    U[:14] = U14
+    U[14:18] = frac * U14[5:9]
+    U[5:9] = U14[5:9] - U[14:18]
+    return U
+
+
+def test_bimodal_split_population_parity(P):
+    """Both liquid sets populated from the start (a share of the seeded droplets moved into
+    the second set): evaporation, Koop freezing of both sets and immersion freezing of the
+    second, 100 FP64 steps against the oracle."""
+    c, uf = _bimodal(cases.freezing_case())
+    o1 = O.Oracle(dict(c, bimodal=0), uf)
+    U0 = _split_liquid(o1.init_state(), 0.375)
+    o = O.Oracle(c, uf)
+    Uo = U0.copy()
+    do = o.step(Uo, 100, 0.5)
+    s = P.Solver(c, uf)
+    s.load_state(torch.tensor(U0), 0.5)
+    s.step(100, 0.5)
+    dg = s.diagnostics()
+    e = field_rel_err(s.state64(), Uo)
+    assert np.all(e <= TOL), report(e)
+    assert np.abs(Uo[14:18]).max() > 0 and do[-1, 7] == dg[7]
+    for k in (1, 2, 3):
+        assert dg[k] == pytest.approx(do[-1, k], rel=1e-12)
+
+
+def _random_bimodal_states(n, seed):
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_source import _random_states
+    U = _random_states(n, seed=seed)
+    V = _random_states(n, seed=seed + 100)
+    out = np.zeros((n, 18))
+    out[:, :14] = U
+    # a second, independent droplet population of heterogeneous origin; the energy is
+    # unchanged, so the temperature adjusts to the added liquid
+    out[:, 14:18] = 0.3 * V[:, 5:9] * (U[:, :1] / V[:, :1])
+    return out
+
+
+def test_source_batch_parity_bimodal(P):
+    """Pointwise source with two liquid sets, FP64, through the C ABI (random states)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_source import _case
+    U = _random_bimodal_states(4000, 21)
+    c = dict(_case(), bimodal=1)
+    for dt in (1e-7, 1e-5):
+        Qo, ao = O.source_batch(c, U, dt)
+        Ud = torch.tensor(U, device="cuda")
+        Q = torch.zeros_like(Ud)
+        aux = torch.zeros((U.shape[0], 11), dtype=torch.float64, device="cuda")
+        P.ct_source_batch(c, P.CT_FP64, Ud, U.shape[0], dt, Q, aux)
+        Qg, ag = Q.cpu().numpy(), aux.cpu().numpy()
+        assert np.abs(Qo[:, 14:18]).max() > 0
+        scale = np.abs(Qo).max(axis=0) + 1e-300
+        rel = np.abs(Qg - Qo) / (np.abs(Qo) + 1e-9 * scale)
+        assert np.all(rel <= 1e-8), (rel.max(axis=0))
+        assert np.array_equal(ao[:, 4], ag[:, 4])
+
+
+def test_bimodal_spectra_parity(P):
+    """Derived 13..18 of the oracle's own bimodal state (after 30 steps of the seeded mixing
+    layer, both sets populated): the lognormal spectrum of each population."""
+    c, uf = _bimodal(cases.mixing_layer_case())
+    o = O.Oracle(c, uf)
+    Uo = o.init_state()
+    o.step(Uo, 30, 0.5)
+    s = P.Solver(c, uf)
+    s.load_state(torch.tensor(Uo), 0.5)
+    for which in (13, 14, 15, 16, 17, 18):
+        g = s.derived(which, 1e-5).cpu().numpy()
+        r = o.derived(Uo, which, 1e-5)
+        assert np.count_nonzero(r) > 100, which
+        assert np.allclose(g, r, rtol=1e-12, atol=0.0), which
+
+
+def test_bimodal_fp32_against_oracle(P):
+    """FP32 transport with FP64 islands, two liquid sets and the diffusive fluxes, 100 steps
+    of the split freezing plume, field by field against the FP64 oracle (the unimodal
+    counterpart is test_fp32_viscous_against_oracle)."""
+    c, uf = _bimodal(_viscous(cases.freezing_case(), 0.05))
+    U0 = _split_liquid(O.Oracle(dict(c, bimodal=0), uf).init_state(), 0.375)
+    o = O.Oracle(c, uf)
+    Uo = U0.copy()
+    o.step(Uo, 100, 0.5)
+    s = P.Solver(c, uf, precision=P.CT_FP32)
+    s.load_state(torch.tensor(U0), 0.5)
+    s.step(100, 0.5)
+    e = field_rel_err(s.state64(), Uo)
+    print("FP32 bimodal freezing plume, 100 steps:", report(e))
+    assert np.all(e[[0, 1, 3, 4, 13]] <= 1e-4), report(e)
+    assert np.all(e <= 5e-3), report(e)
+
+
+def test_bimodal_rejected_with_the_surrogate_and_equilibrium(P):
+    c, uf = _bimodal(cases.freezing_case(nx=32, nr=16))
+    with pytest.raises(P.ContrailError):
+        P.Solver(c, uf, precision=P.CT_FP32_MLP)
+    with pytest.raises(P.ContrailError):
+        P.Solver(dict(c, equilibrium=1), uf)
