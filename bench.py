@@ -74,28 +74,40 @@ def _workload(name):
         if name == "fp32":
             return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 transport + FP64 islands", 1
         return c, uf, "axisymmetric coaxial plume 4096x1024, FP32 + BF16 tensor-core source surrogate", 2
-    if name in ("active_fp64", "active_fp64_tables"):
+    if name == "fp64_bimodal":
+        c, uf = cases.plume_case()
+        return (dict(c, bimodal=1), uf,
+                "axisymmetric coaxial plume 1024x256, FP64, bimodal liquid (two moment sets, 18 fields)", 0)
+    if name in ("active_fp64", "active_fp64_tables", "active_fp64_bimodal"):
         c, uf = cases.mixing_layer_case(nx=1024, nr=256)
         tab = name.endswith("tables")
-        return (dict(c, tables=int(tab)), uf, "hydrogen-like mixing plume 1024x256 (pre-mixed layer), FP64"
-                + (", water properties from tables (2nd-order Taylor)" if tab else ", closed-form properties"), 0)
+        bi = name.endswith("bimodal")
+        return (dict(c, tables=int(tab), bimodal=int(bi)), uf,
+                "hydrogen-like mixing plume 1024x256 (pre-mixed layer), FP64"
+                + (", water properties from tables (2nd-order Taylor)" if tab else ", closed-form properties")
+                + (", bimodal liquid (two moment sets, 18 fields)" if bi else ""), 0)
     # active-heavy hydrogen-like mixing plume: the source fires in about half of the cells
     c, uf = cases.mixing_layer_case(nx=2048, nr=512)
     if name == "active_fp32":
         return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + FP64 islands", 1
+    if name == "active_fp32_bimodal":
+        return (dict(c, bimodal=1), uf,
+                "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + FP64 islands, bimodal liquid", 1)
     return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
 # Per-cell figures of the fused stage kernel with 16 x 16 tiles (the shape the autotuner
 # picks for both workloads), from one ncu capture each (see profiles/): FP64 arithmetic per
-# cell-stage (mean of the two stages: 1005 and 1191 flops) and DRAM bytes per cell per
+# cell-stage (mean of the two stages: 983.2 and 1164.1 flops) and DRAM bytes per cell per
 # launch (mean of the two stages).  The traffic is reported only for that shape.
 TRAFFIC_SHAPE = 1
-FP64_FLOPS_PER_CELL_STAGE = 1098.2
-FP64_TRAFFIC_PER_CELL_LAUNCH = 173.0
-FP32_TRAFFIC_PER_CELL_LAUNCH = 133.4
+FP64_FLOPS_PER_CELL_STAGE = 1073.7
+FP64_TRAFFIC_PER_CELL_LAUNCH = 170.1
+FP32_TRAFFIC_PER_CELL_LAUNCH = 133.9
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s)
 FP64_VISC_FLOPS_PER_CELL_STAGE = 1754.7
+# the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 1095.4 and 1299.2 flops)
+FP64_BI_FLOPS_PER_CELL_STAGE = 1197.3
 
 
 def measure_dgemm_tflops(dev) -> float:
@@ -264,33 +276,36 @@ def run_cuda(args):
     # each timed step (two launches of k_stage per step)
     launch_ms_ev = step_ms / 2.0
     elem = 8 if prec == 0 else 4
+    nf = 18 if c.get("bimodal") else 14   # fields of the state
     if prec == 0:
         # FP64 path: bound by the FP64 pipe.  Algorithmic flops per cell and stage are the
         # kernel's FP64 arithmetic (2 DFMA + DADD + DMUL), counted once with ncu
         # (profiles/k_stage_fp64_plume1024x256.md); the peak is cuBLAS DGEMM measured here.
         fpk = measure_dgemm_tflops(dev)
-        per_cell = FP64_VISC_FLOPS_PER_CELL_STAGE if c.get("viscous") else FP64_FLOPS_PER_CELL_STAGE
+        per_cell = (FP64_VISC_FLOPS_PER_CELL_STAGE if c.get("viscous") else
+                    FP64_BI_FLOPS_PER_CELL_STAGE if c.get("bimodal") else FP64_FLOPS_PER_CELL_STAGE)
         flops = cells * per_cell
         ach = flops / (launch_ms_ev * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fpk, 4),
                 "traffic": (FP64_TRAFFIC_PER_CELL_LAUNCH * cells
-                            if shape == TRAFFIC_SHAPE and not c.get("viscous") else None),
+                            if shape == TRAFFIC_SHAPE and not c.get("viscous") and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{per_cell} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"
                         + ("; figure of the dormant plume, a lower bound where the source fires"
                            if args.workload.startswith("active") else "")}
     else:
-        alg_bytes = cells * 14 * elem * 2.5      # stage 1: read U, write U1; stage 2: read U1, U, write U
+        alg_bytes = cells * nf * elem * 2.5      # stage 1: read U, write U1; stage 2: read U1, U, write U
         bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(bw / peaks["hbm_gbs"], 4),
-                "traffic": FP32_TRAFFIC_PER_CELL_LAUNCH * cells if shape == TRAFFIC_SHAPE else None,
+                "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH * cells
+                            if shape == TRAFFIC_SHAPE and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
-                "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
+                "note": f"algorithmic bytes 2.5*{nf}*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
-    bytes_state = cells * 14 * elem
+    bytes_state = cells * nf * elem
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
@@ -482,8 +497,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=("cuda", "reference"))
     ap.add_argument("--workload", default="fp64",
-                    choices=("fp64", "fp64_viscous", "fp32", "fp32_mlp", "active_fp32", "active_mlp", "active_fp64",
-                             "active_fp64_tables", "batch64"))
+                    choices=("fp64", "fp64_viscous", "fp64_bimodal", "fp32", "fp32_mlp", "active_fp32",
+                             "active_fp32_bimodal", "active_mlp", "active_fp64", "active_fp64_tables",
+                             "active_fp64_bimodal", "batch64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

@@ -474,7 +474,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);   // face fluxes
   T (*fL)[NFACE] = fb + NFX;       // reconstructed left state of each face
   T (*fR)[NFACE] = fb + 2 * NFX;   // reconstructed right state of each face
-  __shared__ double red[NT / 32][NPART];
+  // warp partials in the state precision: the FP32 kernels convert to FP64 once per slot and
+  // CTA (conversions run on the FP64 pipe, a small fraction of the FP32 rate on GB300)
+  __shared__ T red[NT / 32][NPART];
+  __shared__ T s_dt;
   __shared__ double fin[NPART];
 
   const int nx = dc.nx, nr = dc.geom == 1 ? dc.nr : 1;
@@ -482,7 +485,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   const int i0 = bx * TX, j0 = by * TY;
   const int tid = threadIdx.x;
   const double dtd = dc.hdr->dt_cur;
-  const T dt = T(dtd);
+  if (tid == 0) s_dt = T(dtd);   // one conversion per CTA; published by phase A's barrier
   const Geo<T> g = geo_of(dc, T(0));
 
   // phase A: halo primitives.  A thread owns up to NA halo cells; the interior loads of all
@@ -537,6 +540,8 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     }
   }
   __syncthreads();
+
+  const T dt = s_dt;
 
   // phase B1: limited x slopes, once per cell, written as the states of its two faces
   // (tile-local cell c in [-1, TX]; face f lies between cells f-1 and f)
@@ -705,8 +710,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     if (!SURR) {
       const bool act = phase_source<T, BI>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
       nactive = act ? 1 : 0;
-      lnJh = T(lnJ2[0]);
-      lnJt = T(lnJ2[1]);
+      if (act) {   // inactive cells keep -inf without a conversion
+        lnJh = T(lnJ2[0]);
+        lnJt = T(lnJ2[1]);
+      }
 #pragma unroll
       for (int f = 4; f < 13; ++f) acc[f] += Q[f];
       if (BI) {
@@ -761,50 +768,50 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     }
   }
 
-  // block partials: warp shuffles in the state precision, FP64 from the warp level on
+  // block partials: warp and CTA sums in the state precision, FP64 from the CTA level on
   const int warp = tid >> 5, lane = tid & 31;
   {
     T v;
     int a;
-    v = warp_sum(bm); if (lane == 0) red[warp][4] = double(v);
-    v = warp_sum(bw); if (lane == 0) red[warp][5] = double(v);
-    v = warp_sum(be); if (lane == 0) red[warp][6] = double(v);
+    v = warp_sum(bm); if (lane == 0) red[warp][4] = v;
+    v = warp_sum(bw); if (lane == 0) red[warp][5] = v;
+    v = warp_sum(be); if (lane == 0) red[warp][6] = v;
     if (SURR) {
       a = warp_count(ntimeout);
-      if (lane == 0) red[warp][26] = a;
+      if (lane == 0) red[warp][26] = T(a);
     } else if (lane == 0) {
-      red[warp][26] = 0.0;
+      red[warp][26] = T(0);
     }
     if (STAGE == 2) {
-      v = warp_min_nonneg(dtmin); if (lane == 0) red[warp][0] = double(v);
-      v = warp_sum(pM); if (lane == 0) red[warp][1] = double(v);
-      v = warp_sum(pW); if (lane == 0) red[warp][2] = double(v);
-      v = warp_sum(pE); if (lane == 0) red[warp][3] = double(v);
-      a = warp_count(nactive); if (lane == 0) red[warp][7] = a;
-      a = warp_count(nbad); if (lane == 0) red[warp][8] = a;
+      v = warp_min_nonneg(dtmin); if (lane == 0) red[warp][0] = v;
+      v = warp_sum(pM); if (lane == 0) red[warp][1] = v;
+      v = warp_sum(pW); if (lane == 0) red[warp][2] = v;
+      v = warp_sum(pE); if (lane == 0) red[warp][3] = v;
+      a = warp_count(nactive); if (lane == 0) red[warp][7] = T(a);
+      a = warp_count(nbad); if (lane == 0) red[warp][8] = T(a);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         v = warp_max_nonneg(rmax[f]);
-        if (lane == 0) red[warp][9 + f] = double(v);
+        if (lane == 0) red[warp][9 + f] = v;
       }
-      v = warp_max_any(lnJh); if (lane == 0) red[warp][23] = double(v);
-      v = warp_max_any(lnJt); if (lane == 0) red[warp][24] = double(v);
-      a = warp_count(nfallback); if (lane == 0) red[warp][25] = a;
+      v = warp_max_any(lnJh); if (lane == 0) red[warp][23] = v;
+      v = warp_max_any(lnJt); if (lane == 0) red[warp][24] = v;
+      a = warp_count(nfallback); if (lane == 0) red[warp][25] = T(a);
     } else if (lane == 0) {
       // stage 1 needs the boundary inflow and the timeouts only
       for (int q = 0; q < NPART; ++q)
-        if (q < 4 || q > 6) red[warp][q] = q == 26 ? red[warp][q] : 0.0;
+        if (q < 4 || q > 6) red[warp][q] = q == 26 ? red[warp][q] : T(0);
     }
   }
   __syncthreads();
   if (tid < NPART) {
     const int kind = slot_kind(tid);
-    double acc2 = red[0][tid];
+    T acc2 = red[0][tid];
     for (int w2 = 1; w2 < NT / 32; ++w2) {
-      const double v = red[w2][tid];
-      acc2 = kind == 0 ? acc2 + v : (kind == 1 ? fmax(acc2, v) : fmin(acc2, v));
+      const T v = red[w2][tid];
+      acc2 = kind == 0 ? acc2 + v : (kind == 1 ? (v > acc2 ? v : acc2) : (v < acc2 ? v : acc2));
     }
-    dc.partials[(size_t)tile * NPART + tid] = acc2;
+    dc.partials[(size_t)tile * NPART + tid] = double(acc2);
   }
   if (!tile_reduce(dc, by, fin)) return;
   if (tid == 0) {
