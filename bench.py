@@ -96,14 +96,15 @@ def _workload(name):
     return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
-# Per-cell figures of the fused stage kernel with 16 x 16 tiles (the shape the autotuner
-# picks for both workloads), from one ncu capture each (see profiles/): FP64 arithmetic per
-# cell-stage (mean of the two stages: 983.2 and 1164.1 flops) and DRAM bytes per cell per
-# launch (mean of the two stages).  The traffic is reported only for that shape.
-TRAFFIC_SHAPE = 1
+# Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/), in
+# the tile shape the autotuner picks for the workload (FP64: 16 x 16; FP32: 32 x 8 with
+# three CTAs per SM): FP64 arithmetic per cell-stage (mean of the two stages: 983.2 and
+# 1164.1 flops) and DRAM bytes per cell per launch (mean of the two stages).  The traffic is
+# reported only for that shape.
+TRAFFIC_SHAPE = {0: 1, 1: 5}
 FP64_FLOPS_PER_CELL_STAGE = 1073.7
 FP64_TRAFFIC_PER_CELL_LAUNCH = 170.1
-FP32_TRAFFIC_PER_CELL_LAUNCH = 133.9
+FP32_TRAFFIC_PER_CELL_LAUNCH = 137.9
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s)
 FP64_VISC_FLOPS_PER_CELL_STAGE = 1754.7
 # the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 1095.4 and 1299.2 flops)
@@ -289,7 +290,7 @@ def run_cuda(args):
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fpk, 4),
                 "traffic": (FP64_TRAFFIC_PER_CELL_LAUNCH * cells
-                            if shape == TRAFFIC_SHAPE and not c.get("viscous") and not c.get("bimodal") else None),
+                            if shape == TRAFFIC_SHAPE[0] and not c.get("viscous") and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{per_cell} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"
@@ -301,7 +302,7 @@ def run_cuda(args):
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(bw / peaks["hbm_gbs"], 4),
                 "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH * cells
-                            if shape == TRAFFIC_SHAPE and not c.get("bimodal") else None),
+                            if shape == TRAFFIC_SHAPE[1] and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*{nf}*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
@@ -313,8 +314,8 @@ def run_cuda(args):
         "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32+bf16"),
         "data": "synthetic", "impl": "cuda",
         "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
-                   "tile": "%dx%d (autotuned; ms per stage-1 launch per shape: %s)"
-                           % (*P.ct_tile_shape(shape), [round(m, 4) for m in tune_ms]),
+                   "tile": "%dx%d, %d FP32 CTAs/SM (autotuned; ms per stage-1 launch per shape: %s)"
+                           % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape), [round(m, 4) for m in tune_ms]),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
@@ -404,13 +405,14 @@ def run_batch(args):
     launch_ms = step_ms / 2.0
     bw = cells_rank * 14 * 4 * 2.5 / (launch_ms * 1e-3) / 1e9
     tx, ty = P.ct_tile_shape(shape)
+    ctas = P.ct_tile_shape_ctas(shape)
     bytes_state = cells_rank * 14 * 4
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic", "impl": "cuda",
         "config": {"workload": BATCH_DESC, "cases": len(bc) * world, "cells": cells, "cfl": cfl,
-                   "tile": f"{tx}x{ty} (autotuned; ms per stage-1 launch per shape: "
+                   "tile": f"{tx}x{ty}, {ctas} FP32 CTAs/SM (autotuned; ms per stage-1 launch per shape: "
                            f"{[round(m, 4) for m in tune_ms]})",
                    "l2": "inputs larger than L2 (1.25 GB per FP32 state copy)",
                    "parallelism": f"replicas x{world}"},

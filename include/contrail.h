@@ -285,6 +285,12 @@ int ct_tile_shape_count(void);
 /* Cells per tile of shape `shape` in x and r. */
 ct_status ct_tile_shape(int shape, int *tx, int *ty);
 
+/* FP32 CTAs per SM that shape `shape`'s registers are budgeted for: 1 for the tiles of more
+ * than 320 threads, 2 for the others, 3 for the shapes that carry the plain FP32 kernels
+ * only and trade register spills for more resident warps; 0 for an invalid shape.  Shapes
+ * of equal size differ in this budget only. */
+int ct_tile_shape_ctas(int shape);
+
 /* Register `shape` for cases with this case's geometry, grid and precision (-1: back to the
  * default).  CT_ERR_ARG when the shape's kernel does not fit an SM at that precision. */
 ct_status ct_set_tile_shape(const ct_case *c, int precision, int shape);

@@ -11,7 +11,7 @@ from ._lib import (  # noqa: F401
     ct_mlp_dataset, ct_mlp_param_count, ct_mlp_work_bytes, ct_mlp_forward, ct_mlp_loss_grad, ct_mlp_adam,
     ct_mlp_colstats, ct_mlp_standardize, ct_mlp_blob_bytes, ct_mlp_pack, ct_mlp_infer, ct_step_surrogate,
     CT_MLP_IN, CT_MLP_HIDDEN, CT_MLP_OUT,
-    ct_tile_shape_count, ct_tile_shape, ct_set_tile_shape, ct_autotune,
+    ct_tile_shape_count, ct_tile_shape, ct_tile_shape_ctas, ct_set_tile_shape, ct_autotune,
     ct_batch_workspace_bytes, ct_batch_state_elems, ct_batch_create, ct_batch_destroy, ct_batch_init_state,
     ct_batch_load_state, ct_batch_set_tile_shape, ct_batch_tile_shape, ct_batch_autotune, ct_batch_step,
     ct_batch_diagnostics,

@@ -82,6 +82,7 @@ _SIGS = {
     "ct_step_surrogate": (C.c_int, [_cp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_tile_shape_count": (C.c_int, []),
     "ct_tile_shape": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ct_tile_shape_ctas": (C.c_int, [C.c_int]),
     "ct_set_tile_shape": (C.c_int, [_cp, C.c_int, C.c_int]),
     "ct_autotune": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp, C.POINTER(C.c_int),
                               C.POINTER(C.c_float)]),
@@ -278,6 +279,10 @@ def ct_tile_shape(shape: int) -> tuple[int, int]:
     tx, ty = C.c_int(), C.c_int()
     _check(_L().ct_tile_shape(shape, C.byref(tx), C.byref(ty)))
     return tx.value, ty.value
+
+
+def ct_tile_shape_ctas(shape: int) -> int:
+    return _L().ct_tile_shape_ctas(shape)
 
 
 def ct_set_tile_shape(case, precision, shape):

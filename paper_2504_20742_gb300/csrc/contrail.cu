@@ -326,11 +326,15 @@ const StageSet* stage_set_32x8();
 const StageSet* stage_set_16x16();
 const StageSet* stage_set_32x16();
 const StageSet* stage_set_64x8();
+const StageSet* stage_set_16x16_o3();
+const StageSet* stage_set_32x8_o3();
 const StageSet* stage_set(int shape) {
   switch (shape) {
     case 1: return stage_set_16x16();
     case 2: return stage_set_32x16();
     case 3: return stage_set_64x8();
+    case 4: return stage_set_16x16_o3();
+    case 5: return stage_set_32x8_o3();
     default: return stage_set_32x8();
   }
 }
@@ -852,6 +856,8 @@ ct_status ct_tile_shape(int shape, int* tx, int* ty) {
   *ty = stage_set(shape)->ty;
   return CT_OK;
 }
+
+int ct_tile_shape_ctas(int shape) { return shape >= 0 && shape < NSHAPES ? stage_set(shape)->ctas32 : 0; }
 
 ct_status ct_set_tile_shape(const ct_case* c, int precision, int shape) {
   ct_status s = validate(c, precision);

@@ -69,15 +69,16 @@ struct DevCase {
 
 // Tile of TX x TY cells per CTA with a two-cell halo (HX x HY).  NT threads: the larger of
 // the x-face ((TX+1) x TY) and r-face (TX x (TY+1)) counts rounded up to whole warps, so that
-// each face pass takes a single round of the CTA.  MINB: CTAs per SM the register budget is
-// set for (two for the FP32 kernels of tiles up to 320 threads).
-template <int TX_, int TY_>
+// each face pass takes a single round of the CTA.  minb: CTAs per SM the register budget is
+// set for: M32 for the FP32 kernels of tiles up to 320 threads (2: 96 registers; 3: 72
+// registers, more warps to hide latency at the price of spills), else one.
+template <int TX_, int TY_, int M32 = 2>
 struct Tile {
   static constexpr int TX = TX_, TY = TY_, HX = TX + 4, HY = TY + 4, NCELL = TX * TY;
   static constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
   static constexpr int NT = (NFACE + 31) / 32 * 32;
   template <class T>
-  static constexpr int minb() { return sizeof(T) == 4 && NT <= 320 ? 2 : 1; }
+  static constexpr int minb() { return sizeof(T) == 4 && NT <= 320 ? M32 : 1; }
   template <class T, int NFX = NF>
   static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + 3 * NFACE); }
 };
@@ -951,6 +952,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
 constexpr int NVARIANT = 5;
 struct StageSet {
   int tx, ty, nt;
+  int ctas32;                       // FP32 CTAs per SM the registers are budgeted for
   size_t smem[NVARIANT];
   int minb[NVARIANT];
   const void* stage[NVARIANT][2];   // k_stage, stages 1 and 2
@@ -965,6 +967,7 @@ StageSet make_stage_set() {
   s.tx = TL::TX;
   s.ty = TL::TY;
   s.nt = TL::NT;
+  s.ctas32 = TL::template minb<float>();
   s.smem[0] = TL::template smem<double>();
   s.smem[1] = TL::template smem<float>();
   s.smem[2] = stage_smem_surr<TL>();
@@ -1004,8 +1007,31 @@ void add_bimodal_variants(StageSet& s) {
   }
 }
 
+// Plain FP32 kernels only (variant 1, single-case and batched), for the shapes whose
+// registers are budgeted for three CTAs per SM: the FP64 kernels would be those of the
+// two-CTA shape, and the surrogate and bimodal FP32 kernels do not fit three CTAs' shared
+// memory.
+template <class TL>
+StageSet make_stage_set_fp32() {
+  StageSet s;
+  memset(&s, 0, sizeof(s));
+  s.tx = TL::TX;
+  s.ty = TL::TY;
+  s.nt = TL::NT;
+  s.ctas32 = TL::template minb<float>();
+  s.smem[1] = TL::template smem<float>();
+  s.minb[1] = TL::template minb<float>();
+  s.stage[1][0] = (const void*)k_stage<TL, float, 1, false>;
+  s.stage[1][1] = (const void*)k_stage<TL, float, 2, false>;
+  s.batch[1][0] = (const void*)k_batch_stage<TL, float, 1, false>;
+  s.batch[1][1] = (const void*)k_batch_stage<TL, float, 2, false>;
+  return s;
+}
+
 // the tile shapes the library is built with (one translation unit each)
-constexpr int NSHAPES = 4;
-const StageSet* stage_set(int shape);   // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8
+constexpr int NSHAPES = 6;
+// 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8, 4: 16x16 and 5: 32x8 with three FP32 CTAs
+// per SM
+const StageSet* stage_set(int shape);
 
 }  // namespace ct

@@ -67,7 +67,9 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     from synth import cases
     n = P.ct_tile_shape_count()
     shapes = [P.ct_tile_shape(s) for s in range(n)]
-    assert shapes[0] == (32, 8) and len(set(shapes)) == n
+    ctas = [P.ct_tile_shape_ctas(s) for s in range(n)]
+    assert shapes[0] == (32, 8) and len(set(zip(shapes, ctas))) == n
+    assert set(ctas) == {1, 2, 3} and P.ct_tile_shape_ctas(n) == 0
     c, _ = cases.plume_case(nx=64, nr=16)
     # FP64 tiles of 32 x 16 cells do not fit the shared memory of an SM
     k = shapes.index((32, 16))
@@ -78,6 +80,13 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     P.ct_set_tile_shape(c, P.CT_FP32, -1)
     with pytest.raises(P.ContrailError):
         P.ct_set_tile_shape(c, P.CT_FP32, n)
+    # the three-CTA shapes carry the plain FP32 kernels only
+    k3 = ctas.index(3)
+    P.ct_set_tile_shape(c, P.CT_FP32, k3)
+    P.ct_set_tile_shape(c, P.CT_FP32, -1)
+    for prec in (P.CT_FP64, P.CT_FP32_MLP):
+        with pytest.raises(P.ContrailError):
+            P.ct_set_tile_shape(c, prec, k3)
     # the workspace holds the partials of the shape with the most tiles
     ragged, _ = cases.plume_case(nx=40, nr=24)
     tiles = max(-(-40 // tx) * -(-24 // ty) for tx, ty in shapes)
