@@ -3,6 +3,7 @@
 // published in detail, so this is Roe's flux for the frozen ideal mixture with formation
 // energies, passive quantities carried by the upwind mass flux).
 #pragma once
+#include "pair.cuh"
 #include "physics.cuh"
 
 namespace ct {
@@ -15,6 +16,20 @@ namespace ct {
 template <class T>
 __device__ __forceinline__ T vl_half_slope(T dm, T dp) {
   return dm * dp > T(0) ? dm * tdiv(dp, dm + dp) : T(0);
+}
+// The same for two fields at once (pair.cuh).  FP32: paired products and the two
+// reciprocals, the sign test applied as a select.  FP64: field by field, so that the
+// Newton reciprocal (several FP64 instructions, the bottleneck of the FP64 kernels) is
+// skipped where the slope is zero.
+__device__ __forceinline__ float2 vl_half_slope2(float2 dm, float2 dp) {
+  const float2 s = p_add(dm, dp);
+  const float2 q = p_mul(dp, p_make(trcp(s.x), trcp(s.y)));
+  const float2 hs = p_mul(dm, q);
+  const float2 pr = p_mul(dm, dp);
+  return p_make(pr.x > 0.0f ? hs.x : 0.0f, pr.y > 0.0f ? hs.y : 0.0f);
+}
+__device__ __forceinline__ double2 vl_half_slope2(double2 dm, double2 dp) {
+  return p_make(vl_half_slope(dm.x, dp.x), vl_half_slope(dm.y, dp.y));
 }
 
 // Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
@@ -94,8 +109,14 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   F[2] = DIR == 0 ? ft : fn;
   F[3] = fe;
   const T* qu = fm >= T(0) ? qL : qR;
+  // passive quantities (fields 4.. in pairs)
+  const auto fm2 = p_make(fm, fm);
 #pragma unroll
-  for (int f = 4; f < NFX; ++f) F[f] = fm * qu[f];
+  for (int k = 2; k < NFX / 2; ++k) {
+    const auto v = p_mul(fm2, p_make(qu[2 * k], qu[2 * k + 1]));
+    F[2 * k] = v.x;
+    F[2 * k + 1] = v.y;
+  }
 }
 
 // ---- viscous and diffusive face fluxes (Sec. 3.1 Eqs. (25)-(26), central differences) ----

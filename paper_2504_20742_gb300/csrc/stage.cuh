@@ -471,10 +471,22 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   constexpr int TX = TL::TX, TY = TL::TY, HX = TL::HX, HY = TL::HY, NT = TL::NT, NCELL = TL::NCELL;
   constexpr int NFACE = TL::NFACE;
   constexpr int NFX = nf_of<BI>();   // fields of the state (18 with the bimodal liquid)
-  T (*qs)[HY][HX] = reinterpret_cast<T (*)[HY][HX]>(smem_raw);                      // primitives
-  T (*fb)[NFACE] = reinterpret_cast<T (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);   // face fluxes
-  T (*fL)[NFACE] = fb + NFX;       // reconstructed left state of each face
-  T (*fR)[NFACE] = fb + 2 * NFX;   // reconstructed right state of each face
+  // Shared memory holds the fields in pairs (pair.cuh): pair k = fields 2k, 2k+1 side by side.
+  using V = typename PairOf<T>::V;
+  constexpr int NP = NFX / 2;
+  V (*qs2)[HY][HX] = reinterpret_cast<V (*)[HY][HX]>(smem_raw);                       // primitives
+  V (*fb2)[NFACE] = reinterpret_cast<V (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);  // face fluxes
+  V (*fL2)[NFACE] = fb2 + NP;      // reconstructed left state of each face
+  V (*fR2)[NFACE] = fb2 + 2 * NP;  // reconstructed right state of each face
+  // scalar views: field f of a cell or face
+  const auto qs = [&](int f, int hj, int hi) -> T {
+    const V v = qs2[f >> 1][hj][hi];
+    return (f & 1) ? v.y : v.x;
+  };
+  const auto fb = [&](int f, int face) -> T {
+    const V v = fb2[f >> 1][face];
+    return (f & 1) ? v.y : v.x;
+  };
   // warp partials in the state precision: the FP32 kernels convert to FP64 once per slot and
   // CTA (conversions run on the FP64 pipe, a small fraction of the FP32 rate on GB300)
   __shared__ T red[NT / 32][NPART];
@@ -523,21 +535,24 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       }
       Prim<T> w;
       cons_to_prim<T, BI>(u14[r], w);
-      qs[0][hj][hi] = w.rho;
-      qs[1][hj][hi] = w.u;
-      qs[2][hj][hi] = w.v;
-      qs[3][hj][hi] = w.p;
-      qs[4][hj][hi] = w.Yv;
+      T qv[NFX];
+      qv[0] = w.rho;
+      qv[1] = w.u;
+      qv[2] = w.v;
+      qv[3] = w.p;
+      qv[4] = w.Yv;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        qs[5 + q][hj][hi] = w.ml[q];
-        qs[9 + q][hj][hi] = w.ms[q];
+        qv[5 + q] = w.ml[q];
+        qv[9 + q] = w.ms[q];
       }
-      qs[13][hj][hi] = w.ns;
+      qv[13] = w.ns;
       if (BI) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) qs[14 + q][hj][hi] = w.mh[q];
+        for (int q = 0; q < 4; ++q) qv[14 + q] = w.mh[q];
       }
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) qs2[k2][hj][hi] = p_make(qv[2 * k2], qv[2 * k2 + 1]);
     }
   }
   __syncthreads();
@@ -551,11 +566,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const int i = i0 + c, j = j0 + hj;
     if (i > nx || j >= nr) continue;
 #pragma unroll
-    for (int f = 0; f < NFX; ++f) {
-      const T am = qs[f][hj + 2][c + 1], a0 = qs[f][hj + 2][c + 2], a1 = qs[f][hj + 2][c + 3];
-      const T hs = vl_half_slope(a0 - am, a1 - a0);
-      if (c < TX) fL[f][hj * (TX + 1) + c + 1] = a0 + hs;
-      if (c >= 0) fR[f][hj * (TX + 1) + c] = a0 - hs;
+    for (int k2 = 0; k2 < NP; ++k2) {
+      const V am = qs2[k2][hj + 2][c + 1], a0 = qs2[k2][hj + 2][c + 2], a1 = qs2[k2][hj + 2][c + 3];
+      const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
+      if (c < TX) fL2[k2][hj * (TX + 1) + c + 1] = p_add(a0, hs);
+      if (c >= 0) fR2[k2][hj * (TX + 1) + c] = p_sub(a0, hs);
     }
   }
   __syncthreads();
@@ -567,18 +582,21 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     if (i > nx || j >= nr) continue;
     T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
-    for (int f = 0; f < NFX; ++f) {
-      qL[f] = fL[f][p];
-      qR[f] = fR[f][p];
+    for (int k2 = 0; k2 < NP; ++k2) {
+      const V a = fL2[k2][p], b = fR2[k2][p];
+      qL[2 * k2] = a.x;
+      qL[2 * k2 + 1] = a.y;
+      qR[2 * k2] = b.x;
+      qR[2 * k2 + 1] = b.y;
     }
     roe_flux<T, 0, NFX>(qL, qR, F);
     // walls are adiabatic, impermeable and slip: nothing diffuses through them
     if (dc.viscous && !((i == 0 && dc.bc_xlo == 1) || (i == nx && dc.bc_xhi == 1))) {
-      const auto q = [&](int f, int side) -> T { return qs[f][hj + 2][fx + 1 + side]; };
+      const auto q = [&](int f, int side) -> T { return qs(f, hj + 2, fx + 1 + side); };
       sub_diffusive_flux<T, NFX>(q, g.idx, g.nu_t, F);
     }
 #pragma unroll
-    for (int f = 0; f < NFX; ++f) fb[f][p] = F[f];
+    for (int k2 = 0; k2 < NP; ++k2) fb2[k2][p] = p_make(F[2 * k2], F[2 * k2 + 1]);
   }
   __syncthreads();
 
@@ -588,8 +606,8 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   T acc[NFX];
   // water carried by a face flux: vapour, liquid (both sets) and ice
   const auto water_flux = [&](int f) -> T {
-    const T l3 = BI ? fb[8][f] + fb[17][f] : fb[8][f];
-    return fb[4][f] + T(k::YL3) * l3 + T(k::YS3) * fb[12][f];
+    const T l3 = BI ? fb(8, f) + fb(17, f) : fb(8, f);
+    return fb(4, f) + T(k::YL3) * l3 + T(k::YS3) * fb(12, f);
   };
   T bm = T(0), bw = T(0), be = T(0);   // boundary inflow rates of this cell's faces
   T area_w = T(0), area_e = T(0), vol = T(0);
@@ -611,17 +629,22 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
       vol = area_w * g.dx;
     }
+    const V cw2 = p_make(cw, cw), nce2 = p_make(-ce, -ce);
 #pragma unroll
-    for (int f = 0; f < NFX; ++f) acc[f] = cw * fb[f][w] - ce * fb[f][e];
+    for (int k2 = 0; k2 < NP; ++k2) {
+      const V a = p_fma(cw2, fb2[k2][w], p_mul(nce2, fb2[k2][e]));
+      acc[2 * k2] = a.x;
+      acc[2 * k2 + 1] = a.y;
+    }
     if (i == 0) {
-      bm += area_w * fb[0][w];
+      bm += area_w * fb(0, w);
       bw += area_w * water_flux(w);
-      be += area_w * fb[3][w];
+      be += area_w * fb(3, w);
     }
     if (i == nx - 1) {
-      bm -= area_e * fb[0][e];
+      bm -= area_e * fb(0, e);
       bw -= area_e * water_flux(e);
-      be -= area_e * fb[3][e];
+      be -= area_e * fb(3, e);
     }
   }
 
@@ -633,11 +656,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const int ii = i0 + hi, jj = j0 + c;
       if (ii >= nx || jj > nr) continue;
 #pragma unroll
-      for (int f = 0; f < NFX; ++f) {
-        const T am = qs[f][c + 1][hi + 2], a0 = qs[f][c + 2][hi + 2], a1 = qs[f][c + 3][hi + 2];
-        const T hs = vl_half_slope(a0 - am, a1 - a0);
-        if (c < TY) fL[f][(c + 1) * TX + hi] = a0 + hs;
-        if (c >= 0) fR[f][c * TX + hi] = a0 - hs;
+      for (int k2 = 0; k2 < NP; ++k2) {
+        const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
+        const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
+        if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
+        if (c >= 0) fR2[k2][c * TX + hi] = p_sub(a0, hs);
       }
     }
     __syncthreads();
@@ -648,17 +671,20 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       if (ii >= nx || jj > nr) continue;
       T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
-      for (int f = 0; f < NFX; ++f) {
-        qL[f] = fL[f][p];
-        qR[f] = fR[f][p];
+      for (int k2 = 0; k2 < NP; ++k2) {
+        const V a = fL2[k2][p], b = fR2[k2][p];
+        qL[2 * k2] = a.x;
+        qL[2 * k2 + 1] = a.y;
+        qR[2 * k2] = b.x;
+        qR[2 * k2 + 1] = b.y;
       }
       roe_flux<T, 1, NFX>(qL, qR, F);
       if (dc.viscous && !(jj == nr && dc.bc_rhi == 1)) {
-        const auto q = [&](int f, int side) -> T { return qs[f][fy + 1 + side][hi + 2]; };
+        const auto q = [&](int f, int side) -> T { return qs(f, fy + 1 + side, hi + 2); };
         sub_diffusive_flux<T, NFX>(q, g.idr, g.nu_t, F);
       }
 #pragma unroll
-      for (int f = 0; f < NFX; ++f) fb[f][p] = F[f];
+      for (int k2 = 0; k2 < NP; ++k2) fb2[k2][p] = p_make(F[2 * k2], F[2 * k2 + 1]);
     }
     __syncthreads();
   }
@@ -682,12 +708,16 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const T ijh = trcp(T(j) + T(0.5));
       const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
       const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
+      const V cs2 = p_make(cs, cs), ncn2 = p_make(-cn, -cn);
 #pragma unroll
-      for (int f = 0; f < NFX; ++f) {
-        T Fs = fb[f][cj * TX + ci], Fn = fb[f][(cj + 1) * TX + ci];
-        if (wall && j == dc.jw - 1) Fn = f == 2 ? w.p : T(0);
-        if (wall && j == dc.jw) Fs = f == 2 ? w.p : T(0);
-        acc[f] += cs * Fs - cn * Fn;
+      for (int k2 = 0; k2 < NP; ++k2) {
+        V Fs = fb2[k2][cj * TX + ci], Fn = fb2[k2][(cj + 1) * TX + ci];
+        // the duct wall's faces carry the pressure in rho*v (field 2: pair 1) and nothing else
+        if (wall && j == dc.jw - 1) Fn = p_make(k2 == 1 ? w.p : T(0), T(0));
+        if (wall && j == dc.jw) Fs = p_make(k2 == 1 ? w.p : T(0), T(0));
+        const V a = p_add(p_make(acc[2 * k2], acc[2 * k2 + 1]), p_fma(cs2, Fs, p_mul(ncn2, Fn)));
+        acc[2 * k2] = a.x;
+        acc[2 * k2 + 1] = a.y;
       }
       acc[2] += w.p * ijh * g.idr;
       if (dc.viscous) {   // radial component of the vector Laplacian: -mu_e v / r^2
@@ -698,9 +728,9 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       if (j == nr - 1) {
         const T An = T(nr) * g.dr * g.dx;
         const int e = (cj + 1) * TX + ci;
-        bm -= An * fb[0][e];
+        bm -= An * fb(0, e);
         bw -= An * water_flux(e);
-        be -= An * fb[3][e];
+        be -= An * fb(3, e);
       }
     } else {
       acc[1] += w.p * tdiv(area_e - area_w, vol);
@@ -730,15 +760,31 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const size_t n = (size_t)j * nx + i;
     // RK combine
     T out[NFX];
+    const V dt2 = p_make(dt, dt);
     if (STAGE == 1) {
 #pragma unroll
-      for (int f = 0; f < NFX; ++f) out[f] = u14[f] + dt * acc[f];
+      for (int k2 = 0; k2 < NP; ++k2) {
+        const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+        out[2 * k2] = o.x;
+        out[2 * k2 + 1] = o.y;
+      }
     } else {
       const T idt = trcp(dt);
+      const V half2 = p_make(T(0.5), T(0.5));
+      T unv[NFX];
+#pragma unroll
+      for (int f = 0; f < NFX; ++f) unv[f] = Un[f * N + n];
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) {
+        const V un2 = p_make(unv[2 * k2], unv[2 * k2 + 1]);
+        const V t = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+        const V o = p_fma(half2, un2, p_mul(half2, t));
+        out[2 * k2] = o.x;
+        out[2 * k2 + 1] = o.y;
+      }
 #pragma unroll
       for (int f = 0; f < NFX; ++f) {
-        const T un = Un[f * N + n];
-        out[f] = T(0.5) * un + T(0.5) * (u14[f] + dt * acc[f]);
+        const T un = unv[f];
         const T rf = m_fabs(out[f] - un) * idt;
         if (f < NF) {
           rmax[f] = rf;
