@@ -603,6 +603,22 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   const int ci = tid % TX, cj = tid / TX;
   const int i = i0 + ci, j = j0 + cj;
   const bool cell = tid < NCELL && i < nx && j < nr;
+  // limited r slope of tile-local row c in [-1, TY] at column hi -> states of its r faces
+  const auto r_slope = [&](int hi, int c) {
+    const int ii = i0 + hi, jj = j0 + c;
+    if (ii >= nx || jj > nr) return;
+#pragma unroll
+    for (int k2 = 0; k2 < NP; ++k2) {
+      const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
+      const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
+      if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
+      if (c >= 0) fR2[k2][c * TX + hi] = p_sub(a0, hs);
+    }
+  };
+  // The r slopes of rows -1..TY outnumber the threads for the 32-wide tiles; the threads
+  // without a cell take row -1 during the x divergence (the x face states are dead by then),
+  // so that phase D1 is a single round.
+  constexpr bool ROWM1_EARLY = TX * (TY + 2) > NT && NT - NCELL >= TX;
   T acc[NFX];
   // water carried by a face flux: vapour, liquid (both sets) and ice
   const auto water_flux = [&](int f) -> T {
@@ -649,20 +665,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   }
 
   if (dc.geom == 1) {
+    if (ROWM1_EARLY && tid >= NCELL && tid - NCELL < TX) r_slope(tid - NCELL, -1);
     __syncthreads();
     // phase D1: limited r slopes (tile-local row c in [-1, TY]) -> states of the r faces
-    for (int p = tid; p < TX * (TY + 2); p += NT) {
-      const int hi = p % TX, c = p / TX - 1;
-      const int ii = i0 + hi, jj = j0 + c;
-      if (ii >= nx || jj > nr) continue;
-#pragma unroll
-      for (int k2 = 0; k2 < NP; ++k2) {
-        const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
-        const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
-        if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
-        if (c >= 0) fR2[k2][c * TX + hi] = p_sub(a0, hs);
-      }
-    }
+    for (int p = tid + (ROWM1_EARLY ? TX : 0); p < TX * (TY + 2); p += NT) r_slope(p % TX, p / TX - 1);
     __syncthreads();
     // phase D2: r-face Roe fluxes (face fy lies between tile rows fy-1 and fy)
     for (int p = tid; p < TX * (TY + 1); p += NT) {
