@@ -314,8 +314,8 @@ def run_cuda(args):
         "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32+bf16"),
         "data": "synthetic", "impl": "cuda",
         "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
-                   "tile": "%dx%d, %d FP32 CTAs/SM (autotuned; ms per stage-1 launch per shape: %s)"
-                           % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape), [round(m, 4) for m in tune_ms]),
+                   "tile": "%dx%d, %d CTAs/SM (autotuned; ms per stage-1 launch per shape: %s)"
+                           % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape, prec), [round(m, 4) for m in tune_ms]),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
@@ -405,14 +405,14 @@ def run_batch(args):
     launch_ms = step_ms / 2.0
     bw = cells_rank * 14 * 4 * 2.5 / (launch_ms * 1e-3) / 1e9
     tx, ty = P.ct_tile_shape(shape)
-    ctas = P.ct_tile_shape_ctas(shape)
+    ctas = P.ct_tile_shape_ctas(shape, P.CT_FP32_MLP)
     bytes_state = cells_rank * 14 * 4
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic", "impl": "cuda",
         "config": {"workload": BATCH_DESC, "cases": len(bc) * world, "cells": cells, "cfl": cfl,
-                   "tile": f"{tx}x{ty}, {ctas} FP32 CTAs/SM (autotuned; ms per stage-1 launch per shape: "
+                   "tile": f"{tx}x{ty}, {ctas} CTAs/SM (autotuned; ms per stage-1 launch per shape: "
                            f"{[round(m, 4) for m in tune_ms]})",
                    "l2": "inputs larger than L2 (1.25 GB per FP32 state copy)",
                    "parallelism": f"replicas x{world}"},

@@ -285,11 +285,11 @@ int ct_tile_shape_count(void);
 /* Cells per tile of shape `shape` in x and r. */
 ct_status ct_tile_shape(int shape, int *tx, int *ty);
 
-/* FP32 CTAs per SM that shape `shape`'s registers are budgeted for: 1 for the tiles of more
- * than 320 threads, 2 for the others, 3 for the shapes that carry the plain FP32 kernels
- * only and trade register spills for more resident warps; 0 for an invalid shape.  Shapes
- * of equal size differ in this budget only. */
-int ct_tile_shape_ctas(int shape);
+/* CTAs per SM that the registers of shape `shape`'s kernels at `precision` are budgeted for
+ * (more CTAs: more resident warps to hide latency, fewer registers per thread); 0 when the
+ * shape has no kernels at that precision.  Some shapes carry one precision only: 32 x 8 and
+ * 16 x 16 with three FP32 CTAs per SM, 16 x 12 with two FP64 CTAs per SM. */
+int ct_tile_shape_ctas(int shape, int precision);
 
 /* Register `shape` for cases with this case's geometry, grid and precision (-1: back to the
  * default).  CT_ERR_ARG when the shape's kernel does not fit an SM at that precision. */

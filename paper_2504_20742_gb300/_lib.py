@@ -82,7 +82,7 @@ _SIGS = {
     "ct_step_surrogate": (C.c_int, [_cp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_tile_shape_count": (C.c_int, []),
     "ct_tile_shape": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
-    "ct_tile_shape_ctas": (C.c_int, [C.c_int]),
+    "ct_tile_shape_ctas": (C.c_int, [C.c_int, C.c_int]),
     "ct_set_tile_shape": (C.c_int, [_cp, C.c_int, C.c_int]),
     "ct_autotune": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp, C.POINTER(C.c_int),
                               C.POINTER(C.c_float)]),
@@ -281,8 +281,8 @@ def ct_tile_shape(shape: int) -> tuple[int, int]:
     return tx.value, ty.value
 
 
-def ct_tile_shape_ctas(shape: int) -> int:
-    return _L().ct_tile_shape_ctas(shape)
+def ct_tile_shape_ctas(shape: int, precision: int = 1) -> int:
+    return _L().ct_tile_shape_ctas(shape, precision)
 
 
 def ct_set_tile_shape(case, precision, shape):

@@ -328,6 +328,7 @@ const StageSet* stage_set_32x16();
 const StageSet* stage_set_64x8();
 const StageSet* stage_set_16x16_o3();
 const StageSet* stage_set_32x8_o3();
+const StageSet* stage_set_16x12_d2();
 const StageSet* stage_set(int shape) {
   switch (shape) {
     case 1: return stage_set_16x16();
@@ -335,6 +336,7 @@ const StageSet* stage_set(int shape) {
     case 3: return stage_set_64x8();
     case 4: return stage_set_16x16_o3();
     case 5: return stage_set_32x8_o3();
+    case 6: return stage_set_16x12_d2();
     default: return stage_set_32x8();
   }
 }
@@ -857,7 +859,12 @@ ct_status ct_tile_shape(int shape, int* tx, int* ty) {
   return CT_OK;
 }
 
-int ct_tile_shape_ctas(int shape) { return shape >= 0 && shape < NSHAPES ? stage_set(shape)->ctas32 : 0; }
+int ct_tile_shape_ctas(int shape, int precision) {
+  if (shape < 0 || shape >= NSHAPES || precision < CT_FP64 || precision > CT_FP32_MLP) return 0;
+  const StageSet* ss = stage_set(shape);
+  const int p = precision == CT_FP64 ? 0 : (precision == CT_FP32 ? 1 : 2);
+  return ss->stage[p][0] ? ss->minb[p] : 0;
+}
 
 ct_status ct_set_tile_shape(const ct_case* c, int precision, int shape) {
   ct_status s = validate(c, precision);

@@ -71,14 +71,15 @@ struct DevCase {
 // the x-face ((TX+1) x TY) and r-face (TX x (TY+1)) counts rounded up to whole warps, so that
 // each face pass takes a single round of the CTA.  minb: CTAs per SM the register budget is
 // set for: M32 for the FP32 kernels of tiles up to 320 threads (2: 96 registers; 3: 72
-// registers, more warps to hide latency at the price of spills), else one.
-template <int TX_, int TY_, int M32 = 2>
+// registers, more warps to hide latency at the price of spills), else one; M64 for the FP64
+// kernels.
+template <int TX_, int TY_, int M32 = 2, int M64 = 1>
 struct Tile {
   static constexpr int TX = TX_, TY = TY_, HX = TX + 4, HY = TY + 4, NCELL = TX * TY;
   static constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
   static constexpr int NT = (NFACE + 31) / 32 * 32;
   template <class T>
-  static constexpr int minb() { return sizeof(T) == 4 && NT <= 320 ? M32 : 1; }
+  static constexpr int minb() { return sizeof(T) == 4 ? (NT <= 320 ? M32 : 1) : M64; }
   template <class T, int NFX = NF>
   static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + 3 * NFACE); }
 };
@@ -1004,7 +1005,6 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
 constexpr int NVARIANT = 5;
 struct StageSet {
   int tx, ty, nt;
-  int ctas32;                       // FP32 CTAs per SM the registers are budgeted for
   size_t smem[NVARIANT];
   int minb[NVARIANT];
   const void* stage[NVARIANT][2];   // k_stage, stages 1 and 2
@@ -1019,7 +1019,6 @@ StageSet make_stage_set() {
   s.tx = TL::TX;
   s.ty = TL::TY;
   s.nt = TL::NT;
-  s.ctas32 = TL::template minb<float>();
   s.smem[0] = TL::template smem<double>();
   s.smem[1] = TL::template smem<float>();
   s.smem[2] = stage_smem_surr<TL>();
@@ -1070,7 +1069,6 @@ StageSet make_stage_set_fp32() {
   s.tx = TL::TX;
   s.ty = TL::TY;
   s.nt = TL::NT;
-  s.ctas32 = TL::template minb<float>();
   s.smem[1] = TL::template smem<float>();
   s.minb[1] = TL::template minb<float>();
   s.stage[1][0] = (const void*)k_stage<TL, float, 1, false>;
@@ -1080,10 +1078,26 @@ StageSet make_stage_set_fp32() {
   return s;
 }
 
+// Plain FP64 kernels only (variant 0), for a shape whose registers and shared memory are
+// budgeted for two FP64 CTAs per SM.
+template <class TL>
+StageSet make_stage_set_fp64() {
+  StageSet s;
+  memset(&s, 0, sizeof(s));
+  s.tx = TL::TX;
+  s.ty = TL::TY;
+  s.nt = TL::NT;
+  s.smem[0] = TL::template smem<double>();
+  s.minb[0] = TL::template minb<double>();
+  s.stage[0][0] = (const void*)k_stage<TL, double, 1, false>;
+  s.stage[0][1] = (const void*)k_stage<TL, double, 2, false>;
+  return s;
+}
+
 // the tile shapes the library is built with (one translation unit each)
-constexpr int NSHAPES = 6;
+constexpr int NSHAPES = 7;
 // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8, 4: 16x16 and 5: 32x8 with three FP32 CTAs
-// per SM
+// per SM, 6: 16x12 with two FP64 CTAs per SM
 const StageSet* stage_set(int shape);
 
 }  // namespace ct

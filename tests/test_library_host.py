@@ -67,9 +67,11 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     from synth import cases
     n = P.ct_tile_shape_count()
     shapes = [P.ct_tile_shape(s) for s in range(n)]
-    ctas = [P.ct_tile_shape_ctas(s) for s in range(n)]
-    assert shapes[0] == (32, 8) and len(set(zip(shapes, ctas))) == n
-    assert set(ctas) == {1, 2, 3} and P.ct_tile_shape_ctas(n) == 0
+    ctas = [P.ct_tile_shape_ctas(s, P.CT_FP32) for s in range(n)]
+    ctas64 = [P.ct_tile_shape_ctas(s, P.CT_FP64) for s in range(n)]
+    assert shapes[0] == (32, 8) and len(set(zip(shapes, ctas, ctas64))) == n
+    assert set(ctas) == {0, 1, 2, 3} and set(ctas64) == {0, 1, 2} and P.ct_tile_shape_ctas(n, P.CT_FP32) == 0
+    assert P.ct_tile_shape_ctas(0, 7) == 0
     c, _ = cases.plume_case(nx=64, nr=16)
     # FP64 tiles of 32 x 16 cells do not fit the shared memory of an SM
     k = shapes.index((32, 16))
@@ -80,6 +82,12 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     P.ct_set_tile_shape(c, P.CT_FP32, -1)
     with pytest.raises(P.ContrailError):
         P.ct_set_tile_shape(c, P.CT_FP32, n)
+    # the FP64 two-CTA shape carries the plain FP64 kernels only
+    k2 = ctas64.index(2)
+    P.ct_set_tile_shape(c, P.CT_FP64, k2)
+    P.ct_set_tile_shape(c, P.CT_FP64, -1)
+    with pytest.raises(P.ContrailError):
+        P.ct_set_tile_shape(c, P.CT_FP32, k2)
     # the three-CTA shapes carry the plain FP32 kernels only
     k3 = ctas.index(3)
     P.ct_set_tile_shape(c, P.CT_FP32, k3)
