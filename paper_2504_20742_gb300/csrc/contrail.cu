@@ -35,14 +35,7 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
     for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     Prim<T> w;
     cons_to_prim<T, BI>(u14, w);
-    const T c = m_sqrt(w.c2);
-    T rate = (m_fabs(w.u) + c) * T(dc.idx);
-    if (dc.geom == 1) rate += (m_fabs(w.v) + c) * T(dc.idr);
-    if (dc.viscous) {
-      T mu_e;
-      rate += viscous_rate<T>(w, T(dc.nu_t), T(dc.idx * dc.idx + (dc.geom == 1 ? dc.idr * dc.idr : 0.0)), mu_e);
-    }
-    const T d = T(1) / rate;
+    const T d = cell_dt<T>(dc, geo_of(dc, T(0)), w);
     dtmin = d < dtmin ? d : dtmin;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -91,6 +91,10 @@ __device__ __forceinline__ float m_cbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double m_cbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
+// Sound speed from c^2 for the CFL time step: the FP32 path takes c^2 rsqrt(c^2) (no IEEE
+// square root); every kernel that computes a time step uses this one form.
+__device__ __forceinline__ float sound_speed(float c2) { return c2 * rsqrtf(c2); }
+__device__ __forceinline__ double sound_speed(double c2) { return sqrt(c2); }
 __device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
 
@@ -445,9 +449,14 @@ __device__ __forceinline__ bool present_h(const Prim<T>& w) {
 // zero source; only cells near or above saturation pay for the FP64 island.
 template <class T>
 __device__ __forceinline__ bool clearly_inactive(const Prim<T>& w) {
-  float pvf = float(w.rho) * float(w.Yv) * float(k::RV) * float(w.Tg);
+  const float Tf = float(w.Tg);
+  float pvf = float(w.rho) * float(w.Yv) * float(k::RV) * Tf;
   pvf = pvf < 1e-30f ? 1e-30f : pvf;
-  return logf(pvf) - ln_psat_liq<float>(float(w.Tg)) < -1e-3f;
+  // Sonntag's ln p_sat,l with the fast log and division: their errors (about 1e-5 in ln S
+  // here) are far below the margin, and the screen runs in every cell of every stage
+  const float lnps = __fdividef(-6096.9385f, Tf) + float(16.635794 + k::LN100) +
+                     Tf * (-2.711193e-2f + Tf * 1.673952e-5f) + 2.433502f * __logf(Tf);
+  return __logf(pvf) - lnps < -1e-3f;
 }
 
 template <class T, bool BI = false>

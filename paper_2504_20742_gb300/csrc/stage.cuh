@@ -98,6 +98,21 @@ __device__ __forceinline__ Geo<double> geo_of(const DevCase& d, double) {
   return {d.dx, d.idx, d.dr, d.idr, d.wall_len, d.area_a, 1.0 / d.x_throat, d.nu_t};
 }
 
+// Stable time step of a cell for CFL number 1 (reading A10; the diffusion limit with the
+// viscous fluxes).  The stage kernel and the time-step kernel both use this one function,
+// so that a step after a reload takes exactly the time step a continued run takes.
+template <class T>
+__device__ __forceinline__ T cell_dt(const DevCase& dc, const Geo<T>& g, const Prim<T>& w) {
+  const T c = sound_speed(w.c2);
+  T rate = (m_fabs(w.u) + c) * g.idx;
+  if (dc.geom == 1) rate += (m_fabs(w.v) + c) * g.idr;
+  if (dc.viscous) {
+    T mu_e;
+    rate += viscous_rate<T>(w, g.nu_t, g.idx * g.idx + (dc.geom == 1 ? g.idr * g.idr : T(0)), mu_e);
+  }
+  return trcp(rate);
+}
+
 // ---- boundary ghost cells (Sec. 4.1; reading A1) ---------------------------------------
 // Conserved state at (i, j), i in [-2, nx+1], j in [-2, nr+1], not both outside.
 // Out of line on purpose: keeps the nozzle inlet's FP64 arithmetic from being hoisted into
@@ -808,14 +823,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     if (STAGE == 2) {
       Prim<T> wn;
       cons_to_prim<T, BI>(out, wn);
-      const T c = m_sqrt(wn.c2);
-      T rate = (m_fabs(wn.u) + c) * g.idx;
-      if (dc.geom == 1) rate += (m_fabs(wn.v) + c) * g.idr;
-      if (dc.viscous) {
-        T mu_e;
-        rate += viscous_rate<T>(wn, g.nu_t, g.idx * g.idx + (dc.geom == 1 ? g.idr * g.idr : T(0)), mu_e);
-      }
-      dtmin = trcp(rate);   // times cfl at the end
+      dtmin = cell_dt<T>(dc, g, wn);   // times cfl at the end
       pM = vol * out[0];
       pW = vol * (out[4] + T(k::YL3) * (BI ? out[8] + out[17] : out[8]) + T(k::YS3) * out[12]);
       pE = vol * out[3];
