@@ -23,9 +23,11 @@ def P():
     return P
 
 
-def _run_pair(P, c, uf, nsteps, precision=0, cfl=0.5):
+def _run_pair(P, c, uf, nsteps, precision=0, cfl=0.5, autotune=False):
     s = P.Solver(c, uf, precision=precision)
     s.init_state(cfl)
+    if autotune:   # the benchmark's launch configuration: the autotuned tile shape
+        s.autotune(reps=2)
     o = O.Oracle(c, uf)
     Uo = o.init_state()
     U0g = s.state64()
@@ -145,7 +147,7 @@ def test_fp64_parity(P, name):
 def test_fp64_parity_plume_1024x256_100_steps(P):
     """The FP64 benchmark workload at full size, in the benchmark's launch configuration."""
     c, uf = cases.plume_case()
-    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 100)
+    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 100, autotune=True)
     e = field_rel_err(Ug, Uo)
     assert np.all(e <= TOL), report(e)
     for k in (1, 2, 3):
@@ -155,10 +157,21 @@ def test_fp64_parity_plume_1024x256_100_steps(P):
 def test_fp64_parity_plume_1024x256_viscous_50_steps(P):
     """The benchmark plume with viscous and diffusive fluxes (nu_t = 0.5 m^2/s)."""
     c, uf = _viscous(cases.plume_case(), 0.5)
-    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 50)
+    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 50, autotune=True)
     e = field_rel_err(Ug, Uo)
     assert np.all(e <= TOL), report(e)
     assert np.allclose(dg[:, 0], do[:, 0], rtol=1e-11, atol=0)
+
+
+def test_fp64_parity_plume_1024x256_bimodal_50_steps(P):
+    """The bimodal benchmark workload (18 fields) at full size, autotuned as in the bench."""
+    c, uf = _bimodal(cases.plume_case())
+    s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 50, autotune=True)
+    e = field_rel_err(Ug, Uo)
+    assert np.all(e <= TOL), report(e)
+    assert np.allclose(dg[:, 0], do[:, 0], rtol=1e-11, atol=0)
+    for k in (1, 2, 3):
+        assert np.allclose(dg[:, k], do[:, k], rtol=1e-12, atol=0), k
 
 
 def test_source_batch_parity_with_tables(P):
