@@ -122,7 +122,9 @@ typedef struct {
  *   returns CT_ERR_TIMEOUT). */
 
 /* Bytes of device workspace needed by a case at a precision (boundary states, reduction
- * partials, time step and diagnostics).  Returns 0 for an invalid case. */
+ * partials, time step and diagnostics; for CT_FP64 without the bimodal liquid also the
+ * primitive variables of U and U1, 2 x 14 x N doubles, which each stage writes for the next
+ * one so that the halo cells need no second conversion).  Returns 0 for an invalid case. */
 size_t ct_workspace_bytes(const ct_case *c, int precision);
 
 /* Validate the case and prepare the workspace: inflow profile per row (row velocity
@@ -146,7 +148,9 @@ ct_status ct_load_state(const ct_case *c, int precision, void *work, const void 
 /* Advance U by nsteps explicit SSP-RK2 steps (Sec. 3.2) with the global CFL number `cfl`.
  * U1 is a stage buffer of the same size.  The time step of each step is the CFL limit
  * of the state at its start, computed on the device; no host synchronisation happens.
- * Enqueued on `stream`. */
+ * Enqueued on `stream`.  The workspace carries the time step (and, in CT_FP64, the
+ * primitive variables) of the state the last call left in U: after writing U by other
+ * means, call ct_load_state before stepping again. */
 ct_status ct_step(const ct_case *c, int precision, void *U, void *U1, void *work, int nsteps,
                   double cfl, void *stream);
 

@@ -35,6 +35,13 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
     for (int f = 0; f < NFX; ++f) u14[f] = U[f * N + n];
     Prim<T> w;
     cons_to_prim<T, BI>(u14, w);
+    if (dc.prims) {   // the primitives of the state, for the first stage's halo
+      T qv[NFX];
+      prim_vector<T, BI>(w, qv);
+      T* dst = reinterpret_cast<T*>(dc.prims);
+#pragma unroll
+      for (int f = 0; f < NFX; ++f) dst[f * N + n] = qv[f];
+    }
     const T d = cell_dt<T>(dc, geo_of(dc, T(0)), w);
     dtmin = d < dtmin ? d : dtmin;
   }
@@ -407,7 +414,13 @@ static ct_status validate(const ct_case* c, int precision) {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static size_t ws_bytes(const ct_case* c) {
+// Single-case FP64 steps keep the primitive variables of U and U1 in the workspace: each
+// stage writes those of the state it produces, and the next stage reads them for its halo
+// instead of converting the conserved variables again (the FP64 pipe bounds these kernels).
+static bool uses_prims(const ct_case* c, int precision) { return precision == CT_FP64 && !c->bimodal; }
+static size_t prim_bytes(const ct_case* c) { return 2 * (size_t)NF * c->nx * case_nr(c) * sizeof(double); }
+
+static size_t ws_bytes(const ct_case* c, bool prims = false) {
   const size_t nr = (size_t)case_nr(c);
   size_t b = HDR_BYTES;
   b += align256(nr * case_nf(c) * sizeof(double));
@@ -415,6 +428,7 @@ static size_t ws_bytes(const ct_case* c) {
   b += align256((size_t)max_blocks(c) * NPART * sizeof(double));
   b += align256((size_t)max_rows(c) * sizeof(unsigned int));
   b += align256((size_t)max_rows(c) * NPART * sizeof(double));
+  if (prims) b += align256(prim_bytes(c));
   return b;
 }
 
@@ -444,7 +458,7 @@ static ct_status property_tables(const double** tab, const float** tabf) {
   return CT_OK;
 }
 
-static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
+static DevCase make_dev(const ct_case* c, void* work, int shape = 0, bool prims = false) {
   DevCase d;
   memset(&d, 0, sizeof(d));
   d.geom = c->geom;
@@ -498,6 +512,8 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0) {
   d.row_count = (unsigned int*)(base + off);
   off += align256((size_t)max_rows(c) * sizeof(unsigned int));
   d.row_part = (double*)(base + off);
+  off += align256((size_t)max_rows(c) * NPART * sizeof(double));
+  d.prims = prims && work ? (double*)(base + off) : nullptr;
   d.nblocks = num_blocks(c, shape);
   d.tiles_x = tiles_x(c, shape);
   d.tiles_y = tiles_y(c, shape);
@@ -527,7 +543,7 @@ extern "C" {
 
 size_t ct_workspace_bytes(const ct_case* c, int precision) {
   if (validate(c, precision) != CT_OK) return 0;
-  return ws_bytes(c);
+  return ws_bytes(c, uses_prims(c, precision));
 }
 
 ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host, void* work, size_t work_bytes,
@@ -536,7 +552,7 @@ ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host
   if (s != CT_OK) return s;
   if (!work) return fail(CT_ERR_ARG, "null workspace");
   if (((uintptr_t)work & 255) != 0) return fail(CT_ERR_ARG, "workspace must be 256-byte aligned");
-  if (work_bytes < ws_bytes(c)) return fail(CT_ERR_SIZE, "workspace too small (see ct_workspace_bytes)");
+  if (work_bytes < ws_bytes(c, uses_prims(c, precision))) return fail(CT_ERR_SIZE, "workspace too small (see ct_workspace_bytes)");
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, work);
   WsHeader h;
@@ -572,8 +588,9 @@ static ct_status check_setup(const ct_case* c, void* work, void* stream) {
   return CT_OK;
 }
 
-static ct_status launch_dt(const ct_case* c, int precision, void* work, const void* U, double cfl, cudaStream_t st) {
-  DevCase d = make_dev(c, work);
+static ct_status launch_dt(const ct_case* c, int precision, void* work, const void* U, double cfl, cudaStream_t st,
+                           bool prims) {
+  DevCase d = make_dev(c, work, 0, prims);
   d.cfl = cfl;
   const size_t N = (size_t)c->nx * case_nr(c);
   // a grid-stride kernel: a few hundred CTAs keep its one-level reduction short
@@ -607,7 +624,7 @@ ct_status ct_init_state(const ct_case* c, int precision, void* work, void* U, do
     else k_init<float><<<grid, 256, 0, st>>>(*c, d, (float*)U);
   }
   if ((s = cuda_check("k_init")) != CT_OK) return s;
-  return launch_dt(c, precision, work, U, cfl, st);
+  return launch_dt(c, precision, work, U, cfl, st, uses_prims(c, precision));
 }
 
 ct_status ct_load_state(const ct_case* c, int precision, void* work, const void* U_src, void* U, double cfl,
@@ -621,7 +638,7 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   const size_t bytes = N * case_nf(c) * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
   if (U_src != U && cudaMemcpyAsync(U, U_src, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return cuda_check("ct_load_state copy");
-  return launch_dt(c, precision, work, U, cfl, st);
+  return launch_dt(c, precision, work, U, cfl, st, uses_prims(c, precision));
 }
 
 static std::mutex g_attr_mu;
@@ -638,6 +655,8 @@ static ct_status set_stage_attrs(int shape, int p) {
       e = cudaFuncSetAttribute(ss->stage[p][st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
     if (e == cudaSuccess && ss->batch[p][st])
       e = cudaFuncSetAttribute(ss->batch[p][st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
+    if (e == cudaSuccess && p == 0 && ss->stage_sp[st])
+      e = cudaFuncSetAttribute(ss->stage_sp[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
   g_attr_done[shape][p] = true;
@@ -653,18 +672,20 @@ static void launch_stage(const StageSet* ss, int p, int stage, const DevCase& d,
   void* a3 = Uout;
   const void* a4 = blob;
   void* args[] = {&dc, &a1, &a2, &a3, &a4};
-  cudaLaunchKernel(ss->stage[p][stage - 1], grid, dim3(ss->nt), args, ss->smem[p], st);
+  // FP64 with the stored primitives in the workspace: the kernel that reads and writes them
+  const void* fn = (p == 0 && d.prims) ? ss->stage_sp[stage - 1] : ss->stage[p][stage - 1];
+  cudaLaunchKernel(fn, grid, dim3(ss->nt), args, ss->smem[p], st);
 }
 
 static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
-                               cudaStream_t st, const void* blob = nullptr, int shape = -1) {
+                               cudaStream_t st, bool prims, const void* blob = nullptr, int shape = -1) {
   const int p = variant_of(c, precision);
   if (shape < 0) shape = shape_for(c, precision);
   if (!shape_usable(shape, p)) shape = 0;
   ct_status s = set_stage_attrs(shape, p);
   if (s != CT_OK) return s;
   const StageSet* ss = stage_set(shape);
-  DevCase d = make_dev(c, work, shape);
+  DevCase d = make_dev(c, work, shape, prims);
   d.cfl = cfl;
   dim3 grid(tiles_x(c, shape), tiles_y(c, shape));
   for (int k2 = 0; k2 < nsteps; ++k2) {
@@ -683,7 +704,7 @@ ct_status ct_step_surrogate(const ct_case* c, void* U, void* U1, void* work, con
   if (((uintptr_t)blob & 15) != 0) return fail(CT_ERR_ARG, "surrogate blob must be 16-byte aligned");
   if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
   if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
-  return enqueue_steps(c, CT_FP32_MLP, U, U1, work, nsteps, cfl, (cudaStream_t)stream, blob);
+  return enqueue_steps(c, CT_FP32_MLP, U, U1, work, nsteps, cfl, (cudaStream_t)stream, false, blob);
 }
 
 ct_status ct_step(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
@@ -695,7 +716,7 @@ ct_status ct_step(const ct_case* c, int precision, void* U, void* U1, void* work
   if (nsteps < 0) return fail(CT_ERR_ARG, "nsteps < 0");
   if (!(cfl > 0.0 && cfl <= 1.0)) return fail(CT_ERR_ARG, "cfl must be in (0, 1]");
   if (precision == CT_FP32_MLP) return fail(CT_ERR_ARG, "CT_FP32_MLP steps go through ct_step_surrogate");
-  return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, (cudaStream_t)stream);
+  return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, (cudaStream_t)stream, uses_prims(c, precision));
 }
 
 ct_status ct_step_host(const ct_case* c, int precision, const void* U_host_in, void* U_host_out, void* U, void* U1,
@@ -707,7 +728,7 @@ ct_status ct_step_host(const ct_case* c, int precision, const void* U_host_in, v
   const size_t N = (size_t)c->nx * case_nr(c);
   const size_t bytes = N * case_nf(c) * (precision == CT_FP64 ? sizeof(double) : sizeof(float));
   if (cudaMemcpyAsync(U, U_host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return cuda_check("h2d");
-  if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
+  if ((s = launch_dt(c, precision, work, U, cfl, st, uses_prims(c, precision))) != CT_OK) return s;
   if ((s = ct_step(c, precision, U, U1, work, nsteps, cfl, stream)) != CT_OK) return s;
   if (cudaMemcpyAsync(U_host_out, U, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return cuda_check("d2h");
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_step_host sync");
@@ -838,8 +859,8 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   if (c->geom == 1)
     k_setup<<<1, 256, 0, st>>>(*c, ufac_rows_dev, (double*)d.inflow, (double*)d.amb, d.nr, d.dr, case_nf(c));
   if ((s = cuda_check("ct_step_static setup")) != CT_OK) return s;
-  if ((s = launch_dt(c, precision, work, U, cfl, st)) != CT_OK) return s;
-  return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st);
+  if ((s = launch_dt(c, precision, work, U, cfl, st, false)) != CT_OK) return s;
+  return enqueue_steps(c, precision, U, U1, work, nsteps, cfl, st, false);
 }
 
 // ---- tile shapes and the autotuner ------------------------------------------------------
@@ -888,7 +909,7 @@ ct_status ct_autotune(const ct_case* c, int precision, const void* U, void* U1, 
     if (shape_usable(sh, p)) {
       if ((s = set_stage_attrs(sh, p)) != CT_OK) return s;
       const StageSet* ss = stage_set(sh);
-      DevCase d = make_dev(c, work, sh);
+      DevCase d = make_dev(c, work, sh, uses_prims(c, precision));
       const dim3 grid(tiles_x(c, sh), tiles_y(c, sh));
       // stage 1 only: it reads U and writes the scratch state U1, so U is left as it was
       auto launch = [&]() { launch_stage(ss, p, 1, d, grid, U, nullptr, U1, blob, st); };

@@ -155,42 +155,57 @@ struct Prim {
   T mh[4];   // bimodal liquid: droplets of heterogeneous origin (set only when BI)
 };
 
+// Arithmetic with its rounding pinned (the compiler neither fuses nor splits these), so that
+// a function built from them gives the same bits in every kernel it is inlined into.
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
 // BI: the state has the 18 fields of the bimodal liquid; Y_l is the sum of both sets.
+// Every operation has its rounding pinned: the primitive variables a kernel stores for the
+// next stage are then bit for bit those the next stage would compute itself.
 template <class T, bool BI = false>
 __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   const T rho = U[0];
   // rho c_v straight from the conserved partial densities, then one reciprocal serves
   // 1/rho = (rho c_v) X and 1/c_v = rho^2 X, X = 1/(rho rho c_v)
-  const T rYl = BI ? T(k::YL3) * (U[8] + U[17]) : T(k::YL3) * U[8], rYs = T(k::YS3) * U[12];
-  const T rcv = (rho - U[4] - rYl - rYs) * T(k::CVA) + U[4] * T(k::CVV) + rYl * T(k::CL) + rYs * T(k::CS);
-  const T X = trcp(rho * rcv);
-  const T ir = rcv * X;
+  const T rYl = rn_mul(T(k::YL3), BI ? rn_add(U[8], U[17]) : U[8]), rYs = rn_mul(T(k::YS3), U[12]);
+  const T rYa = rn_sub(rn_sub(rn_sub(rho, U[4]), rYl), rYs);
+  const T rcv = rn_fma(rYs, T(k::CS), rn_fma(rYl, T(k::CL), rn_fma(U[4], T(k::CVV), rn_mul(rYa, T(k::CVA)))));
+  const T X = trcp(rn_mul(rho, rcv));
+  const T ir = rn_mul(rcv, X);
   w.rho = rho;
-  w.u = U[1] * ir;
-  w.v = U[2] * ir;
-  w.Yv = U[4] * ir;
+  w.u = rn_mul(U[1], ir);
+  w.v = rn_mul(U[2], ir);
+  w.Yv = rn_mul(U[4], ir);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    w.ml[q] = U[5 + q] * ir;
-    w.ms[q] = U[9 + q] * ir;
+    w.ml[q] = rn_mul(U[5 + q], ir);
+    w.ms[q] = rn_mul(U[9 + q], ir);
   }
-  w.ns = U[13] * ir;
+  w.ns = rn_mul(U[13], ir);
   if constexpr (BI) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) w.mh[q] = U[14 + q] * ir;
-    w.Yl = T(k::YL3) * (w.ml[3] + w.mh[3]);
+    for (int q = 0; q < 4; ++q) w.mh[q] = rn_mul(U[14 + q], ir);
+    w.Yl = rn_mul(T(k::YL3), rn_add(w.ml[3], w.mh[3]));
   } else {
-    w.Yl = T(k::YL3) * w.ml[3];
+    w.Yl = rn_mul(T(k::YL3), w.ml[3]);
   }
-  w.Ys = T(k::YS3) * w.ms[3];
-  const T Ya = T(1) - w.Yv - w.Yl - w.Ys;
-  const T e = U[3] * ir - T(0.5) * (w.u * w.u + w.v * w.v);
-  w.cv = rcv * ir;
-  const T icv = rho * rho * X;
-  w.Tg = (e - w.Yv * T(k::E0V) - w.Ys * T(k::E0S)) * icv;
-  w.Rg = Ya * T(k::RA) + w.Yv * T(k::RV);
-  w.p = rho * w.Rg * w.Tg;
-  w.c2 = (T(1) + w.Rg * icv) * w.p * ir;
+  w.Ys = rn_mul(T(k::YS3), w.ms[3]);
+  const T Ya = rn_sub(rn_sub(rn_sub(T(1), w.Yv), w.Yl), w.Ys);
+  const T ke = rn_mul(T(0.5), rn_fma(w.u, w.u, rn_mul(w.v, w.v)));
+  const T e = rn_fma(U[3], ir, -ke);
+  w.cv = rn_mul(rcv, ir);
+  const T icv = rn_mul(rn_mul(rho, rho), X);
+  w.Tg = rn_mul(rn_fma(-w.Ys, T(k::E0S), rn_fma(-w.Yv, T(k::E0V), e)), icv);
+  w.Rg = rn_fma(w.Yv, T(k::RV), rn_mul(Ya, T(k::RA)));
+  w.p = rn_mul(rn_mul(rho, w.Rg), w.Tg);
+  w.c2 = rn_mul(rn_mul(rn_fma(w.Rg, icv, T(1)), w.p), ir);
 }
 
 // Conserved state from (p, T, u, v, Y_v, scaled moments, soot per kg).

@@ -65,6 +65,11 @@ struct DevCase {
   double* partials;       // nblocks x NPART, tile by * tiles_x + bx
   unsigned int* row_count;  // tiles_y arrival tickets (zero between launches)
   double* row_part;       // tiles_y x NPART row records
+  // FP64 single-case steps: primitive planes (0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..12 moments per
+  // kg, 13 soot per kg) of U (first nf x N block) and of U1 (second block), written by the
+  // kernel that produces each state and read by the next stage; null: every stage converts
+  // its halo cells itself
+  double* prims;
 };
 
 // Tile of TX x TY cells per CTA with a two-cell halo (HX x HY).  NT threads: the larger of
@@ -476,11 +481,33 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
 }
 
 
+// The primitive vector of the stencil (fields of the state, conserved -> primitive).
+template <class T, bool BI>
+__device__ __forceinline__ void prim_vector(const Prim<T>& w, T* qv) {
+  qv[0] = w.rho;
+  qv[1] = w.u;
+  qv[2] = w.v;
+  qv[3] = w.p;
+  qv[4] = w.Yv;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    qv[5 + q] = w.ml[q];
+    qv[9 + q] = w.ms[q];
+  }
+  qv[13] = w.ns;
+  if (BI) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qv[14 + q] = w.mh[q];
+  }
+}
+
 // One stage on tile (bx, by) of a case; `tile` = by * tiles_x + bx indexes the partial
 // records.  All threads of the CTA call this.  STAGE 1: Uout = Uin + dt L(Uin).
 // STAGE 2: Uout = (Un + Uin + dt L(Uin))/2 (Uout may be Un); the last tile of the case to
 // finish reduces the partials and publishes cfl * (stable step) as the next time step.
-template <class TL, class T, int STAGE, bool SURR, bool BI = false>
+// SP: the primitive planes of dc.prims are in use (the input state's are read for the
+// interior halo cells instead of converting them, the output state's are written).
+template <class TL, class T, int STAGE, bool SURR, bool BI = false, bool SP = false>
 __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, int tile, const T* __restrict__ Uin,
                                            const T* Un, T* Uout, const unsigned char* __restrict__ blob,
                                            unsigned char* smem_raw, double cfl, TcCtx* tcx) {
@@ -534,8 +561,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       kind[r] = !need ? 0 : (xin && rin ? 1 : 2);
       if (kind[r] == 1) {
         const size_t n = (size_t)j * nx + i;
+        // SP: the primitives of the input state, written by the kernel that produced it
+        const T* src = SP ? reinterpret_cast<const T*>(dc.prims) + (STAGE == 1 ? 0 : (size_t)NFX * N) : Uin;
 #pragma unroll
-        for (int f = 0; f < NFX; ++f) u14[r][f] = Uin[f * N + n];
+        for (int f = 0; f < NFX; ++f) u14[r][f] = src[f * N + n];
       }
     }
 #pragma unroll
@@ -549,23 +578,14 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
         for (int f = 0; f < NFX; ++f) u14[r][f] = g14[f];
       }
-      Prim<T> w;
-      cons_to_prim<T, BI>(u14[r], w);
       T qv[NFX];
-      qv[0] = w.rho;
-      qv[1] = w.u;
-      qv[2] = w.v;
-      qv[3] = w.p;
-      qv[4] = w.Yv;
+      if (SP && kind[r] == 1) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        qv[5 + q] = w.ml[q];
-        qv[9 + q] = w.ms[q];
-      }
-      qv[13] = w.ns;
-      if (BI) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) qv[14 + q] = w.mh[q];
+        for (int f = 0; f < NFX; ++f) qv[f] = u14[r][f];
+      } else {
+        Prim<T> w;
+        cons_to_prim<T, BI>(u14[r], w);
+        prim_vector<T, BI>(w, qv);
       }
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) qs2[k2][hj][hi] = p_make(qv[2 * k2], qv[2 * k2 + 1]);
@@ -820,10 +840,19 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       Uout[f * N + n] = out[f];
       nbad += finite_bits(out[f]) ? 0 : 1;
     }
-    if (STAGE == 2) {
+    if (STAGE == 2 || SP) {
       Prim<T> wn;
       cons_to_prim<T, BI>(out, wn);
-      dtmin = cell_dt<T>(dc, g, wn);   // times cfl at the end
+      if (SP) {   // the primitives of the output state, for the next stage's halo
+        T qv[NFX];
+        prim_vector<T, BI>(wn, qv);
+        T* dst = reinterpret_cast<T*>(dc.prims) + (STAGE == 1 ? (size_t)NFX * N : 0);
+#pragma unroll
+        for (int f = 0; f < NFX; ++f) dst[f * N + n] = qv[f];
+      }
+      if (STAGE == 2) dtmin = cell_dt<T>(dc, g, wn);   // times cfl at the end
+    }
+    if (STAGE == 2) {
       pM = vol * out[0];
       pW = vol * (out[4] + T(k::YL3) * (BI ? out[8] + out[17] : out[8]) + T(k::YS3) * out[12]);
       pE = vol * out[3];
@@ -911,7 +940,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 // Register budget from __launch_bounds__: the register file is split between the SM's four
 // schedulers, so 18 warps (two CTAs of 288 threads) leave 96 registers per thread and 9
 // warps (one FP64 CTA) 168; a larger cap fails at launch.
-template <class TL, class T, int STAGE, bool SURR, bool BI = false>
+template <class TL, class T, int STAGE, bool SURR, bool BI = false, bool SP = false>
 __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     k_stage(DevCase dc, const T* __restrict__ Uin, const T* Un, T* Uout, const unsigned char* __restrict__ blob) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -926,7 +955,7 @@ __global__ void __launch_bounds__(TL::NT, TL::template minb<T>())
     tcx.wphase = 0;
     tcx.ready = true;
   }
-  stage_tile<TL, T, STAGE, SURR, BI>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
+  stage_tile<TL, T, STAGE, SURR, BI, SP>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, blob,
                                  smem_raw, dc.cfl, &tcx);
   if (SURR) tc_release(tcx.tmem);
 }
@@ -1016,6 +1045,7 @@ struct StageSet {
   size_t smem[NVARIANT];
   int minb[NVARIANT];
   const void* stage[NVARIANT][2];   // k_stage, stages 1 and 2
+  const void* stage_sp[2];          // FP64 k_stage with the stored primitives (variant 0)
   const void* batch[NVARIANT][2];   // k_batch_stage (FP32 variants only)
 };
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
@@ -1035,6 +1065,8 @@ StageSet make_stage_set() {
   if constexpr (TL::template smem<double>() <= SMEM_LIMIT) {
     s.stage[0][0] = (const void*)k_stage<TL, double, 1, false>;
     s.stage[0][1] = (const void*)k_stage<TL, double, 2, false>;
+    s.stage_sp[0] = (const void*)k_stage<TL, double, 1, false, false, true>;
+    s.stage_sp[1] = (const void*)k_stage<TL, double, 2, false, false, true>;
   }
   s.stage[1][0] = (const void*)k_stage<TL, float, 1, false>;
   s.stage[1][1] = (const void*)k_stage<TL, float, 2, false>;
@@ -1099,6 +1131,8 @@ StageSet make_stage_set_fp64() {
   s.minb[0] = TL::template minb<double>();
   s.stage[0][0] = (const void*)k_stage<TL, double, 1, false>;
   s.stage[0][1] = (const void*)k_stage<TL, double, 2, false>;
+  s.stage_sp[0] = (const void*)k_stage<TL, double, 1, false, false, true>;
+  s.stage_sp[1] = (const void*)k_stage<TL, double, 2, false, false, true>;
   return s;
 }
 
