@@ -123,8 +123,8 @@ typedef struct {
 
 /* Bytes of device workspace needed by a case at a precision (boundary states, reduction
  * partials, time step and diagnostics; for CT_FP64 without the bimodal liquid also the
- * primitive variables of U and U1, 2 x 14 x N doubles, which each stage writes for the next
- * one so that the halo cells need no second conversion).  Returns 0 for an invalid case. */
+ * primitive variables of U and U1 with the temperature and c_v, 2 x 16 x N doubles, which
+ * each stage writes for the next one so that no cell is converted twice).  Returns 0 for an invalid case. */
 size_t ct_workspace_bytes(const ct_case *c, int precision);
 
 /* Validate the case and prepare the workspace: inflow profile per row (row velocity

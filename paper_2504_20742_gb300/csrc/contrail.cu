@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(NT_AUX) k_dt(DevCase dc, const T* __restrict__
       T* dst = reinterpret_cast<T*>(dc.prims);
 #pragma unroll
       for (int f = 0; f < NFX; ++f) dst[f * N + n] = qv[f];
+      dst[NFX * N + n] = w.Tg;
+      dst[(NFX + 1) * N + n] = w.cv;
     }
     const T d = cell_dt<T>(dc, geo_of(dc, T(0)), w);
     dtmin = d < dtmin ? d : dtmin;
@@ -418,7 +420,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // stage writes those of the state it produces, and the next stage reads them for its halo
 // instead of converting the conserved variables again (the FP64 pipe bounds these kernels).
 static bool uses_prims(const ct_case* c, int precision) { return precision == CT_FP64 && !c->bimodal; }
-static size_t prim_bytes(const ct_case* c) { return 2 * (size_t)NF * c->nx * case_nr(c) * sizeof(double); }
+static size_t prim_bytes(const ct_case* c) { return 2 * (size_t)NPLANE * c->nx * case_nr(c) * sizeof(double); }
 
 static size_t ws_bytes(const ct_case* c, bool prims = false) {
   const size_t nr = (size_t)case_nr(c);

@@ -66,9 +66,9 @@ struct DevCase {
   unsigned int* row_count;  // tiles_y arrival tickets (zero between launches)
   double* row_part;       // tiles_y x NPART row records
   // FP64 single-case steps: primitive planes (0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..12 moments per
-  // kg, 13 soot per kg) of U (first nf x N block) and of U1 (second block), written by the
-  // kernel that produces each state and read by the next stage; null: every stage converts
-  // its halo cells itself
+  // kg, 13 soot per kg, 14 T, 15 c_v) of U (first NPLANE x N block) and of U1 (second block),
+  // written by the kernel that produces each state and read by the next stage; null: every
+  // stage converts its halo cells and its own cells itself
   double* prims;
 };
 
@@ -481,6 +481,9 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
 }
 
 
+// planes of stored primitive variables per state: the stencil's fields, T and c_v
+constexpr int NPLANE = NF + 2;
+
 // The primitive vector of the stencil (fields of the state, conserved -> primitive).
 template <class T, bool BI>
 __device__ __forceinline__ void prim_vector(const Prim<T>& w, T* qv) {
@@ -562,7 +565,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       if (kind[r] == 1) {
         const size_t n = (size_t)j * nx + i;
         // SP: the primitives of the input state, written by the kernel that produced it
-        const T* src = SP ? reinterpret_cast<const T*>(dc.prims) + (STAGE == 1 ? 0 : (size_t)NFX * N) : Uin;
+        const T* src = SP ? reinterpret_cast<const T*>(dc.prims) + (STAGE == 1 ? 0 : (size_t)NPLANE * N) : Uin;
 #pragma unroll
         for (int f = 0; f < NFX; ++f) u14[r][f] = src[f * N + n];
       }
@@ -745,7 +748,27 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const size_t n = (size_t)j * nx + i;
 #pragma unroll
     for (int f = 0; f < NFX; ++f) u14[f] = Uin[f * N + n];
-    cons_to_prim<T, BI>(u14, w);
+    if (SP) {   // the cell's primitives: the stencil's from shared memory, T and c_v stored
+      w.rho = qs(0, cj + 2, ci + 2);
+      w.u = qs(1, cj + 2, ci + 2);
+      w.v = qs(2, cj + 2, ci + 2);
+      w.p = qs(3, cj + 2, ci + 2);
+      w.Yv = qs(4, cj + 2, ci + 2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        w.ml[q] = qs(5 + q, cj + 2, ci + 2);
+        w.ms[q] = qs(9 + q, cj + 2, ci + 2);
+      }
+      w.ns = qs(13, cj + 2, ci + 2);
+      w.Yl = rn_mul(T(k::YL3), w.ml[3]);   // as the conversion forms them
+      w.Ys = rn_mul(T(k::YS3), w.ms[3]);
+      const T* src = reinterpret_cast<const T*>(dc.prims) + (STAGE == 1 ? 0 : (size_t)NPLANE * N);
+      w.Tg = src[NFX * N + n];
+      w.cv = src[(NFX + 1) * N + n];
+      w.Rg = w.c2 = T(0);   // not used by the cell update
+    } else {
+      cons_to_prim<T, BI>(u14, w);
+    }
     if (dc.geom == 1) {
       const T ijh = trcp(T(j) + T(0.5));
       const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
@@ -843,12 +866,14 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     if (STAGE == 2 || SP) {
       Prim<T> wn;
       cons_to_prim<T, BI>(out, wn);
-      if (SP) {   // the primitives of the output state, for the next stage's halo
+      if (SP) {   // the primitives of the output state, for the next stage
         T qv[NFX];
         prim_vector<T, BI>(wn, qv);
-        T* dst = reinterpret_cast<T*>(dc.prims) + (STAGE == 1 ? (size_t)NFX * N : 0);
+        T* dst = reinterpret_cast<T*>(dc.prims) + (STAGE == 1 ? (size_t)NPLANE * N : 0);
 #pragma unroll
         for (int f = 0; f < NFX; ++f) dst[f * N + n] = qv[f];
+        dst[NFX * N + n] = wn.Tg;
+        dst[(NFX + 1) * N + n] = wn.cv;
       }
       if (STAGE == 2) dtmin = cell_dt<T>(dc, g, wn);   // times cfl at the end
     }
