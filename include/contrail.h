@@ -292,7 +292,7 @@ ct_status ct_tile_shape(int shape, int *tx, int *ty);
 /* CTAs per SM that the registers of shape `shape`'s kernels at `precision` are budgeted for
  * (more CTAs: more resident warps to hide latency, fewer registers per thread); 0 when the
  * shape has no kernels at that precision.  Some shapes carry one precision only: 32 x 8 and
- * 16 x 16 with three FP32 CTAs per SM, 16 x 12 with two FP64 CTAs per SM. */
+ * 16 x 16 with three FP32 CTAs per SM, 16 x 12 and 16 x 16 with two FP64 CTAs per SM. */
 int ct_tile_shape_ctas(int shape, int precision);
 
 /* Register `shape` for cases with this case's geometry, grid and precision (-1: back to the

@@ -83,10 +83,17 @@ struct Tile {
   static constexpr int TX = TX_, TY = TY_, HX = TX + 4, HY = TY + 4, NCELL = TX * TY;
   static constexpr int NFACE = (TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1);
   static constexpr int NT = (NFACE + 31) / 32 * 32;
+  // The r slopes of rows -1..TY outnumber the threads for the 32-wide tiles; then the threads
+  // without a cell take row -1 during the x divergence (see stage_tile).
+  static constexpr bool ROWM1_EARLY = TX * (TY + 2) > NT && NT - NCELL >= TX;
+  // face buffers: left and right reconstructed states; each face's flux overwrites its left
+  // state (the thread that read it writes it), except where row -1's r slopes are written
+  // during the x divergence, which still reads the x fluxes: there a third buffer
+  static constexpr int NFBUF = ROWM1_EARLY ? 3 : 2;
   template <class T>
   static constexpr int minb() { return sizeof(T) == 4 ? (NT <= 320 ? M32 : 1) : M64; }
   template <class T, int NFX = NF>
-  static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + 3 * NFACE); }
+  static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + NFBUF * NFACE); }
 };
 // thread count of the auxiliary kernels (time step of a given state)
 constexpr int NT_AUX = 288;
@@ -521,9 +528,9 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   using V = typename PairOf<T>::V;
   constexpr int NP = NFX / 2;
   V (*qs2)[HY][HX] = reinterpret_cast<V (*)[HY][HX]>(smem_raw);                       // primitives
-  V (*fb2)[NFACE] = reinterpret_cast<V (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);  // face fluxes
-  V (*fL2)[NFACE] = fb2 + NP;      // reconstructed left state of each face
-  V (*fR2)[NFACE] = fb2 + 2 * NP;  // reconstructed right state of each face
+  V (*fL2)[NFACE] = reinterpret_cast<V (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);  // left states
+  V (*fR2)[NFACE] = fL2 + NP;                                       // right states
+  V (*fb2)[NFACE] = TL::NFBUF == 3 ? fL2 + 2 * NP : fL2;            // face fluxes
   // scalar views: field f of a cell or face
   const auto qs = [&](int f, int hj, int hi) -> T {
     const V v = qs2[f >> 1][hj][hi];
@@ -657,7 +664,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   // The r slopes of rows -1..TY outnumber the threads for the 32-wide tiles; the threads
   // without a cell take row -1 during the x divergence (the x face states are dead by then),
   // so that phase D1 is a single round.
-  constexpr bool ROWM1_EARLY = TX * (TY + 2) > NT && NT - NCELL >= TX;
+  constexpr bool ROWM1_EARLY = TL::ROWM1_EARLY;
   T acc[NFX];
   // water carried by a face flux: vapour, liquid (both sets) and ice
   const auto water_flux = [&](int f) -> T {
@@ -1162,9 +1169,9 @@ StageSet make_stage_set_fp64() {
 }
 
 // the tile shapes the library is built with (one translation unit each)
-constexpr int NSHAPES = 7;
+constexpr int NSHAPES = 8;
 // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8, 4: 16x16 and 5: 32x8 with three FP32 CTAs
-// per SM, 6: 16x12 with two FP64 CTAs per SM
+// per SM, 6: 16x12 and 7: 16x16 with two FP64 CTAs per SM
 const StageSet* stage_set(int shape);
 
 }  // namespace ct
