@@ -86,14 +86,15 @@ struct Tile {
   // The r slopes of rows -1..TY outnumber the threads for the 32-wide tiles; then the threads
   // without a cell take row -1 during the x divergence (see stage_tile).
   static constexpr bool ROWM1_EARLY = TX * (TY + 2) > NT && NT - NCELL >= TX;
-  // face buffers: left and right reconstructed states; each face's flux overwrites its left
-  // state (the thread that read it writes it), except where row -1's r slopes are written
-  // during the x divergence, which still reads the x fluxes: there a third buffer
-  static constexpr int NFBUF = ROWM1_EARLY ? 3 : 2;
+  // Face buffers: left and right reconstructed states; each face's flux overwrites its left
+  // state (the thread that read it writes it).  Row -1's r slopes, written during the x
+  // divergence while the x fluxes are still read, go to a side buffer of TX faces.
+  static constexpr int NFBUF = 2;
+  static constexpr int NSIDE = ROWM1_EARLY ? TX : 0;
   template <class T>
   static constexpr int minb() { return sizeof(T) == 4 ? (NT <= 320 ? M32 : 1) : M64; }
   template <class T, int NFX = NF>
-  static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + NFBUF * NFACE); }
+  static constexpr size_t smem() { return sizeof(T) * (size_t)NFX * (HX * HY + NFBUF * NFACE + NSIDE); }
 };
 // thread count of the auxiliary kernels (time step of a given state)
 constexpr int NT_AUX = 288;
@@ -530,7 +531,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   V (*qs2)[HY][HX] = reinterpret_cast<V (*)[HY][HX]>(smem_raw);                       // primitives
   V (*fL2)[NFACE] = reinterpret_cast<V (*)[NFACE]>(smem_raw + sizeof(T) * NFX * HX * HY);  // left states
   V (*fR2)[NFACE] = fL2 + NP;                                       // right states
-  V (*fb2)[NFACE] = TL::NFBUF == 3 ? fL2 + 2 * NP : fL2;            // face fluxes
+  V (*fb2)[NFACE] = fL2;                                            // face fluxes
+  // left states of the r faces of row 0 from the early row -1 slopes (32-wide tiles)
+  V (*fLm1)[TL::NSIDE > 0 ? TL::NSIDE : 1] =
+      reinterpret_cast<V (*)[TL::NSIDE > 0 ? TL::NSIDE : 1]>(fR2 + NP);
   // scalar views: field f of a cell or face
   const auto qs = [&](int f, int hj, int hi) -> T {
     const V v = qs2[f >> 1][hj][hi];
@@ -657,7 +661,8 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     for (int k2 = 0; k2 < NP; ++k2) {
       const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
       const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
-      if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
+      if (TL::ROWM1_EARLY && c < 0) fLm1[k2][hi] = p_add(a0, hs);
+      else if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
       if (c >= 0) fR2[k2][c * TX + hi] = p_sub(a0, hs);
     }
   };
@@ -724,7 +729,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) {
-        const V a = fL2[k2][p], b = fR2[k2][p];
+        const V a = (TL::ROWM1_EARLY && p < TX) ? fLm1[k2][p] : fL2[k2][p], b = fR2[k2][p];
         qL[2 * k2] = a.x;
         qL[2 * k2 + 1] = a.y;
         qR[2 * k2] = b.x;

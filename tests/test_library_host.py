@@ -73,13 +73,16 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     assert set(ctas) == {0, 1, 2, 3} and set(ctas64) == {0, 1, 2} and P.ct_tile_shape_ctas(n, P.CT_FP32) == 0
     assert P.ct_tile_shape_ctas(0, 7) == 0
     c, _ = cases.plume_case(nx=64, nr=16)
-    # FP64 tiles of 32 x 16 cells do not fit the shared memory of an SM
-    k = shapes.index((32, 16))
-    with pytest.raises(P.ContrailError) as e:
-        P.ct_set_tile_shape(c, P.CT_FP64, k)
-    assert e.value.status == 1
-    P.ct_set_tile_shape(c, P.CT_FP32, k)
-    P.ct_set_tile_shape(c, P.CT_FP32, -1)
+    # a shape takes a precision exactly when it has kernels for it
+    for k in range(n):
+        for prec, have in ((P.CT_FP64, ctas64[k]), (P.CT_FP32, ctas[k])):
+            if have:
+                P.ct_set_tile_shape(c, prec, k)
+                P.ct_set_tile_shape(c, prec, -1)
+            else:
+                with pytest.raises(P.ContrailError) as e:
+                    P.ct_set_tile_shape(c, prec, k)
+                assert e.value.status == 1
     with pytest.raises(P.ContrailError):
         P.ct_set_tile_shape(c, P.CT_FP32, n)
     # the FP64 two-CTA shape carries the plain FP64 kernels only
