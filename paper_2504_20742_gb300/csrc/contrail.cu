@@ -332,6 +332,7 @@ const StageSet* stage_set_16x16_o3();
 const StageSet* stage_set_32x8_o3();
 const StageSet* stage_set_16x12_d2();
 const StageSet* stage_set_16x16_d2();
+const StageSet* stage_set_16x14_d2();
 const StageSet* stage_set(int shape) {
   switch (shape) {
     case 1: return stage_set_16x16();
@@ -341,6 +342,7 @@ const StageSet* stage_set(int shape) {
     case 5: return stage_set_32x8_o3();
     case 6: return stage_set_16x12_d2();
     case 7: return stage_set_16x16_d2();
+    case 8: return stage_set_16x14_d2();
     default: return stage_set_32x8();
   }
 }

@@ -1174,9 +1174,9 @@ StageSet make_stage_set_fp64() {
 }
 
 // the tile shapes the library is built with (one translation unit each)
-constexpr int NSHAPES = 8;
+constexpr int NSHAPES = 9;
 // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8, 4: 16x16 and 5: 32x8 with three FP32 CTAs
-// per SM, 6: 16x12 and 7: 16x16 with two FP64 CTAs per SM
+// per SM, 6: 16x12, 7: 16x16 and 8: 16x14 with two FP64 CTAs per SM
 const StageSet* stage_set(int shape);
 
 }  // namespace ct
