@@ -97,14 +97,14 @@ def _workload(name):
 
 
 # Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/), in
-# the tile shape the autotuner picks for the workload (FP64: 16 x 16 with two CTAs per SM;
+# the tile shape the autotuner picks for the workload (FP64: 16 x 14 with two CTAs per SM;
 # FP32: 32 x 8 with three CTAs per SM): FP64 arithmetic per cell-stage (mean of the two
-# stages: 903.0 and 1034.9 flops, the FP64 kernels reading the stored primitive variables;
-# the 16 x 12 tile, within 1 % in time, does 977.2 with its larger halo) and DRAM bytes per
+# stages: 908.3 and 1041.1 flops, the FP64 kernels reading the stored primitive variables;
+# the 16 x 16 tile, within 2 % in time, does 969.0 with its smaller halo) and DRAM bytes per
 # cell per launch (mean of the two stages).  The traffic is reported only for that shape.
-TRAFFIC_SHAPE = {0: 7, 1: 5}
-FP64_FLOPS_PER_CELL_STAGE = 969.0
-FP64_TRAFFIC_PER_CELL_LAUNCH = 450.7
+TRAFFIC_SHAPE = {0: 8, 1: 5}
+FP64_FLOPS_PER_CELL_STAGE = 974.7
+FP64_TRAFFIC_PER_CELL_LAUNCH = 394.4
 FP32_TRAFFIC_PER_CELL_LAUNCH = 134.8
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s; counted before
 # the kernels read stored primitive variables, so an upper estimate of today's count)
