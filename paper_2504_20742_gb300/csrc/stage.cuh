@@ -234,9 +234,35 @@ __device__ __forceinline__ float warp_max_any(float v) {
   const int k = __reduce_max_sync(0xffffffffu, i >= 0 ? i : i ^ 0x7fffffff);
   return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
 }
-__device__ __forceinline__ double warp_max_nonneg(double v) { return warp_max(v); }
-__device__ __forceinline__ double warp_min_nonneg(double v) { return warp_min(v); }
-__device__ __forceinline__ double warp_max_any(double v) { return warp_max(v); }
+// The same for doubles, whose 64-bit keys compare as (high word, low word): the extreme high
+// word first, then the extreme low word among the lanes that hold it.  Two redux.sync and no
+// FP64 instruction, where a shuffle tree takes five FP64 comparisons.
+__device__ __forceinline__ double key_double(unsigned hi, unsigned lo) {
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  return key_double(mh, __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u));
+}
+__device__ __forceinline__ double warp_min_nonneg(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+  return key_double(mh, __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu));
+}
+__device__ __forceinline__ double warp_max_any(double v) {
+  long long b = __double_as_longlong(v);
+  b = b >= 0 ? b : b ^ 0x7fffffffffffffffLL;   // order-preserving signed key
+  const int hi = (int)(b >> 32);
+  const unsigned lo = (unsigned)b;
+  const int mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+  long long k = (long long)(((unsigned long long)(unsigned)mh << 32) | ml);
+  k = k >= 0 ? k : k ^ 0x7fffffffffffffffLL;
+  return __longlong_as_double(k);
+}
 
 // kind: 0 sum, 1 max, 2 min
 __device__ __forceinline__ int slot_kind(int q) { return q == 0 ? 2 : ((q >= 9 && q <= 24) ? 1 : 0); }
@@ -846,7 +872,6 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
         out[2 * k2 + 1] = o.y;
       }
     } else {
-      const T idt = trcp(dt);
       const V half2 = p_make(T(0.5), T(0.5));
       T unv[NFX];
 #pragma unroll
@@ -862,7 +887,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
       for (int f = 0; f < NFX; ++f) {
         const T un = unv[f];
-        const T rf = m_fabs(out[f] - un) * idt;
+        const T rf = m_fabs(out[f] - un);   // divided by dt once per CTA
         if (f < NF) {
           rmax[f] = rf;
         } else {   // the second liquid set shares the residual slots of the first
@@ -901,9 +926,14 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   {
     T v;
     int a;
-    v = warp_sum(bm); if (lane == 0) red[warp][4] = v;
-    v = warp_sum(bw); if (lane == 0) red[warp][5] = v;
-    v = warp_sum(be); if (lane == 0) red[warp][6] = v;
+    // boundary fluxes: only tiles on the inflow, outflow or far-field boundary have any
+    if (i0 == 0 || i0 + TX >= nx || (dc.geom == 1 && j0 + TY >= nr)) {
+      v = warp_sum(bm); if (lane == 0) red[warp][4] = v;
+      v = warp_sum(bw); if (lane == 0) red[warp][5] = v;
+      v = warp_sum(be); if (lane == 0) red[warp][6] = v;
+    } else if (lane == 0) {
+      red[warp][4] = red[warp][5] = red[warp][6] = T(0);
+    }
     if (SURR) {
       a = warp_count(ntimeout);
       if (lane == 0) red[warp][26] = T(a);
@@ -939,6 +969,9 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const T v = red[w2][tid];
       acc2 = kind == 0 ? acc2 + v : (kind == 1 ? (v > acc2 ? v : acc2) : (v < acc2 ? v : acc2));
     }
+    // residual max-norms |dU| / dt: rounding is monotone, so scaling the maximum gives the
+    // maximum of the scaled values
+    if (STAGE == 2 && tid >= 9 && tid < 9 + NF) acc2 *= trcp(dt);
     dc.partials[(size_t)tile * NPART + tid] = double(acc2);
   }
   if (!tile_reduce(dc, by, fin)) return;
