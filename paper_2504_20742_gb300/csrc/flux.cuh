@@ -32,6 +32,39 @@ __device__ __forceinline__ double2 vl_half_slope2(double2 dm, double2 dp) {
   return p_make(vl_half_slope(dm.x, dp.x), vl_half_slope(dm.y, dp.y));
 }
 
+// States of a cell's two faces in one direction, lo = a0 - hs and hi = a0 + hs, from the
+// cell value a0, its neighbours am (minus side) and a1 (plus side) and the van Leer half
+// slope hs above.  FP64: the same values bit for bit, with the decisions taken on the
+// integer pipe (the FP64 pipe is the bottleneck of the FP64 kernels).  Three bitwise-equal
+// values have zero differences and slope; differences of opposite signs have a product
+// <= 0; same-signed differences whose magnitudes lie in [2^-511, 2^511) have a product that
+// is positive and normal.  The rest (zeros, tiny or huge values, NaN) take the product test
+// itself.  With a zero slope, hi = a0 + 0, which turns -0 into +0.
+__device__ __forceinline__ void vl_faces(double am, double a0, double a1, double& lo, double& hi) {
+  const long long bm = __double_as_longlong(am), b0 = __double_as_longlong(a0), b1 = __double_as_longlong(a1);
+  lo = a0;
+  hi = b0 == (long long)0x8000000000000000ULL ? 0.0 : a0;
+  if (bm == b0 && b1 == b0) return;
+  const double dm = a0 - am, dp = a1 - a0;
+  const int hm = __double2hiint(dm), hp = __double2hiint(dp);
+  if ((hm ^ hp) < 0) return;
+  const unsigned em = ((unsigned)hm >> 20) & 0x7ffu, ep = ((unsigned)hp >> 20) & 0x7ffu;
+  if ((em - 0x200u < 0x3feu && ep - 0x200u < 0x3feu) || dm * dp > 0.0) {
+    const double hs = dm * tdiv(dp, dm + dp);
+    lo = a0 - hs;
+    hi = a0 + hs;
+  }
+}
+__device__ __forceinline__ void vl_faces2(double2 am, double2 a0, double2 a1, double2& lo, double2& hi) {
+  vl_faces(am.x, a0.x, a1.x, lo.x, hi.x);
+  vl_faces(am.y, a0.y, a1.y, lo.y, hi.y);
+}
+__device__ __forceinline__ void vl_faces2(float2 am, float2 a0, float2 a1, float2& lo, float2& hi) {
+  const float2 hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
+  hi = p_add(a0, hs);
+  lo = p_sub(a0, hs);
+}
+
 // Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
 // formation energy and frozen sound speed squared.  One reciprocal, E = 1/(rho R_g c_v),
 // gives T = p c_v E, R_g/c_v = rho R_g^2 E, and H = (c_v + R_g) T + e_f + |u|^2/2.
@@ -67,11 +100,12 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   const T unL = DIR == 0 ? qL[1] : qL[2], utL = DIR == 0 ? qL[2] : qL[1];
   const T unR = DIR == 0 ? qR[1] : qR[2], utR = DIR == 0 ? qR[2] : qR[1];
   const T mL = qL[0] * unL, mR = qR[0] * unR;
-  // Roe averages
-  const T sL = m_sqrt(qL[0]), sR = m_sqrt(qR[0]);
-  const T isum = trcp(sL + sR);
-  const T wL = sL * isum, wR = sR * isum;
-  const T rt = sL * sR;
+  // Roe averages.  The weights sqrt(rho_L) / (sqrt(rho_L) + sqrt(rho_R)) and its mirror,
+  // multiplied through by sqrt(rho_L), need one root: rt = sqrt(rho_L rho_R), w_L =
+  // rho_L / (rho_L + rt), w_R = rt / (rho_L + rt).
+  const T rt = m_sqrt(qL[0] * qR[0]);
+  const T isum = trcp(qL[0] + rt);
+  const T wL = qL[0] * isum, wR = rt * isum;
   const T un = wL * unL + wR * unR;
   const T ut = wL * utL + wR * utR;
   const T H = wL * HL + wR * HR;

@@ -644,9 +644,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
     for (int k2 = 0; k2 < NP; ++k2) {
       const V am = qs2[k2][hj + 2][c + 1], a0 = qs2[k2][hj + 2][c + 2], a1 = qs2[k2][hj + 2][c + 3];
-      const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
-      if (c < TX) fL2[k2][hj * (TX + 1) + c + 1] = p_add(a0, hs);
-      if (c >= 0) fR2[k2][hj * (TX + 1) + c] = p_sub(a0, hs);
+      V flo, fhi;
+      vl_faces2(am, a0, a1, flo, fhi);
+      if (c < TX) fL2[k2][hj * (TX + 1) + c + 1] = fhi;
+      if (c >= 0) fR2[k2][hj * (TX + 1) + c] = flo;
     }
   }
   __syncthreads();
@@ -686,10 +687,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
     for (int k2 = 0; k2 < NP; ++k2) {
       const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
-      const V hs = vl_half_slope2(p_sub(a0, am), p_sub(a1, a0));
-      if (TL::ROWM1_EARLY && c < 0) fLm1[k2][hi] = p_add(a0, hs);
-      else if (c < TY) fL2[k2][(c + 1) * TX + hi] = p_add(a0, hs);
-      if (c >= 0) fR2[k2][c * TX + hi] = p_sub(a0, hs);
+      V flo, fhi;
+      vl_faces2(am, a0, a1, flo, fhi);
+      if (TL::ROWM1_EARLY && c < 0) fLm1[k2][hi] = fhi;
+      else if (c < TY) fL2[k2][(c + 1) * TX + hi] = fhi;
+      if (c >= 0) fR2[k2][c * TX + hi] = flo;
     }
   };
   // The r slopes of rows -1..TY outnumber the threads for the 32-wide tiles; the threads
