@@ -3,6 +3,8 @@
 // published in detail, so this is Roe's flux for the frozen ideal mixture with formation
 // energies, passive quantities carried by the upwind mass flux).
 #pragma once
+#include <type_traits>
+
 #include "pair.cuh"
 #include "physics.cuh"
 
@@ -65,6 +67,21 @@ __device__ __forceinline__ void vl_faces2(float2 am, float2 a0, float2 a1, float
   lo = p_sub(a0, hs);
 }
 
+// a < b.  FP64 on the integer pipe, through order-preserving keys of the bit patterns: the
+// same result for all values but NaN and the pair (-0, +0), which it orders.
+template <class T>
+__device__ __forceinline__ bool less(T a, T b) {
+  return a < b;
+}
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+template <>
+__device__ __forceinline__ bool less(double a, double b) {
+  return order_key(a) < order_key(b);
+}
+
 // Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
 // formation energy and frozen sound speed squared.  One reciprocal, E = 1/(rho R_g c_v),
 // gives T = p c_v E, R_g/c_v = rho R_g^2 E, and H = (c_v + R_g) T + e_f + |u|^2/2.
@@ -74,15 +91,35 @@ struct FaceThermo {
 };
 template <class T, bool BI = false>
 __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
-  const T Yl = BI ? T(k::YL3) * (q[8] + q[17]) : T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
-  const T Ya = T(1) - q[4] - Yl - Ys;
-  const T cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
+  T Ya, cv, ef;
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64, rounding pinned term by term.  Where the state carries no liquid and no ice (the
+    // third moments are +-0) the terms of Y_l and Y_s drop out exactly (x - 0 = x and
+    // fma(0, c, x) = x for x != 0), so that case skips them on the FP64 pipe.
+    const long long z3 = __double_as_longlong(q[8]) | __double_as_longlong(q[12]) |
+                         (BI ? __double_as_longlong(q[17]) : 0LL);
+    if ((z3 << 1) == 0) {
+      Ya = 1.0 - q[4];
+      cv = fma(q[4], k::CVV, Ya * k::CVA);
+      ef = q[4] * k::E0V;
+    } else {
+      const double Yl = BI ? k::YL3 * (q[8] + q[17]) : k::YL3 * q[8], Ys = k::YS3 * q[12];
+      Ya = ((1.0 - q[4]) - Yl) - Ys;
+      cv = fma(Ys, k::CS, fma(Yl, k::CL, fma(q[4], k::CVV, Ya * k::CVA)));
+      ef = fma(Ys, k::E0S, q[4] * k::E0V);
+    }
+  } else {
+    const T Yl = BI ? T(k::YL3) * (q[8] + q[17]) : T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
+    Ya = T(1) - q[4] - Yl - Ys;
+    cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
+    ef = q[4] * T(k::E0V) + Ys * T(k::E0S);
+  }
   const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
   const T rR = q[0] * Rg;
   const T E = trcp(rR * cv);
   const T Tg = q[3] * cv * E;
   FaceThermo<T> t;
-  t.ef = q[4] * T(k::E0V) + Ys * T(k::E0S);
+  t.ef = ef;
   t.g = T(1) + Rg * rR * E;
   t.H = (cv + Rg) * Tg + t.ef + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
   t.c2 = t.g * Rg * Tg;
@@ -113,8 +150,8 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   const T gam = T(0.5) * (gL + gR);
   const T q2 = un * un + ut * ut;
   T c2 = (gam - T(1)) * (H - T(0.5) * q2 - ef);
-  const T c2min = T(0.01) * (c2L < c2R ? c2L : c2R);
-  c2 = c2 < c2min ? c2min : c2;
+  const T c2min = T(0.01) * (less(c2L, c2R) ? c2L : c2R);
+  c2 = less(c2, c2min) ? c2min : c2;
   const T rc = m_rsqrt(c2);
   const T c = c2 * rc;
   const T ic2 = rc * rc;
@@ -127,8 +164,8 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   const T delta = T(0.1) * (m_fabs(un) + c);
   T l1 = m_fabs(un - c), l5 = m_fabs(un + c);
   const T l2 = m_fabs(un);
-  if (l1 < delta) l1 = fdiv(l1 * l1 + delta * delta, T(2) * delta);
-  if (l5 < delta) l5 = fdiv(l5 * l5 + delta * delta, T(2) * delta);
+  if (less(l1, delta)) l1 = fdiv(l1 * l1 + delta * delta, T(2) * delta);
+  if (less(l5, delta)) l5 = fdiv(l5 * l5 + delta * delta, T(2) * delta);
   const T w1 = l1 * a1, w2 = l2 * a2, w3 = l2 * a3, w5 = l5 * a5;
   const T D0 = w1 + w2 + w5;
   const T D1 = w1 * (un - c) + w2 * un + w5 * (un + c);
@@ -142,14 +179,41 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   F[1] = DIR == 0 ? fn : ft;
   F[2] = DIR == 0 ? ft : fn;
   F[3] = fe;
-  const T* qu = fm >= T(0) ? qL : qR;
-  // passive quantities (fields 4.. in pairs)
-  const auto fm2 = p_make(fm, fm);
+  // passive quantities: the mass flux times the upwind value
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64: upwind side from the bits of fm (fm >= 0, -0 included), and the moment fields,
+    // zero wherever there is no liquid or ice, without multiplications when all are +0 on
+    // that side (fm * +0 is a zero with the sign of fm)
+    const long long bf = __double_as_longlong(fm);
+    const bool up = bf >= 0 || bf == (long long)0x8000000000000000ULL;
+    const auto qu = [&](int f) { return up ? qL[f] : qR[f]; };
+    F[4] = fm * qu(4);
+    F[13] = fm * qu(13);
+    long long z = 0;
 #pragma unroll
-  for (int k = 2; k < NFX / 2; ++k) {
-    const auto v = p_mul(fm2, p_make(qu[2 * k], qu[2 * k + 1]));
-    F[2 * k] = v.x;
-    F[2 * k + 1] = v.y;
+    for (int f = 5; f < NFX; ++f)
+      if (f != 13) z |= __double_as_longlong(qu(f));
+    if (z == 0) {
+      const double s0 = __longlong_as_double(bf & (long long)0x8000000000000000ULL);
+#pragma unroll
+      for (int f = 5; f < NFX; ++f)
+        if (f != 13) F[f] = s0;
+    } else {
+#pragma unroll
+      for (int f = 5; f < NFX; ++f)
+        if (f != 13) F[f] = fm * qu(f);
+    }
+  } else {
+    // fields 4.. in pairs; the upwind values selected one by one (a selected pointer would
+    // put both face states in local memory)
+    const bool up = fm >= T(0);
+    const auto fm2 = p_make(fm, fm);
+#pragma unroll
+    for (int k = 2; k < NFX / 2; ++k) {
+      const auto v = p_mul(fm2, p_make(up ? qL[2 * k] : qR[2 * k], up ? qL[2 * k + 1] : qR[2 * k + 1]));
+      F[2 * k] = v.x;
+      F[2 * k + 1] = v.y;
+    }
   }
 }
 
