@@ -5,6 +5,7 @@
 // mixed-precision path keeps (ln S, the nucleation exponent and exp(-dG*/kT)).  Moments are
 // handled in scaled radius units (1 um) throughout, so that FP32 stays in range.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -166,17 +167,38 @@ __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double rn_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float rn_fma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// Moment fields of the state vector: liquid 5..8, ice 9..12 and, with the bimodal liquid,
+// the second liquid set 14..17.
+__host__ __device__ constexpr bool is_moment(int f) { return (f >= 5 && f <= 12) || f >= 14; }
+// true when every moment field of the NFX-field vector got(f) is +0 or -0 (integer pipe)
+template <int NFX, class Get>
+__device__ __forceinline__ bool moments_zero(const Get& got) {
+  long long z = 0;
+#pragma unroll
+  for (int f = 0; f < NFX; ++f)
+    if (is_moment(f)) z |= __double_as_longlong(double(got(f)));
+  return (z << 1) == 0;
+}
+
 // BI: the state has the 18 fields of the bimodal liquid; Y_l is the sum of both sets.
 // Every operation has its rounding pinned: the primitive variables a kernel stores for the
-// next stage are then bit for bit those the next stage would compute itself.
-template <class T, bool BI = false>
-__device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
+// next stage are then bit for bit those the next stage would compute itself.  ZERO: the
+// moment fields are +-0 (no liquid, no ice), and the terms they enter drop out exactly
+// (x - 0 = x, fma(0, c, x) = x for x != 0, and (+-0) / rho keeps the zero's sign), so the
+// same bits come with fewer operations.
+template <class T, bool BI, bool ZERO>
+__device__ __forceinline__ void cons_to_prim_impl(const T* U, Prim<T>& w) {
   const T rho = U[0];
   // rho c_v straight from the conserved partial densities, then one reciprocal serves
   // 1/rho = (rho c_v) X and 1/c_v = rho^2 X, X = 1/(rho rho c_v)
-  const T rYl = rn_mul(T(k::YL3), BI ? rn_add(U[8], U[17]) : U[8]), rYs = rn_mul(T(k::YS3), U[12]);
-  const T rYa = rn_sub(rn_sub(rn_sub(rho, U[4]), rYl), rYs);
-  const T rcv = rn_fma(rYs, T(k::CS), rn_fma(rYl, T(k::CL), rn_fma(U[4], T(k::CVV), rn_mul(rYa, T(k::CVA)))));
+  T rcv;
+  if constexpr (ZERO) {
+    rcv = rn_fma(U[4], T(k::CVV), rn_mul(rn_sub(rho, U[4]), T(k::CVA)));
+  } else {
+    const T rYl = rn_mul(T(k::YL3), BI ? rn_add(U[8], U[17]) : U[8]), rYs = rn_mul(T(k::YS3), U[12]);
+    const T rYa = rn_sub(rn_sub(rn_sub(rho, U[4]), rYl), rYs);
+    rcv = rn_fma(rYs, T(k::CS), rn_fma(rYl, T(k::CL), rn_fma(U[4], T(k::CVV), rn_mul(rYa, T(k::CVA)))));
+  }
   const T X = trcp(rn_mul(rho, rcv));
   const T ir = rn_mul(rcv, X);
   w.rho = rho;
@@ -185,27 +207,40 @@ __device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
   w.Yv = rn_mul(U[4], ir);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    w.ml[q] = rn_mul(U[5 + q], ir);
-    w.ms[q] = rn_mul(U[9 + q], ir);
+    w.ml[q] = ZERO ? U[5 + q] : rn_mul(U[5 + q], ir);
+    w.ms[q] = ZERO ? U[9 + q] : rn_mul(U[9 + q], ir);
   }
   w.ns = rn_mul(U[13], ir);
   if constexpr (BI) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) w.mh[q] = rn_mul(U[14 + q], ir);
+    for (int q = 0; q < 4; ++q) w.mh[q] = ZERO ? U[14 + q] : rn_mul(U[14 + q], ir);
     w.Yl = rn_mul(T(k::YL3), rn_add(w.ml[3], w.mh[3]));
   } else {
-    w.Yl = rn_mul(T(k::YL3), w.ml[3]);
+    w.Yl = ZERO ? w.ml[3] : rn_mul(T(k::YL3), w.ml[3]);
   }
-  w.Ys = rn_mul(T(k::YS3), w.ms[3]);
-  const T Ya = rn_sub(rn_sub(rn_sub(T(1), w.Yv), w.Yl), w.Ys);
+  w.Ys = ZERO ? w.ms[3] : rn_mul(T(k::YS3), w.ms[3]);
+  const T Ya = ZERO ? rn_sub(T(1), w.Yv) : rn_sub(rn_sub(rn_sub(T(1), w.Yv), w.Yl), w.Ys);
   const T ke = rn_mul(T(0.5), rn_fma(w.u, w.u, rn_mul(w.v, w.v)));
   const T e = rn_fma(U[3], ir, -ke);
   w.cv = rn_mul(rcv, ir);
   const T icv = rn_mul(rn_mul(rho, rho), X);
-  w.Tg = rn_mul(rn_fma(-w.Ys, T(k::E0S), rn_fma(-w.Yv, T(k::E0V), e)), icv);
+  w.Tg = ZERO ? rn_mul(rn_fma(-w.Yv, T(k::E0V), e), icv)
+              : rn_mul(rn_fma(-w.Ys, T(k::E0S), rn_fma(-w.Yv, T(k::E0V), e)), icv);
   w.Rg = rn_fma(w.Yv, T(k::RV), rn_mul(Ya, T(k::RA)));
   w.p = rn_mul(rn_mul(rho, w.Rg), w.Tg);
   w.c2 = rn_mul(rn_mul(rn_fma(w.Rg, icv, T(1)), w.p), ir);
+}
+// FP64 takes the shorter form where the moments are zero (the FP64 pipe is the bottleneck
+// of the FP64 kernels); FP32 always the full one.
+template <class T, bool BI = false>
+__device__ __forceinline__ void cons_to_prim(const T* U, Prim<T>& w) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (moments_zero<nf_of<BI>()>([&](int f) { return U[f]; })) {
+      cons_to_prim_impl<T, BI, true>(U, w);
+      return;
+    }
+  }
+  cons_to_prim_impl<T, BI, false>(U, w);
 }
 
 // Conserved state from (p, T, u, v, Y_v, scaled moments, soot per kg).

@@ -570,6 +570,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     const V v = fb2[f >> 1][face];
     return (f & 1) ? v.y : v.x;
   };
+  constexpr bool IS64 = std::is_same<T, double>::value;
   // warp partials in the state precision: the FP32 kernels convert to FP64 once per slot and
   // CTA (conversions run on the FP64 pipe, a small fraction of the FP32 rate on GB300)
   __shared__ T red[NT / 32][NPART];
@@ -724,12 +725,30 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
       vol = area_w * g.dx;
     }
-    const V cw2 = p_make(cw, cw), nce2 = p_make(-ce, -ce);
+    if constexpr (IS64) {
+      // FP64: where the x fluxes of every moment field are zero, so is their divergence.
+      // (A zero's sign cannot reach the update: a zero term is added to a non-zero one, or
+      // to a state that is +0 as every state this code writes.)
 #pragma unroll
-    for (int k2 = 0; k2 < NP; ++k2) {
-      const V a = p_fma(cw2, fb2[k2][w], p_mul(nce2, fb2[k2][e]));
-      acc[2 * k2] = a.x;
-      acc[2 * k2 + 1] = a.y;
+      for (int f = 0; f < NFX; ++f)
+        if (!is_moment(f)) acc[f] = fma(cw, fb(f, w), -ce * fb(f, e));
+      if (moments_zero<NFX>([&](int f) { return fb(f, w); }) && moments_zero<NFX>([&](int f) { return fb(f, e); })) {
+#pragma unroll
+        for (int f = 0; f < NFX; ++f)
+          if (is_moment(f)) acc[f] = T(0);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NFX; ++f)
+          if (is_moment(f)) acc[f] = fma(cw, fb(f, w), -ce * fb(f, e));
+      }
+    } else {
+      const V cw2 = p_make(cw, cw), nce2 = p_make(-ce, -ce);
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) {
+        const V a = p_fma(cw2, fb2[k2][w], p_mul(nce2, fb2[k2][e]));
+        acc[2 * k2] = a.x;
+        acc[2 * k2 + 1] = a.y;
+      }
     }
     if (i == 0) {
       bm += area_w * fb(0, w);
@@ -813,16 +832,31 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       const T ijh = trcp(T(j) + T(0.5));
       const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
       const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
-      const V cs2 = p_make(cs, cs), ncn2 = p_make(-cn, -cn);
+      // the duct wall's faces carry the pressure in rho*v (field 2) and nothing else
+      const bool wall_s = wall && j == dc.jw, wall_n = wall && j == dc.jw - 1;
+      if constexpr (IS64) {
+        const int fs = cj * TX + ci, fn = (cj + 1) * TX + ci;
+        const auto Fs = [&](int f) -> T { return wall_s ? (f == 2 ? w.p : T(0)) : fb(f, fs); };
+        const auto Fn = [&](int f) -> T { return wall_n ? (f == 2 ? w.p : T(0)) : fb(f, fn); };
 #pragma unroll
-      for (int k2 = 0; k2 < NP; ++k2) {
-        V Fs = fb2[k2][cj * TX + ci], Fn = fb2[k2][(cj + 1) * TX + ci];
-        // the duct wall's faces carry the pressure in rho*v (field 2: pair 1) and nothing else
-        if (wall && j == dc.jw - 1) Fn = p_make(k2 == 1 ? w.p : T(0), T(0));
-        if (wall && j == dc.jw) Fs = p_make(k2 == 1 ? w.p : T(0), T(0));
-        const V a = p_add(p_make(acc[2 * k2], acc[2 * k2 + 1]), p_fma(cs2, Fs, p_mul(ncn2, Fn)));
-        acc[2 * k2] = a.x;
-        acc[2 * k2 + 1] = a.y;
+        for (int f = 0; f < NFX; ++f)
+          if (!is_moment(f)) acc[f] = acc[f] + fma(cs, Fs(f), -cn * Fn(f));
+        if (!(moments_zero<NFX>(Fs) && moments_zero<NFX>(Fn))) {   // as in the x divergence
+#pragma unroll
+          for (int f = 0; f < NFX; ++f)
+            if (is_moment(f)) acc[f] = acc[f] + fma(cs, Fs(f), -cn * Fn(f));
+        }
+      } else {
+        const V cs2 = p_make(cs, cs), ncn2 = p_make(-cn, -cn);
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          V Fs = fb2[k2][cj * TX + ci], Fn = fb2[k2][(cj + 1) * TX + ci];
+          if (wall_n) Fn = p_make(k2 == 1 ? w.p : T(0), T(0));
+          if (wall_s) Fs = p_make(k2 == 1 ? w.p : T(0), T(0));
+          const V a = p_add(p_make(acc[2 * k2], acc[2 * k2 + 1]), p_fma(cs2, Fs, p_mul(ncn2, Fn)));
+          acc[2 * k2] = a.x;
+          acc[2 * k2 + 1] = a.y;
+        }
       }
       acc[2] += w.p * ijh * g.idr;
       if (dc.viscous) {   // radial component of the vector Laplacian: -mu_e v / r^2
@@ -846,15 +880,17 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     if (!SURR) {
       const bool act = phase_source<T, BI>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr);
       nactive = act ? 1 : 0;
-      if (act) {   // inactive cells keep -inf without a conversion
+      // inactive cells keep -inf without a conversion, and their source is +0: adding it
+      // could only turn a -0 into +0, which the update cannot tell apart
+      if (act) {
         lnJh = T(lnJ2[0]);
         lnJt = T(lnJ2[1]);
-      }
 #pragma unroll
-      for (int f = 4; f < 13; ++f) acc[f] += Q[f];
-      if (BI) {
+        for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+        if (BI) {
 #pragma unroll
-        for (int f = 14; f < 18; ++f) acc[f] += Q[f];
+          for (int f = 14; f < 18; ++f) acc[f] += Q[f];
+        }
       }
     }
   }
@@ -866,12 +902,78 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     // RK combine
     T out[NFX];
     const V dt2 = p_make(dt, dt);
-    if (STAGE == 1) {
+    // FP64: moment fields that are +0 in the input states with a zero rate stay +0 (exactly
+    // what the update gives), and their residual is 0
+    bool mz = false;
+    if constexpr (IS64) {
+      const auto bits0 = [&](const T* v) {
+        long long z = 0;
 #pragma unroll
-      for (int k2 = 0; k2 < NP; ++k2) {
-        const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
-        out[2 * k2] = o.x;
-        out[2 * k2 + 1] = o.y;
+        for (int f = 0; f < NFX; ++f)
+          if (is_moment(f)) z |= __double_as_longlong(v[f]);
+        return z == 0;
+      };
+      mz = bits0(u14) && moments_zero<NFX>([&](int f) { return acc[f]; });
+      if (STAGE == 2) {
+        if (mz) {
+          T unm[NFX];
+#pragma unroll
+          for (int f = 0; f < NFX; ++f)
+            if (is_moment(f)) unm[f] = Un[f * N + n];
+          mz = bits0(unm);
+        }
+      }
+    }
+    if (STAGE == 1) {
+      if constexpr (IS64) {
+#pragma unroll
+        for (int f = 0; f < NFX; ++f)
+          if (!is_moment(f)) out[f] = fma(dt, acc[f], u14[f]);
+        if (mz) {
+#pragma unroll
+          for (int f = 0; f < NFX; ++f)
+            if (is_moment(f)) out[f] = T(0);
+        } else {
+#pragma unroll
+          for (int f = 0; f < NFX; ++f)
+            if (is_moment(f)) out[f] = fma(dt, acc[f], u14[f]);
+        }
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+          out[2 * k2] = o.x;
+          out[2 * k2 + 1] = o.y;
+        }
+      }
+    } else if (IS64) {
+#pragma unroll
+      for (int f = 0; f < NFX; ++f) {
+        if (is_moment(f)) continue;
+        const T un = Un[f * N + n];
+        out[f] = fma(T(0.5), un, T(0.5) * fma(dt, acc[f], u14[f]));
+        if (f < NF) rmax[f] = m_fabs(out[f] - un);   // divided by dt once per CTA
+      }
+      if (mz) {
+#pragma unroll
+        for (int f = 0; f < NFX; ++f)
+          if (is_moment(f)) {
+            out[f] = T(0);
+            if (f < NF) rmax[f] = T(0);   // the second set's slots keep their maximum
+          }
+      } else {
+#pragma unroll
+        for (int f = 0; f < NFX; ++f) {
+          if (!is_moment(f)) continue;
+          const T un = Un[f * N + n];
+          out[f] = fma(T(0.5), un, T(0.5) * fma(dt, acc[f], u14[f]));
+          const T rf = m_fabs(out[f] - un);
+          if (f < NF) {
+            rmax[f] = rf;
+          } else {   // the second liquid set shares the residual slots of the first
+            rmax[f - 9] = rf > rmax[f - 9] ? rf : rmax[f - 9];
+          }
+        }
       }
     } else {
       const V half2 = p_make(T(0.5), T(0.5));
