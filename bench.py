@@ -99,18 +99,18 @@ def _workload(name):
 # Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/), in
 # the tile shape the autotuner picks for the workload (FP64: 16 x 14 with two CTAs per SM;
 # FP32: 32 x 8 with three CTAs per SM): FP64 arithmetic per cell-stage (mean of the two
-# stages: 908.3 and 1041.1 flops, the FP64 kernels reading the stored primitive variables;
-# the 16 x 16 tile, within 2 % in time, does 969.0 with its smaller halo) and DRAM bytes per
+# stages, 549.3 and 634.7 flops: the FP64 kernels executed on the plume, where they skip
+# the exact zeros of the particle moments in air without liquid or ice) and DRAM bytes per
 # cell per launch (mean of the two stages).  The traffic is reported only for that shape.
 TRAFFIC_SHAPE = {0: 8, 1: 5}
-FP64_FLOPS_PER_CELL_STAGE = 974.7
-FP64_TRAFFIC_PER_CELL_LAUNCH = 394.4
-FP32_TRAFFIC_PER_CELL_LAUNCH = 134.8
-# the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s; counted before
-# the kernels read stored primitive variables, so an upper estimate of today's count)
-FP64_VISC_FLOPS_PER_CELL_STAGE = 1754.7
-# the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 1095.4 and 1299.2 flops)
-FP64_BI_FLOPS_PER_CELL_STAGE = 1197.3
+FP64_FLOPS_PER_CELL_STAGE = 592.0
+FP64_TRAFFIC_PER_CELL_LAUNCH = 392.9
+FP32_TRAFFIC_PER_CELL_LAUNCH = 134.4
+# the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s: 1154.7 and
+# 1407.0 flops)
+FP64_VISC_FLOPS_PER_CELL_STAGE = 1280.9
+# the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 595.3 and 717.6 flops)
+FP64_BI_FLOPS_PER_CELL_STAGE = 656.5
 
 
 def measure_dgemm_tflops(dev) -> float:
