@@ -186,6 +186,18 @@ ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, 
 ct_status ct_source_batch(const ct_case *c, int precision, const double *U, int n, double dt,
                           double *Q, double *aux, void *stream);
 
+/* MUSCL reconstruction with the van Leer limiter (Sec. 3.2), the step the FP64 stage kernels
+ * take for every field, cell and direction, here for n independent cells.  From the values
+ * am (minus-side neighbour), a0 (the cell) and a1 (plus-side neighbour) it forms the states
+ * of the cell's two faces, lo = a0 - hs and hi = a0 + hs, where hs = dm dp / (dm + dp) with
+ * dm = a0 - am and dp = a1 - a0 where dm dp > 0, and hs = 0 (hi = a0 + 0) otherwise.  The
+ * arithmetic and the decisions are the stage kernels' own: the reciprocal by Newton
+ * iteration (valid while dm + dp is finite and normal) and the tests on the integer pipe.
+ * All arrays are device arrays of n doubles; the call enqueues on `stream`.  n = 0 does
+ * nothing; n < 0 or a null array gives CT_ERR_ARG. */
+ct_status ct_reconstruct_faces(const double *am, const double *a0, const double *a1, int n, double *lo,
+                               double *hi, void *stream);
+
 /* ---- source surrogate (Sec. 2.2 rates; the network is this library's, not the paper's) ----
  * A 16 -> 4x128 (SiLU) -> 10 multilayer perceptron stands in for the stiff pointwise rates
  * of Sec. 2.2 (nucleation Eqs. 3-6/10, growth Eq. 16, the stage relaxation rates) in the

@@ -66,6 +66,7 @@ _SIGS = {
     "ct_diagnostics": (C.c_int, [_vp, _dp, C.c_int, _vp]),
     "ct_derived": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp]),
     "ct_source_batch": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "ct_reconstruct_faces": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp]),
     "ct_step_static": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_mlp_dataset": (C.c_int, [_cp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "ct_mlp_param_count": (C.c_int, []),
@@ -202,6 +203,10 @@ def ct_derived(case, precision, U, which, dt, out, stream=None):
 def ct_source_batch(case, precision, U, n, dt, Q, aux, stream=None):
     _check(_L().ct_source_batch(C.byref(_case(case)), precision, _ptr(U), n, dt, _ptr(Q), _ptr(aux),
                                 _stream(stream)))
+
+
+def ct_reconstruct_faces(am, a0, a1, n, lo, hi, stream=None):
+    _check(_L().ct_reconstruct_faces(_ptr(am), _ptr(a0), _ptr(a1), n, _ptr(lo), _ptr(hi), _stream(stream)))
 
 
 def ct_step_static(case, precision, ufac_rows_dev, U, U1, nsteps, cfl, stream=None):

@@ -797,6 +797,25 @@ ct_status ct_source_batch(const ct_case* c, int precision, const double* U, int 
   return cuda_check("k_source_batch");
 }
 
+__global__ void k_faces(const double* am, const double* a0, const double* a1, int n, double* lo, double* hi) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double l, h;
+    vl_faces(am[i], a0[i], a1[i], l, h);
+    lo[i] = l;
+    hi[i] = h;
+  }
+}
+
+ct_status ct_reconstruct_faces(const double* am, const double* a0, const double* a1, int n, double* lo, double* hi,
+                               void* stream) {
+  if (n < 0) return fail(CT_ERR_ARG, "n < 0");
+  if (n == 0) return CT_OK;
+  if (!am || !a0 || !a1 || !lo || !hi) return fail(CT_ERR_ARG, "null buffer");
+  const int grid = std::min((n + 255) / 256, 8192);
+  k_faces<<<grid, 256, 0, (cudaStream_t)stream>>>(am, a0, a1, n, lo, hi);
+  return cuda_check("k_faces");
+}
+
 // ---- allocation-free variant of ct_step ----------------------------------------------------
 // Some callers cannot allocate device memory at all: code running inside a host framework
 // whose allocator is reserved or already captured, firmware-style launchers that only own

@@ -55,6 +55,12 @@ def test_invalid_arguments_are_rejected_without_a_gpu(P):
         P.ct_setup(c, P.CT_FP64, None, 0x1001, 1 << 30, None)
     with pytest.raises(P.ContrailError):
         P.ct_derived(c, P.CT_FP64, 0x1000, 99, 1e-6, 0x2000)
+    P.ct_reconstruct_faces(None, None, None, 0, None, None)   # n = 0: nothing to do
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_reconstruct_faces(0x1000, 0x1000, 0x1000, -1, 0x2000, 0x3000)
+    assert e.value.status == 1
+    with pytest.raises(P.ContrailError):
+        P.ct_reconstruct_faces(0x1000, None, 0x1000, 4, 0x2000, 0x3000)
 
 
 def test_binding_has_no_oracle_dependency():
