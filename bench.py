@@ -295,7 +295,9 @@ def run_cuda(args):
                             if shape == TRAFFIC_SHAPE[0] and not c.get("viscous") and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
-                "note": f"{per_cell} FP64 flops per cell-stage; mean launch {launch_ms_ev:.4f} ms"
+                "note": f"{per_cell} FP64 flops per cell-stage executed (a DFMA counts 2, a DADD or DMUL 1; "
+                        "the FP64 pipe was 80 % busy on the plume in the ncu capture, profiles/); "
+                        f"mean launch {launch_ms_ev:.4f} ms"
                         + ("; figure of the dormant plume, a lower bound where the source fires"
                            if args.workload.startswith("active") else "")}
     else:
