@@ -201,6 +201,24 @@ __device__ __forceinline__ V warp_sum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Warp sums of three values a, b, c with the additions of warp_sum in a transposed order:
+// at the first two levels each lane adds only the part of the set it keeps (lanes below 16
+// keep a and b, the others c; then lanes with bit 3 clear keep the first of their two), so
+// 6 additions replace 15 and each sum is formed by the same additions as warp_sum's (bit
+// for bit).  The sum of a ends in lane 0, b in lane 8, c in lane 16.
+template <class V>
+__device__ __forceinline__ V warp_sum3(V a, V b, V c) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  V k0 = h16 ? c : a, k1 = h16 ? V(0) : b;
+  k0 += __shfl_xor_sync(0xffffffffu, h16 ? a : c, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, h16 ? b : V(0), 16);
+  V v = h8 ? k1 : k0;
+  v += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 template <class V>
 __device__ __forceinline__ V warp_max(V v) {
 #pragma unroll
@@ -584,6 +602,26 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   const double dtd = dc.hdr->dt_cur;
   if (tid == 0) s_dt = T(dtd);   // one conversion per CTA; published by phase A's barrier
   const Geo<T> g = geo_of(dc, T(0));
+  // FP64, axisymmetric: the geometry of the tile's rows (1/(j + 1/2), the r-face weights,
+  // the x-face area per radian, the cell volume per radian) and the duct-wall test of its
+  // columns, once per row and column with the expressions the cells would evaluate
+  // themselves (the same bits), published by phase A's barrier.  The FP32 kernels keep the
+  // per-cell form: their shared memory is the tighter budget.
+  __shared__ T s_row[IS64 ? TY : 1][5];
+  __shared__ bool s_wall[IS64 ? TX : 1];
+  if (IS64 && dc.geom == 1) {
+    for (int r = tid; r < TY; r += NT) {
+      const int j = j0 + r;
+      const T ijh = trcp(T(j) + T(0.5));
+      const T area = (T(j) + T(0.5)) * g.dr * g.dr;
+      s_row[r][0] = ijh;
+      s_row[r][1] = T(j) * ijh * g.idr;
+      s_row[r][2] = T(j + 1) * ijh * g.idr;
+      s_row[r][3] = area;
+      s_row[r][4] = area * g.dx;
+    }
+    for (int c = tid; c < TX; c += NT) s_wall[c] = g.wall_len > T(0) && (T(i0 + c) + T(0.5)) * g.dx < g.wall_len;
+  }
 
   // phase A: halo primitives.  A thread owns up to NA halo cells; the interior loads of all
   // of them are issued before any is converted, so their latencies overlap.
@@ -722,8 +760,13 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       vol = Ac * g.dx;
     } else {
       cw = ce = g.idx;
-      area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
-      vol = area_w * g.dx;
+      if constexpr (IS64) {
+        area_w = area_e = s_row[cj][3];
+        vol = s_row[cj][4];
+      } else {
+        area_w = area_e = (T(j) + T(0.5)) * g.dr * g.dr;
+        vol = area_w * g.dx;
+      }
     }
     if constexpr (IS64) {
       // FP64: where the x fluxes of every moment field are zero, so is their divergence.
@@ -829,9 +872,19 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       cons_to_prim<T, BI>(u14, w);
     }
     if (dc.geom == 1) {
-      const T ijh = trcp(T(j) + T(0.5));
-      const T cs = T(j) * ijh * g.idr, cn = T(j + 1) * ijh * g.idr;
-      const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
+      T ijh, cs, cn;
+      bool wall;
+      if constexpr (IS64) {
+        ijh = s_row[cj][0];
+        cs = s_row[cj][1];
+        cn = s_row[cj][2];
+        wall = s_wall[ci];
+      } else {
+        ijh = trcp(T(j) + T(0.5));
+        cs = T(j) * ijh * g.idr;
+        cn = T(j + 1) * ijh * g.idr;
+        wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
+      }
       // the duct wall's faces carry the pressure in rho*v (field 2) and nothing else
       const bool wall_s = wall && j == dc.jw, wall_n = wall && j == dc.jw - 1;
       if constexpr (IS64) {
@@ -1032,9 +1085,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     int a;
     // boundary fluxes: only tiles on the inflow, outflow or far-field boundary have any
     if (i0 == 0 || i0 + TX >= nx || (dc.geom == 1 && j0 + TY >= nr)) {
-      v = warp_sum(bm); if (lane == 0) red[warp][4] = v;
-      v = warp_sum(bw); if (lane == 0) red[warp][5] = v;
-      v = warp_sum(be); if (lane == 0) red[warp][6] = v;
+      v = warp_sum3(bm, bw, be);
+      if (lane == 0) red[warp][4] = v;
+      if (lane == 8) red[warp][5] = v;
+      if (lane == 16) red[warp][6] = v;
     } else if (lane == 0) {
       red[warp][4] = red[warp][5] = red[warp][6] = T(0);
     }
@@ -1046,9 +1100,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     }
     if (STAGE == 2) {
       v = warp_min_nonneg(dtmin); if (lane == 0) red[warp][0] = v;
-      v = warp_sum(pM); if (lane == 0) red[warp][1] = v;
-      v = warp_sum(pW); if (lane == 0) red[warp][2] = v;
-      v = warp_sum(pE); if (lane == 0) red[warp][3] = v;
+      v = warp_sum3(pM, pW, pE);
+      if (lane == 0) red[warp][1] = v;
+      if (lane == 8) red[warp][2] = v;
+      if (lane == 16) red[warp][3] = v;
       a = warp_count(nactive); if (lane == 0) red[warp][7] = T(a);
       a = warp_count(nbad); if (lane == 0) red[warp][8] = T(a);
 #pragma unroll
