@@ -96,21 +96,20 @@ def _workload(name):
     return c, uf, "hydrogen-like mixing plume 2048x512 (pre-mixed layer), FP32 + BF16 tensor-core surrogate", 2
 
 
-# Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/), in
-# the tile shape the autotuner picks for the workload (FP64: 16 x 14 with two CTAs per SM;
-# FP32: 32 x 8 with three CTAs per SM): FP64 arithmetic per cell-stage (mean of the two
-# stages, 549.3 and 634.7 flops: the FP64 kernels executed on the plume, where they skip
-# the exact zeros of the particle moments in air without liquid or ice) and DRAM bytes per
-# cell per launch (mean of the two stages).  The traffic is reported only for that shape.
-TRAFFIC_SHAPE = {0: 8, 1: 5}
-FP64_FLOPS_PER_CELL_STAGE = 592.0
-FP64_TRAFFIC_PER_CELL_LAUNCH = 392.9
-FP32_TRAFFIC_PER_CELL_LAUNCH = 134.4
-# the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s: 1154.7 and
-# 1407.0 flops)
-FP64_VISC_FLOPS_PER_CELL_STAGE = 1280.9
-# the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 595.3 and 717.6 flops)
-FP64_BI_FLOPS_PER_CELL_STAGE = 656.5
+# Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/):
+# FP64 arithmetic per cell-stage executed on the plume (mean of the two stages, 527.9 and
+# 602.2 flops on the 16 x 16 two-CTA tile; the kernels skip the exact zeros of the particle
+# moments in air without liquid or ice; the 16 x 14 tile's larger halo adds about 1 %), and
+# DRAM bytes per cell per launch (mean of the two stages) by tile shape, reported only for
+# a shape counted on the current kernel.
+FP64_FLOPS_PER_CELL_STAGE = 565.1
+FP64_TRAFFIC_PER_CELL_LAUNCH = {7: 452.0}    # 16 x 16, two CTAs per SM
+FP32_TRAFFIC_PER_CELL_LAUNCH = {5: 134.3}    # 32 x 8, three CTAs per SM
+# the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s, 16 x 14 tile:
+# 1135.9 and 1377.4 flops)
+FP64_VISC_FLOPS_PER_CELL_STAGE = 1256.7
+# the bimodal FP64 kernel (18 fields; same recipe, dormant plume: 576.3 and 688.6 flops)
+FP64_BI_FLOPS_PER_CELL_STAGE = 632.5
 
 
 def measure_dgemm_tflops(dev) -> float:
@@ -291,12 +290,13 @@ def run_cuda(args):
         ach = flops / (launch_ms_ev * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fpk, 4), "unit": "TFLOP/s",
                 "frac": round(ach / fpk, 4),
-                "traffic": (FP64_TRAFFIC_PER_CELL_LAUNCH * cells
-                            if shape == TRAFFIC_SHAPE[0] and not c.get("viscous") and not c.get("bimodal") else None),
+                "traffic": (FP64_TRAFFIC_PER_CELL_LAUNCH[shape] * cells
+                            if shape in FP64_TRAFFIC_PER_CELL_LAUNCH and not c.get("viscous") and not c.get("bimodal")
+                            else None),
                 "kernel": "ct::k_stage<double>",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{per_cell} FP64 flops per cell-stage executed (a DFMA counts 2, a DADD or DMUL 1; "
-                        "the FP64 pipe was 80 % busy on the plume in the ncu capture, profiles/); "
+                        "the FP64 pipe was 76-78 % busy on the plume in the ncu capture, profiles/); "
                         f"mean launch {launch_ms_ev:.4f} ms"
                         + ("; figure of the dormant plume, a lower bound where the source fires"
                            if args.workload.startswith("active") else "")}
@@ -305,8 +305,8 @@ def run_cuda(args):
         bw = alg_bytes / (launch_ms_ev * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(bw / peaks["hbm_gbs"], 4),
-                "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH * cells
-                            if shape == TRAFFIC_SHAPE[1] and not c.get("bimodal") else None),
+                "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH[shape] * cells
+                            if shape in FP32_TRAFFIC_PER_CELL_LAUNCH and not c.get("bimodal") else None),
                 "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*{nf}*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
