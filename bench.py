@@ -99,11 +99,11 @@ def _workload(name):
 # Per-cell figures of the fused stage kernel, from one ncu capture each (see profiles/):
 # FP64 arithmetic per cell-stage executed on the plume (mean of the two stages, 527.9 and
 # 602.2 flops on the 16 x 16 two-CTA tile; the kernels skip the exact zeros of the particle
-# moments in air without liquid or ice; the 16 x 14 tile's larger halo adds about 1 %), and
-# DRAM bytes per cell per launch (mean of the two stages) by tile shape, reported only for
-# a shape counted on the current kernel.
+# moments in air without liquid or ice; the 16 x 14 tile's larger halo adds 0.5 %: 530.5
+# and 605.2), and DRAM bytes per cell per launch (mean of the two stages) by tile shape,
+# reported only for a shape counted on the current kernel.
 FP64_FLOPS_PER_CELL_STAGE = 565.1
-FP64_TRAFFIC_PER_CELL_LAUNCH = {7: 452.0}    # 16 x 16, two CTAs per SM
+FP64_TRAFFIC_PER_CELL_LAUNCH = {7: 452.0, 8: 392.8}    # 16 x 16 and 16 x 14, two CTAs per SM
 FP32_TRAFFIC_PER_CELL_LAUNCH = {5: 134.3}    # 32 x 8, three CTAs per SM
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s, 16 x 14 tile:
 # 1135.9 and 1377.4 flops)
@@ -225,7 +225,11 @@ def run_cuda(args):
         if prec == P.CT_FP32_MLP:
             from paper_2504_20742_gb300 import surrogate as S
             s.attach_surrogate(S.Surrogate.load(S.default_path()).blob(dev))
-        shape, tune_ms = s.autotune(reps=3)     # the state is left as it was
+        if args.tile_shape >= 0:                 # a given tile shape instead of the autotuner's
+            shape, tune_ms = args.tile_shape, []
+            P.ct_set_tile_shape(c, prec, shape)
+        else:
+            shape, tune_ms = s.autotune(reps=3)     # the state is left as it was
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         for _ in range(args.warmup):
             s.step(1, cfl)
@@ -318,8 +322,10 @@ def run_cuda(args):
         "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32+bf16"),
         "data": "synthetic", "impl": "cuda",
         "config": {"workload": desc, "cells": cells, "nx": c["nx"], "nr": c["nr"], "cfl": cfl,
-                   "tile": "%dx%d, %d CTAs/SM (autotuned; ms per stage-1 launch per shape: %s)"
-                           % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape, prec), [round(m, 4) for m in tune_ms]),
+                   "tile": ("%dx%d, %d CTAs/SM (autotuned; ms per stage-1 launch per shape: %s)"
+                            % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape, prec), [round(m, 4) for m in tune_ms])
+                            if tune_ms else "%dx%d, %d CTAs/SM (given)"
+                            % (*P.ct_tile_shape(shape), P.ct_tile_shape_ctas(shape, prec))),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
@@ -506,6 +512,9 @@ def main():
                     choices=("fp64", "fp64_viscous", "fp64_bimodal", "fp32", "fp32_mlp", "active_fp32",
                              "active_fp32_bimodal", "active_mlp", "active_fp64", "active_fp64_tables",
                              "active_fp64_bimodal", "batch64"))
+    ap.add_argument("--tile-shape", type=int, default=-1,
+                    help="stage-kernel tile shape (ct_tile_shape index) instead of the autotuner's pick "
+                         "(single-case workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
