@@ -28,6 +28,16 @@ def test_exports_every_declared_symbol(P):
     assert P.ct_version().startswith("contrail-gb300")
 
 
+def test_binding_covers_every_declared_symbol(P):
+    """The Python binding has a function of the same name, with a ctypes signature, for
+    every entry point the header declares."""
+    from paper_2504_20742_gb300 import _lib
+    hdr = open(os.path.join(ROOT, "include", "contrail.h")).read()
+    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(ct_[a-z_0-9]+)\s*\(", hdr, re.M))
+    assert sorted(names - set(_lib._SIGS)) == []
+    assert sorted(n for n in names if not callable(getattr(_lib, n, None))) == []
+
+
 def test_workspace_size_and_case_validation(P):
     from synth import cases
     c, _ = cases.plume_case()
