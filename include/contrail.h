@@ -267,9 +267,12 @@ ct_status ct_mlp_infer(const void *blob, const float *X, int n, float *Y, int *e
 ct_status ct_step_surrogate(const ct_case *c, void *U, void *U1, void *work, const void *blob, int nsteps, double cfl,
                             void *stream);
 
-/* Maximum scratch of ct_step_static, in bytes (4 MiB: about 16,000 tiles of 32x8 cells,
- * e.g. a 4096 x 1024 plume). */
-#define CT_STATIC_SCRATCH_BYTES (4u << 20)
+/* Maximum scratch of ct_step_static, in bytes (6 MiB).  A case needs ct_workspace_bytes(c,
+ * CT_FP32) bytes: a 1 KB header, the inflow profile (nr x fields doubles) and 27 doubles of
+ * reduction record per tile, counted for the tile shape with the most tiles on the grid (the
+ * 16 x 12 shape: 22,016 tiles on a 4096 x 1024 plume, 4.9 MB in all).  So every grid up to
+ * 4096 x 1024 cells fits; an 8192 x 2048 plume (88,064 tiles) does not. */
+#define CT_STATIC_SCRATCH_BYTES (6u << 20)
 
 /* Allocation-free variant of ct_step.  The paper has no counterpart: this serves callers
  * that cannot allocate device memory (a host framework whose allocator they may not call,
@@ -285,7 +288,12 @@ ct_status ct_step_surrogate(const ct_case *c, void *U, void *U1, void *work, con
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current: make it before any stream capture.  All calls share the one
  * array and it keeps the last call's contents, so calls that overlap on the GPU (other
- * streams, other threads) race.  Errors: CT_ERR_SIZE when the case needs more scratch than
+ * streams, other threads) race.  The device address found on the first call stays cached
+ * for the process: after cudaDeviceReset() on a device, later calls on that device are
+ * invalid (the module, and the array with it, may move).  The step's diagnostics record
+ * (totals, time step, non-finite count) stays in the static array and no call returns it,
+ * so this path does not report CT_ERR_NONFINITE: a caller that needs that check reads the
+ * state it owns.  Errors: CT_ERR_SIZE when the case needs more scratch than
  * CT_STATIC_SCRATCH_BYTES; CT_ERR_ARG for invalid arguments (CT_FP32_MLP is rejected). */
 ct_status ct_step_static(const ct_case *c, int precision, const double *ufac_rows_dev, void *U, void *U1,
                          int nsteps, double cfl, void *stream);

@@ -826,7 +826,8 @@ constexpr size_t STATIC_SCRATCH_BYTES = (size_t)CT_STATIC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-static void* g_static_ptr[MAX_DEVICES];   // device address of g_static_scratch, per device
+static std::mutex g_static_mu;
+static void* g_static_ptr[MAX_DEVICES];   // device address of g_static_scratch, per device (under g_static_mu)
 
 __global__ void k_scratch_reset(int nblocks, unsigned int* row_count, int nrows) {
   // everything that must start at zero for a fresh run: the header and the row tickets
@@ -843,6 +844,7 @@ static ct_status static_scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cuda_check("cudaGetDevice");
   if (dev < 0 || dev >= MAX_DEVICES) return fail(CT_ERR_ARG, "device index beyond the static scratch table");
+  std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[dev]) {
     // host code cannot use g_static_scratch's name as a device address: ask the runtime,
     // with this device current, once per device
@@ -870,10 +872,9 @@ extern "C" ct_status ct_step_static(const ct_case* c, int precision, const doubl
   const size_t need = ws_bytes(c);
   if (need > STATIC_SCRATCH_BYTES) {
     snprintf(g_err, sizeof(g_err),
-             "case needs %zu bytes of scratch but the static scratch holds %zu (about %d tiles of %dx%d cells); "
-             "use ct_step with a caller workspace",
-             need, STATIC_SCRATCH_BYTES, (int)((STATIC_SCRATCH_BYTES - HDR_BYTES) / (NPART * sizeof(double))),
-             stage_set(0)->tx, stage_set(0)->ty);
+             "case needs %zu bytes of scratch (reduction records for %d tiles, the largest tile count over the "
+             "built tile shapes) but the static scratch holds %zu; use ct_step with a caller workspace",
+             need, max_blocks(c), STATIC_SCRATCH_BYTES);
     return CT_ERR_SIZE;
   }
   void* work = nullptr;

@@ -139,3 +139,23 @@ def test_batch_sizes_and_validation_without_a_gpu(P):
     assert e.value.status == 6
     with pytest.raises(P.ContrailError):
         P.ct_batch_create(bc, P.CT_FP32, None, 0x101, ws, None)
+
+
+def test_static_scratch_covers_the_grids_its_header_names(P):
+    """The allocation-free step's static scratch (CT_STATIC_SCRATCH_BYTES, read from the
+    header) holds the workspace of every plume grid up to 4096 x 1024 cells (the FP32 size:
+    the static path keeps no stored primitives in either precision), and not that of an
+    8192 x 2048 plume (rejected with CT_ERR_SIZE)."""
+    from synth import cases
+    hdr = open(os.path.join(ROOT, "include", "contrail.h")).read()
+    m = re.search(r"#define\s+CT_STATIC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", hdr)
+    limit = int(m.group(1)) << int(m.group(2))
+    for nx, nr in ((4096, 1024), (4096, 1000), (1024, 256), (2048, 512), (37, 5)):
+        c, _ = cases.plume_case(nx=nx, nr=nr)
+        need = P.ct_workspace_bytes(c, P.CT_FP32)
+        assert 0 < need <= limit, (nx, nr, need, limit)
+    big, _ = cases.plume_case(nx=8192, nr=2048)
+    assert P.ct_workspace_bytes(big, P.CT_FP32) > limit
+    with pytest.raises(P.ContrailError) as e:
+        P.ct_step_static(big, P.CT_FP64, None, 0x1000, 0x2000, 1, 0.5)
+    assert e.value.status == 6 and "static scratch" in str(e.value)

@@ -34,13 +34,17 @@ def _field_rel_err(a, b):
     return max(out)
 
 
-@pytest.mark.parametrize("precision,name", [(0, "freezing"), (1, "freezing"), (0, "plume")])
+@pytest.mark.parametrize("precision,name", [(0, "freezing"), (1, "freezing"), (0, "plume"), (1, "plume4096")])
 def test_static_scratch_step_matches_workspace_step(P, precision, name):
+    n = 20
     if name == "freezing":
         c, uf = cases.freezing_case(nx=96, nr=40)
-    else:
+    elif name == "plume":
         c, uf = cases.plume_case(nx=256, nr=64)
-    cfl, n = 0.5, 20
+    else:   # the largest grid the static scratch is sized for
+        c, uf = cases.plume_case(nx=4096, nr=1024)
+        n = 3
+    cfl = 0.5
     # reference: the workspace path, two runs of n steps from the same start
     ref = P.Solver(c, uf, precision=precision)
     ref.init_state(cfl)
@@ -68,7 +72,7 @@ def test_static_scratch_step_matches_workspace_step(P, precision, name):
 
 
 def test_static_scratch_rejects_oversized_cases(P):
-    c, uf = cases.plume_case(nx=8192, nr=2048)     # 65,536 tiles: beyond the 4 MiB scratch
+    c, uf = cases.plume_case(nx=8192, nr=2048)     # 88,064 tiles of 16x12: beyond the 6 MiB scratch
     U = torch.zeros(1, device="cuda")
     U1 = torch.zeros(1, device="cuda")
     with pytest.raises(P.ContrailError) as e:
