@@ -15,6 +15,7 @@ from .oracle import (  # noqa: F401
     koop_log10J,
     hfg,
     roe_flux,
+    roe_c2,
     dv_mol,
     table_eval,
     diffusive_flux,

@@ -804,6 +804,31 @@ static void face_state(const double *q, int bi, face_t *s) {
   s->c2 = s->gam * s->p / s->rho;
 }
 
+/* Roe averages of a face (reading K): density, normal and tangential velocity, total
+ * enthalpy and formation energy with the weights sqrt(rho) / (sqrt(rho_L) + sqrt(rho_R)),
+ * gamma as the arithmetic mean, and the sound speed of the averaged state.  For physical
+ * face states (p, rho, T > 0) c2 >= (gamma~ - 1) min(h_L, h_R) >= c_min^2 / 2, since
+ * H~ - ef~ - q~^2/2 = w_L h_L + w_R h_R + w_L w_R |du|^2 / 2 with the sensible enthalpy
+ * h = c_v T + p/rho; c2 is nevertheless held at or above 1 % of the smaller side's c^2
+ * (c2_used), a guard against reconstructed states that rounding has made unphysical. */
+typedef struct { double rho, un, ut, H, ef, gam, q2, c2, c2_used; } roe_avg_t;
+
+static void roe_average(const face_t *L, const face_t *R, double unL, double utL, double unR, double utR,
+                        roe_avg_t *a) {
+  double sL = sqrt(L->rho), sR = sqrt(R->rho);
+  double wL = sL / (sL + sR), wR = sR / (sL + sR);
+  a->rho = sL * sR;
+  a->un = wL * unL + wR * unR;
+  a->ut = wL * utL + wR * utR;
+  a->H = wL * L->H + wR * R->H;
+  a->ef = wL * L->ef + wR * R->ef;
+  a->gam = 0.5 * (L->gam + R->gam);
+  a->q2 = a->un * a->un + a->ut * a->ut;
+  a->c2 = (a->gam - 1.0) * (a->H - 0.5 * a->q2 - a->ef);
+  double c2min = 0.01 * (L->c2 < R->c2 ? L->c2 : R->c2);
+  a->c2_used = a->c2 < c2min ? c2min : a->c2;
+}
+
 /* Roe flux between reconstructed primitive vectors qL, qR of nf fields (14, or 18 for the
  * bimodal liquid); F gets nf components. */
 static void roe_flux(const double *qL, const double *qR, int dir, int nf, double *F) {
@@ -815,19 +840,10 @@ static void roe_flux(const double *qL, const double *qR, int dir, int nf, double
   /* physical fluxes in (rho, rho u_n, rho u_t, rho E) */
   double FL[4] = {L.rho * unL, L.rho * unL * unL + L.p, L.rho * unL * utL, L.rho * unL * L.H};
   double FR[4] = {R.rho * unR, R.rho * unR * unR + R.p, R.rho * unR * utR, R.rho * unR * R.H};
-  /* Roe averages */
-  double sL = sqrt(L.rho), sR = sqrt(R.rho);
-  double wL = sL / (sL + sR), wR = sR / (sL + sR);
-  double rho_t = sL * sR;
-  double un = wL * unL + wR * unR;
-  double ut = wL * utL + wR * utR;
-  double H = wL * L.H + wR * R.H;
-  double ef = wL * L.ef + wR * R.ef;
-  double gam = 0.5 * (L.gam + R.gam);
-  double q2 = un * un + ut * ut;
-  double c2 = (gam - 1.0) * (H - 0.5 * q2 - ef);
-  double c2min = 0.01 * (L.c2 < R.c2 ? L.c2 : R.c2);
-  if (c2 < c2min) c2 = c2min;
+  roe_avg_t a;
+  roe_average(&L, &R, unL, utL, unR, utR, &a);
+  double rho_t = a.rho, un = a.un, ut = a.ut, H = a.H, q2 = a.q2;
+  double c2 = a.c2_used;
   double c = sqrt(c2);
   /* wave strengths */
   double drho = R.rho - L.rho, dun = unR - unL, dut = utR - utL, dp = R.p - L.p;
@@ -862,6 +878,19 @@ static void roe_flux(const double *qL, const double *qR, int dir, int nf, double
   for (int f = NF; f < nf; ++f) F[f] = Fc[0] * qu[f];
 }
 void or_roe_flux(const double *qL, const double *qR, int dir, double *F) { roe_flux(qL, qR, dir, NF, F); }
+/* Roe sound speed squared of a face, before (out[0]) and after (out[1]) the 1 % guard, and
+ * the two sides' c^2 (out[2], out[3]); for the pins of the averages. */
+void or_roe_c2(const double *qL, const double *qR, int dir, int nf, double *out) {
+  face_t L, R;
+  face_state(qL, nf == NF_BI, &L);
+  face_state(qR, nf == NF_BI, &R);
+  roe_avg_t a;
+  roe_average(&L, &R, dir == 0 ? L.u : L.v, dir == 0 ? L.v : L.u, dir == 0 ? R.u : R.v, dir == 0 ? R.v : R.u, &a);
+  out[0] = a.c2;
+  out[1] = a.c2_used;
+  out[2] = L.c2;
+  out[3] = R.c2;
+}
 void or_roe_flux_n(const double *qL, const double *qR, int dir, int nf, double *F) { roe_flux(qL, qR, dir, nf, F); }
 
 /* ------------------------------------------------------------------------------------

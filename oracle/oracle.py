@@ -251,3 +251,15 @@ class Oracle:
         amb = np.zeros(self.nf)
         _L().or_boundary_states(self._h, _ptr(inflow), _ptr(amb))
         return inflow, amb
+
+
+def roe_c2(qL: np.ndarray, qR: np.ndarray, direction: int) -> np.ndarray:
+    """Roe sound speed squared of a face before and after its 1 % guard, and both sides'
+    c^2 (face primitive vectors of 14 or 18 fields)."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    out = np.zeros(4)
+    lib = _L()
+    lib.or_roe_c2.argtypes = [_dp, _dp, C.c_int, C.c_int, _dp]
+    lib.or_roe_c2(_ptr(qL), _ptr(qR), direction, qL.shape[0], _ptr(out))
+    return out

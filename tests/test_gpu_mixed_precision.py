@@ -13,7 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_helpers import FIELD_NAMES, field_rel_err, report
+from gpu_helpers import FIELD_NAMES, FLOOR_FP32, field_rel_err, report
 from synth import cases
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_fp32_plume_4096x1024_against_fp64_after_2000_steps(P):
     c, uf = cases.plume_case_mixed_precision()
     U64, d64 = _run(P, c, uf, P.CT_FP64)
     U32, d32 = _run(P, c, uf, P.CT_FP32)
-    err = field_rel_err(U32, U64)
+    err = field_rel_err(U32, U64, FLOOR_FP32)
     a = U32.reshape(14, -1) - U64.reshape(14, -1)
     scale = np.maximum(np.abs(U64.reshape(14, -1)).max(1), 1e-300)
     scale[2] = max(scale[1], scale[2])              # rho v on the momentum scale

@@ -1,13 +1,14 @@
 """GPU parity: the CUDA FP64 path against the CPU oracle, element by element, through the
-C ABI.  Tolerance 1e-9 relative per field after 100 steps (max over cells of
-|gpu - oracle| / (|oracle| + 1e-6 max|oracle_f|))."""
+C ABI.  Tolerance 1e-9 relative per field after 100 steps: max over cells of
+|gpu - oracle| / (|oracle| + 1e-6 max|oracle_f|), with rho v on the momentum scale and a
+1e-3 floor (gpu_helpers).  The FP32 tests here keep a 1e-3 floor for every field."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 import oracle as O
-from gpu_helpers import field_rel_err, report
+from gpu_helpers import FLOOR_FP32, field_rel_err, report
 from synth import cases
 
 pytestmark = pytest.mark.gpu
@@ -227,7 +228,7 @@ def test_fp32_viscous_against_oracle(P):
     plume, field by field against the FP64 oracle."""
     c, uf = _viscous(cases.freezing_case(), 0.05)
     s, o, U0g, Ug, Uo, dg, do = _run_pair(P, c, uf, 100, precision=1)
-    e = field_rel_err(Ug, Uo)
+    e = field_rel_err(Ug, Uo, FLOOR_FP32)
     print("FP32 viscous freezing plume, 100 steps:", report(e))
     # bulk fields to FP32 rounding accumulated over the run; the droplet moments also carry
     # the FP32 rates of freezing and evaporation (exponentials of the Koop rate)
@@ -440,7 +441,7 @@ def test_bimodal_fp32_against_oracle(P):
     s = P.Solver(c, uf, precision=P.CT_FP32)
     s.load_state(torch.tensor(U0), 0.5)
     s.step(100, 0.5)
-    e = field_rel_err(s.state64(), Uo)
+    e = field_rel_err(s.state64(), Uo, FLOOR_FP32)
     print("FP32 bimodal freezing plume, 100 steps:", report(e))
     assert np.all(e[[0, 1, 3, 4, 13]] <= 1e-4), report(e)
     assert np.all(e <= 5e-3), report(e)

@@ -121,3 +121,35 @@ def test_mirror_state_gives_a_solid_wall():
     qR[1] = -qR[1]
     F = O.roe_flux(qL, qR, 0)
     assert F[0] == 0.0 and F[3] == 0.0 and np.all(F[4:] == 0.0)
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_roe_sound_speed_and_its_guard(d):
+    """Reading K's Roe averages: with weights w = sqrt(rho)/(sqrt(rho_L) + sqrt(rho_R)) and
+    the mean gamma, the averaged sound speed is
+        c~^2 = (gamma~ - 1) (w_L h_L + w_R h_R + w_L w_R |u_R - u_L|^2 / 2),
+    h = c^2/(gamma - 1) the sensible enthalpy of each side (c^2 = gamma p / rho), which
+    follows from H~ - ef~ - |u~|^2/2 with the latent formation energy averaged like H.
+    Hence c~^2 >= min(c_L^2, c_R^2)/2 for every physical pair, and the oracle's 1 % guard on
+    c~^2 never acts on them.  Random pairs with jumps in composition (vapour up to 0.2,
+    droplets, crystals), temperature (180-900 K) and velocity (up to 800 m/s)."""
+    rng = np.random.default_rng(11 + d)
+    for _ in range(400):
+        qs = []
+        for _side in range(2):
+            q, _ = _q_from(rng.uniform(5e3, 5e4), rng.uniform(180, 900), rng.uniform(-800, 800),
+                           rng.uniform(-800, 800), rng.uniform(0, 0.2),
+                           ml=tuple(rng.uniform(0, 1e11) * 0.1**k for k in range(4)),
+                           ms=tuple(rng.uniform(0, 1e9) * 1.0**k for k in range(4)),
+                           ns=rng.uniform(0, 1e12))
+            qs.append(q)
+        qL, qR = qs
+        c2, c2_used, c2L, c2R = O.roe_c2(qL, qR, d)
+        gL, gR = c2L * qL[0] / qL[3], c2R * qR[0] / qR[3]
+        sL, sR = math.sqrt(qL[0]), math.sqrt(qR[0])
+        wL, wR = sL / (sL + sR), sR / (sL + sR)
+        du2 = (qR[1] - qL[1]) ** 2 + (qR[2] - qL[2]) ** 2
+        expect = (0.5 * (gL + gR) - 1.0) * (wL * c2L / (gL - 1.0) + wR * c2R / (gR - 1.0) + 0.5 * wL * wR * du2)
+        assert c2 == pytest.approx(expect, rel=1e-11)
+        assert c2 >= 0.5 * min(c2L, c2R)
+        assert c2_used == c2

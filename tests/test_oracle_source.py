@@ -237,31 +237,72 @@ def test_every_source_conserves_water_and_never_creates_mass(dt):
     assert aux[:, 4].sum() > 100
 
 
-def test_freezing_transfers_mass_without_loss():
-    """Immersion + homogeneous freezing moves droplets to ice at equal mass
-    (rho_s r_f^3 = rho_l r_v^3); with growth switched off by S_l = S_i = 1 nothing else acts."""
-    T, p = 225.0, 24e3
-    r, n = 2e-7, 1e9
+def _freezing_state(T, p, r, n, ns):
+    """Droplets of radius r (n per kg) in vapour exactly at ice saturation (liquid
+    subsaturated: the droplets evaporate slowly while they freeze)."""
     ml = tuple(n * (r / 1e-6) ** k for k in range(4))
-    # vapour exactly at ice saturation; liquid subsaturated -> evaporation + freezing
     Ra, Rv = 287.05, O.const("R_v")
     pv = math.exp(O.ln_psat_i(T))
     Yv = pv * Ra / (Rv * (p - pv) + pv * Ra)
-    U = _state(p, T, Yv, ml=ml, ns=1e12)
-    Q, aux = O.source_batch(_case(), U, 1e-12)
-    omega = aux[0, 10]
-    assert omega > 0
+    return _state(p, T, Yv, ml=ml, ns=ns)
+
+
+def test_freezing_transfers_mass_without_loss():
+    """Eqs. (12)-(15) with reading H, checked without restating the source's formulas:
+    - frozen droplets become crystals of equal mass: the ice mass gained equals the liquid
+      mass lost by freezing, and the crystals' mean radius mu1/mu0 is r (rho_l/rho_s)^(1/3);
+    - the homogeneous part of the per-droplet rate scales with the droplet volume (x8 for
+      twice the radius) and equals Koop's rate coefficient (cm^-3 s^-1 -> m^-3 s^-1) times
+      that volume;
+    - the immersion part does not depend on the droplet size and equals
+      k_imm n_s 4 pi <r_p^2> chi, with <r_p^2> of the lognormal soot spectrum by quadrature
+      and chi = min(1, n_soot / mu0);
+    - over many short stages the droplet number decays as exp(-omega t), the solution of the
+      first-order freezing kinetics."""
+    T, p, r, n = 225.0, 24e3, 2e-7, 1e9
+    c = _case(freezing=1)
     dt = 1e-12
-    Nf = n * (-math.expm1(-omega * dt) / dt)     # first-order decay over the stage
-    rf = r * (1000.0 / 917.0) ** (1.0 / 3.0)
-    rho = U[0]
-    for k in range(4):
-        assert Q[0, 9 + k] == pytest.approx(rho * Nf * rf**k / 1e-6**k, rel=1e-12)
-    # Koop: 10^J in cm^-3 s^-1, clamped range of Delta a_w
-    daw = 1 - math.exp(O.ln_psat_i(T) - O.ln_psat_l(T))
-    assert aux[0, 9] == pytest.approx(O.koop_log10J(daw), rel=1e-14)
-    assert O.koop_log10J(0.2) == -math.inf
-    assert O.koop_log10J(0.5) == O.koop_log10J(0.34)
+    # homogeneous freezing alone (no soot): volume scaling and Koop's coefficient
+    Q1, a1 = O.source_batch(c, _freezing_state(T, p, r, n, 0.0), dt)
+    Q2, a2 = O.source_batch(c, _freezing_state(T, p, 2 * r, n, 0.0), dt)
+    assert a2[0, 10] / a1[0, 10] == pytest.approx(8.0, rel=1e-12)
+    daw = 1.0 - math.exp(O.ln_psat_i(T) - O.ln_psat_l(T))
+    assert a1[0, 10] == pytest.approx(1e6 * 10 ** O.koop_log10J(daw) * 4.0 / 3.0 * PI * r**3, rel=1e-12)
+    # immersion part alone at 250 K, where Delta a_w = 0.20 lies below Koop's range (no
+    # homogeneous freezing): soot per kg ns with chi = min(1, ns / n)
+    rm, sg = c["soot_rm"], c["soot_sigma"]
+    x = np.linspace(-10, 10, 20001)
+    pdf = np.exp(-0.5 * x * x) / math.sqrt(2 * PI)
+    rp2 = np.trapezoid(pdf * (rm * np.exp(math.log(sg) * x)) ** 2, x)     # <r_p^2> by quadrature
+    for ns_per_kg in (0.25 * n, 4.0 * n):
+        om = []
+        for rr in (r, 2 * r):
+            U = _freezing_state(250.0, p, rr, n, 0.0)
+            U[13] = U[0] * ns_per_kg
+            om.append(O.source_batch(c, U, dt)[1][0, 10])
+        assert om[0] == pytest.approx(om[1], rel=1e-12)                    # size-independent
+        assert om[0] == pytest.approx(1.0 * 1e8 * 4.0 * PI * rp2 * min(1.0, ns_per_kg / n), rel=1e-9)
+    # mass transfer: ice gained = liquid lost to freezing, crystals at r (rho_l/rho_s)^(1/3)
+    U = _freezing_state(T, p, r, n, 1e12)
+    Q, aux = O.source_batch(c, U, dt)
+    cf = O.source_batch(dict(c, freezing=0), U, dt)[0]
+    dliq_freeze = 1000.0 * (Q[0, 8] - cf[0, 8])      # rho_l d(mu3) from freezing alone
+    dice = 917.0 * Q[0, 12]
+    assert dice > 0 and dice == pytest.approx(-dliq_freeze, rel=1e-9)
+    assert Q[0, 10] / Q[0, 9] * 1e-6 == pytest.approx(r * (1000.0 / 917.0) ** (1.0 / 3.0), rel=1e-12)
+    # number decay over many short stages against exp(-omega t)
+    omega = aux[0, 10]
+    t_end = 0.5 / omega
+    m = 2000
+    h = t_end / m
+    cnum = dict(c)
+    V = U.copy()
+    for _ in range(m):
+        Qs, _ = O.source_batch(cnum, V, h)
+        V = V + h * Qs[0]                            # no transport: the cell's own kinetics
+    # the liquid also evaporates slightly (subsaturated): compare number, which only
+    # freezing changes (evaporation of a present population keeps mu0)
+    assert V[5] / U[5] == pytest.approx(math.exp(-omega * t_end), rel=2e-3)
 
 
 def test_koop_threshold_temperature():
