@@ -343,6 +343,70 @@ def run_cuda(args):
         dist.destroy_process_group()
 
 
+SURROGATE_DESC = ("hydrogen-like mixing plume 4096x1024 (pre-mixed layer, Y_v 0.2 core, 205 K ambient): "
+                  "the source fires in about half of the cells")
+
+
+def surrogate_record(dev, steps=20, err_steps=10):
+    """The metric's second half on a workload where the network runs: the plain FP64, the
+    plain FP32 and the FP32 + BF16 tensor-core surrogate paths on the same plume at config
+    4's grid, each timed over `steps` steps (CUDA events, autotuned tiles, after 3 warm-up
+    steps), with the active and fallback fractions and each FP32 path's per-field error
+    against the FP64 path after `err_steps` steps from the same initial state (the
+    nucleating mixing layer is chaotic over longer runs)."""
+    import torch
+    import paper_2504_20742_gb300 as P
+    from paper_2504_20742_gb300 import surrogate as S
+    from synth import cases
+    c, uf = cases.mixing_layer_case(nx=4096, nr=1024)
+    cells = c["nx"] * c["nr"]
+    blob = S.Surrogate.load(S.default_path()).blob(dev)
+    out = {"workload": SURROGATE_DESC, "cells": cells, "steps": steps}
+    stream = torch.cuda.Stream(dev)
+    ref = None
+    errs = {}
+    for name, prec in (("fp64", P.CT_FP64), ("fp32", P.CT_FP32), ("fp32_mlp", P.CT_FP32_MLP)):
+        with torch.cuda.stream(stream):
+            s = P.Solver(c, uf, precision=prec, device=dev, stream=stream)
+            s.init_state(0.5)
+            if prec == P.CT_FP32_MLP:
+                s.attach_surrogate(blob)
+            s.autotune(reps=2)
+            s.step(err_steps, 0.5)
+            U = s.state64()
+            if ref is None:
+                ref = U
+            else:
+                e = []
+                mom = max(np.abs(ref[1]).max(), np.abs(ref[2]).max())
+                for f in range(14):
+                    m = np.abs(ref[f]).max() if f != 2 else mom
+                    e.append(0.0 if m == 0 else float(np.max(np.abs(U[f] - ref[f]) / (np.abs(ref[f]) + 1e-3 * m))))
+                errs[name] = {"max_over_fields": round(max(e), 6), "rho": round(e[0], 8), "rho_E": round(e[3], 8),
+                              "liquid_number": round(e[5], 6), "ice_number": round(e[9], 6)}
+            s.step(3, 0.5)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps, 0.5)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            d = s.diagnostics()
+            out[name] = {"ms_per_step": round(ms, 4), "value": round(cells / (ms * 1e-3) / 1e9, 5),
+                         "active_frac": round(d[7] / cells, 4)}
+            if prec == P.CT_FP32_MLP:
+                out[name]["fallback_frac_of_active"] = round(d[26] / max(d[7], 1.0), 4)
+            del s
+            torch.cuda.empty_cache()
+    out["err_vs_fp64_after_steps"] = err_steps
+    out["err_vs_fp64"] = errs
+    out["speedup_fp32_mlp_over_fp64"] = round(out["fp64"]["ms_per_step"] / out["fp32_mlp"]["ms_per_step"], 3)
+    out["speedup_fp32_mlp_over_fp32"] = round(out["fp32"]["ms_per_step"] / out["fp32_mlp"]["ms_per_step"], 3)
+    out["error_metric"] = "max over cells of |x - x_fp64| / (|x_fp64| + 1e-3 max|x_fp64|), per field"
+    return out
+
+
 def run_batch(args):
     """The 64-case sweep stepped by the batched persistent kernel (one replica per GPU)."""
     import torch
@@ -516,6 +580,8 @@ def main():
                     help="stage-kernel tile shape (ct_tile_shape index) instead of the autotuner's pick "
                          "(single-case workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="leave out the FP64 / FP32 / FP32+surrogate record of the default workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -178,6 +178,16 @@ ct_status ct_diagnostics(const void *work, double *host_out, int nout, void *str
 ct_status ct_derived(const ct_case *c, int precision, const void *U, int which, double dt,
                      double *out, void *stream);
 
+/* Copy field `field` (0 .. nf-1, the SoA order of the state) of the state U (device, the
+ * precision's type, nf x nr x nx) into host_dst (host, n = nx * nr doubles, x fastest),
+ * converting FP32 states to FP64 on the host.  Synchronises `stream` (the copy follows the
+ * work already queued on it).  The fields are the conserved variables of Sec. 3.1 (Eqs.
+ * 22-26): rho, rho u, rho v, rho E, rho Y_v, then the moments rho mu_k of the liquid, the
+ * ice and the soot number (scaled as stated above).  Errors: CT_ERR_ARG for a bad field,
+ * size or pointer; CT_ERR_CUDA if the copy fails. */
+ct_status ct_read_field(const ct_case *c, int precision, const void *U, int field, double *host_dst, size_t n,
+                        void *stream);
+
 /* Phase-change source (Sec. 2.2) of n independent cells: U (device, n x nf doubles,
  * row-major conserved states, nf = CT_NFIELDS_BIMODAL for a bimodal case, else CT_NFIELDS)
  * -> Q (device, n x nf) and aux (device,
@@ -230,6 +240,13 @@ ct_status ct_mlp_forward(const float *params, const float *X, int n, float *Y, v
 ct_status ct_mlp_loss_grad(const float *params, const float *X, const float *Y, const float *M, int n, float *grad,
                            float *loss, void *work, size_t work_bytes, void *stream);
 
+/* The same loss and gradient with every GEMM (forward, input and weight gradients) on the
+ * BF16 tensor cores (tcgen05, FP32 accumulation in TMEM; operands rounded to BF16 as they
+ * are staged, FP32 master weights untouched); bias, SiLU, loss and bias gradients in FP32.
+ * err_flag (device int) is set to 1 if a bounded tensor-core wait gave up. */
+ct_status ct_mlp_loss_grad_tc(const float *params, const float *X, const float *Y, const float *M, int n, float *grad,
+                              float *loss, int *err_flag, void *work, size_t work_bytes, void *stream);
+
 /* One Adam step (bias-corrected, step >= 1) on nparam parameters. */
 ct_status ct_mlp_adam(float *params, const float *grad, float *m, float *v, int nparam, float lr, float beta1,
                       float beta2, float eps, int step, void *stream);
@@ -240,6 +257,36 @@ ct_status ct_mlp_colstats(const float *X, const float *M, int n, int d, float *o
 
 /* In-place standardisation X = (X - mean)/sd, column-wise (sd <= 0 treated as 1). */
 ct_status ct_mlp_standardize(float *X, int n, int d, const float *mean, const float *sd, void *stream);
+
+/* Configuration of ct_train_surrogate. */
+typedef struct {
+  int epochs;          /* passes over the rows */
+  int batch;           /* rows per Adam step (the last partial batch of an epoch is left out) */
+  float lr, lr_final;  /* learning rate, cosine decay from lr to lr_final over all steps */
+  float beta1, beta2, eps;   /* Adam */
+  uint64_t seed;       /* per-epoch shuffles: Fisher-Yates from splitmix64 */
+  int tensor_cores;    /* 1: BF16 tcgen05 GEMMs with FP32 accumulation and FP32 master weights */
+} ct_train_cfg;
+
+/* Bytes of device workspace ct_train_surrogate needs for n rows (0 for invalid sizes). */
+size_t ct_train_workspace_bytes(int n, int batch, int epochs);
+
+/* Train the source surrogate (the paper has no network: it stands in for the rates of
+ * Sec. 2.2) in one call: column statistics of X (inputs) and of Y over its mask M
+ * (targets), standardisation, then epochs of shuffled mini-batches, the masked MSE and its
+ * gradient (ct_mlp_loss_grad, or ct_mlp_loss_grad_tc with tensor_cores) and Adam with the
+ * cosine learning-rate schedule.
+ * X (n x CT_MLP_IN), Y and M (n x CT_MLP_OUT): device, raw units (ct_mlp_dataset).
+ * params: device, ct_mlp_param_count() floats, in: initial weights, out: trained weights
+ * (standardised units).  stats: device, 4 x CT_MLP_IN then 4 x CT_MLP_OUT floats out (mean,
+ * sd, min, max of the inputs and of the masked targets; sd below 1e-6 stored as 1), the
+ * arguments ct_mlp_pack takes.  loss_hist: host, epochs floats out (mean batch loss).
+ * work: device, ct_train_workspace_bytes(n, batch, epochs).  Runs on `stream` and returns
+ * after it has finished.  Errors: CT_ERR_ARG, CT_ERR_SIZE, CT_ERR_CUDA, CT_ERR_TIMEOUT (a
+ * tensor-core wait gave up). */
+ct_status ct_train_surrogate(const float *X, const float *Y, const float *M, int n, const ct_train_cfg *cfg,
+                             float *params, float *stats, float *loss_hist, void *work, size_t work_bytes,
+                             void *stream);
 
 /* Bytes of the device blob of a packed surrogate (BF16 weights in tensor-core operand
  * order, FP32 biases, input/output standardisation and the training hull). */

@@ -47,6 +47,12 @@ class CtCase(C.Structure):
         return s
 
 
+class CtTrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64),
+                ("tensor_cores", C.c_int)]
+
+
 class ContrailError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"contrail status {status}: {msg}")
@@ -65,6 +71,7 @@ _SIGS = {
     "ct_step_host": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "ct_diagnostics": (C.c_int, [_vp, _dp, C.c_int, _vp]),
     "ct_derived": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp]),
+    "ct_read_field": (C.c_int, [_cp, C.c_int, _vp, C.c_int, _dp, C.c_size_t, _vp]),
     "ct_source_batch": (C.c_int, [_cp, C.c_int, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
     "ct_reconstruct_faces": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp]),
     "ct_step_static": (C.c_int, [_cp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
@@ -73,10 +80,14 @@ _SIGS = {
     "ct_mlp_work_bytes": (C.c_size_t, [C.c_int]),
     "ct_mlp_forward": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp]),
     "ct_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "ct_mlp_loss_grad_tc": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "ct_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                               _vp]),
     "ct_mlp_colstats": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp]),
     "ct_mlp_standardize": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "ct_train_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "ct_train_surrogate": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(CtTrainCfg), _vp, _vp,
+                                     C.POINTER(C.c_float), _vp, C.c_size_t, _vp]),
     "ct_mlp_blob_bytes": (C.c_size_t, []),
     "ct_mlp_pack": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ct_mlp_infer": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
@@ -236,6 +247,11 @@ def ct_mlp_loss_grad(params, X, Y, M, n, grad, loss, work, work_bytes, stream=No
                                  work_bytes, _stream(stream)))
 
 
+def ct_mlp_loss_grad_tc(params, X, Y, M, n, grad, loss, err_flag, work, work_bytes, stream=None):
+    _check(_L().ct_mlp_loss_grad_tc(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), n, _ptr(grad), _ptr(loss),
+                                    _ptr(err_flag), _ptr(work), work_bytes, _stream(stream)))
+
+
 def ct_mlp_adam(params, grad, m, v, nparam, lr, beta1, beta2, eps, step, stream=None):
     _check(_L().ct_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), nparam, lr, beta1, beta2, eps, step,
                             _stream(stream)))
@@ -370,3 +386,29 @@ def ct_batch_diagnostics(b, ncases: int, raise_nonfinite: bool = False) -> np.nd
     if st != 0 and (st != 3 or raise_nonfinite):
         _check(st)
     return out
+
+
+def ct_read_field(case, precision, U, field, stream=None) -> np.ndarray:
+    """Field `field` of the device state U as an (nr, nx) float64 host array."""
+    c = _case(case)
+    nr = c.nr if c.geom == 1 else 1
+    out = np.empty((nr, c.nx), dtype=np.float64)
+    _check(_L().ct_read_field(C.byref(c), precision, _ptr(U), field, out.ctypes.data_as(_dp), out.size,
+                              _stream(stream)))
+    return out
+
+
+def ct_train_workspace_bytes(n, batch, epochs) -> int:
+    return _L().ct_train_workspace_bytes(n, batch, epochs)
+
+
+def ct_train_surrogate(X, Y, M, n, cfg: dict, params, stats, work, work_bytes, stream=None) -> np.ndarray:
+    """Runs the whole training loop in the library; returns the per-epoch mean loss."""
+    k = CtTrainCfg(epochs=int(cfg["epochs"]), batch=int(cfg["batch"]), lr=float(cfg["lr"]),
+                   lr_final=float(cfg["lr_final"]), beta1=float(cfg.get("beta1", 0.9)),
+                   beta2=float(cfg.get("beta2", 0.999)), eps=float(cfg.get("eps", 1e-8)),
+                   seed=int(cfg.get("seed", 0)), tensor_cores=int(cfg.get("tensor_cores", 0)))
+    hist = (C.c_float * k.epochs)()
+    _check(_L().ct_train_surrogate(_ptr(X), _ptr(Y), _ptr(M), n, C.byref(k), _ptr(params), _ptr(stats), hist,
+                                   _ptr(work), work_bytes, _stream(stream)))
+    return np.array([float(v) for v in hist])

@@ -756,6 +756,31 @@ ct_status ct_diagnostics(const void* work, double* host_out, int nout, void* str
   return CT_OK;
 }
 
+ct_status ct_read_field(const ct_case* c, int precision, const void* U, int field, double* host_dst, size_t n,
+                        void* stream) {
+  ct_status s = validate(c, precision);
+  if (s != CT_OK) return s;
+  if (!U || !host_dst) return fail(CT_ERR_ARG, "null buffer");
+  if (field < 0 || field >= case_nf(c)) return fail(CT_ERR_ARG, "field out of range");
+  const size_t N = (size_t)c->nx * case_nr(c);
+  if (n != N) return fail(CT_ERR_ARG, "n must be nx * nr");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == CT_FP64) {
+    if (cudaMemcpyAsync(host_dst, (const double*)U + (size_t)field * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+      return cuda_check("ct_read_field copy");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_read_field sync");
+    return CT_OK;
+  }
+  std::vector<float> tmp(N);
+  if (cudaMemcpyAsync(tmp.data(), (const float*)U + (size_t)field * N, N * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return cuda_check("ct_read_field copy");
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_read_field sync");
+  for (size_t i = 0; i < N; ++i) host_dst[i] = (double)tmp[i];
+  return CT_OK;
+}
+
 ct_status ct_derived(const ct_case* c, int precision, const void* U, int which, double dt, double* out, void* stream) {
   ct_status s = validate(c, precision);
   if (s != CT_OK) return s;

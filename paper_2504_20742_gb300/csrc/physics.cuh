@@ -524,6 +524,41 @@ __device__ __forceinline__ Sat<T> saturation(const Prim<T>& w, const SrcCase& sc
   return s;
 }
 
+// Classical nucleation, Eqs. (3), (4), (9), (10), with the soot gate of J_het (reading F):
+// the Kelvin radius, the vapour density and the two rates, in FP64 (ln S, the barrier and
+// its exponential are the FP64 islands of the FP32 path).  Only for ln S_l > 0.  lnJ2 gets
+// ln J_hom and ln J_het,eff (-inf without soot).
+struct Cnt {
+  double rc, rhov, Jhom, Jhet, Jsum;
+};
+template <class T>
+__device__ __forceinline__ Cnt cnt_rates(const Prim<T>& w, double lnSl, const SrcCase& sc, double* lnJ2) {
+  const T Tg = w.Tg, rho = w.rho;
+  Cnt c;
+  const T sig = prop_sigma<T>(sc, Tg);
+  const double sigd = double(sig);
+  c.rc = 2.0 * sigd / (k::RHOL * k::RV * double(Tg) * lnSl);
+  const double dGkT = k::FOUR_PI_3 * sigd * c.rc * c.rc / (k::KB * double(Tg));
+  c.rhov = double(rho) * double(w.Yv);
+  // ln A = ln q_c + 1/2 ln(2 sigma N_A^3 / (pi M^3)) + 2 ln rho_v - ln rho_l
+  const double lnA = 0.5 * m_log(2.0 * sigd) + 0.5 * m_log(k::NA * k::NA * k::NA / (k::PI * k::MW * k::MW * k::MW)) +
+                     2.0 * m_log(c.rhov) - m_log(k::RHOL);
+  const double lnJhom = lnA - dGkT;
+  const double lnJhet = lnA - k::FTHETA * dGkT;
+  c.Jhom = m_exp(lnJhom);
+  c.Jsum = c.Jhom;
+  c.Jhet = 0.0;
+  lnJ2[0] = lnJhom;
+  const double nsv = double(rho) * double(w.ns);
+  if (sc.n_soot_ref > 0.0 && nsv > 0.0) {
+    const double gate = nsv / sc.n_soot_ref;
+    c.Jhet = m_exp(lnJhet) * gate;
+    c.Jsum += c.Jhet;
+    lnJ2[1] = lnJhet + m_log(gate);
+  }
+  return c;
+}
+
 // Plain rates, Sec. 2.2.  ext (optional, the surrogate's training targets): 0 ln Jeff,
 // 1 ln r_crit/um, 2 G_l raw (um/s), 3 G_s raw, 4 1/tau_l, 5 1/tau_s, 6 ln J_hom,
 // 7 ln J_het,eff, 8 ln(1+phi), 9 T_sat,l - T.
@@ -552,26 +587,8 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
   T Tsat_l = T(0);
   bool have_tsat_l = false;
   if (lnSl > 0.0) {
-    const T sig = prop_sigma<T>(sc, Tg);
-    const double sigd = double(sig);
-    const double rc = 2.0 * sigd / (k::RHOL * k::RV * double(Tg) * lnSl);
-    const double dGkT = k::FOUR_PI_3 * sigd * rc * rc / (k::KB * double(Tg));
-    const double rhov = double(rho) * double(w.Yv);
-    // ln A = ln q_c + 1/2 ln(2 sigma N_A^3 / (pi M^3)) + 2 ln rho_v - ln rho_l
-    const double lnA = 0.5 * m_log(2.0 * sigd) + 0.5 * m_log(k::NA * k::NA * k::NA / (k::PI * k::MW * k::MW * k::MW)) +
-                       2.0 * m_log(rhov) - m_log(k::RHOL);
-    const double lnJhom = lnA - dGkT;
-    const double lnJhet = lnA - k::FTHETA * dGkT;
-    const double Jhom = m_exp(lnJhom);
-    double Jsum = Jhom, Jhet = 0.0;
-    lnJ2[0] = lnJhom;
-    const double nsv = double(rho) * double(w.ns);
-    if (sc.n_soot_ref > 0.0 && nsv > 0.0) {
-      const double gate = nsv / sc.n_soot_ref;
-      Jhet = m_exp(lnJhet) * gate;
-      Jsum += Jhet;
-      lnJ2[1] = lnJhet + m_log(gate);
-    }
+    const Cnt c = cnt_rates<T>(w, lnSl, sc, lnJ2);
+    const double rc = c.rc, rhov = c.rhov, Jhom = c.Jhom, Jhet = c.Jhet, Jsum = c.Jsum;
     // Eq. (5) with alpha_crit from Young's law at r_crit (reading F)
     Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
     have_tsat_l = true;

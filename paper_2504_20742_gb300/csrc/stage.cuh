@@ -507,19 +507,19 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
       const float* y = reinterpret_cast<const float*>(smem + SM_RES) + 10 * threadIdx.x;
       const bool nuc = st.lnSl > 0.0;
       Rates<T> r;
-      r.Jeff = nuc ? T(__expf(y[0])) : T(0);
-      // the Kelvin radius of Eq. (3) is a closed form: evaluated, not predicted
-      r.rc_um = nuc ? T(2.0f * prop_sigma<float>(dc.sc, float(w.Tg)) * 1e6f /
-                        (float(k::RHOL * k::RV) * float(w.Tg) * float(st.lnSl)))
-                    : T(0);
+      r.Jeff = r.rc_um = T(0);
+      if (nuc) {
+        // the nucleation rates and the Kelvin radius are closed forms (Eqs. 3, 4, 10) whose
+        // exponent is an FP64 island: evaluated, not predicted.  The network supplies the
+        // Kantrowitz factor ln(1 + phi) (Eq. 5, which needs T_sat and Young's law at r_crit)
+        const Cnt c = cnt_rates<T>(w, st.lnSl, dc.sc, lnJ2);
+        r.Jeff = T(float(c.Jsum) * __expf(-y[8]));
+        r.rc_um = T(c.rc * 1e6);
+      }
       r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);
       r.Gs = st.pres_s ? T(MLP_G0 * sinhf(y[3])) : T(0);
       r.xl = st.pres_l ? T(__expf(y[4])) : T(0);
       r.xs = st.pres_s ? T(__expf(y[5])) : T(0);
-      if (nuc) {
-        lnJ2[0] = y[6];
-        if (dc.sc.n_soot_ref > 0.0 && w.rho * w.ns > T(0)) lnJ2[1] = y[7];
-      }
       source_tail<T>(w, u14, acc, dt, dc.sc, st.pres_l, st.pres_s, st.lnSl, st.lnSi, r, Q, nullptr);
     }
   }

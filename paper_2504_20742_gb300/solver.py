@@ -65,6 +65,10 @@ class Solver:
         self.stream.synchronize()
         return self.U.detach().to(torch.float64).cpu().numpy()
 
+    def read_field(self, field: int) -> np.ndarray:
+        """One field of the state as an (nr, nx) float64 host array (ct_read_field)."""
+        return L.ct_read_field(self.case, self.precision, self.U, field, self.stream)
+
 
 class Batch:
     """Many axisymmetric cases stepped together by the persistent, graph-captured kernel.

@@ -124,51 +124,28 @@ class Surrogate:
 
 
 def train(X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int = 20, batch: int = 8192,
-          lr: float = 2e-3, seed: int = 0, lr_final: float = 5e-5, verbose: bool = False) -> Surrogate:
-    """Adam on the masked MSE of standardised targets, cosine learning-rate decay."""
+          lr: float = 2e-3, seed: int = 0, lr_final: float = 5e-5, tensor_cores: bool = False,
+          verbose: bool = False) -> Surrogate:
+    """Adam on the masked MSE of standardised targets with a cosine learning-rate decay, run
+    entirely by the library (ct_train_surrogate: statistics, standardisation, shuffles,
+    batches, gradients and Adam); this wrapper allocates the device buffers."""
     dev = X.device
     n = X.shape[0]
-    sx = colstats(X)
-    sy = colstats(Y, M)
-    x_sd = torch.where(sx[1] > 1e-6, sx[1], torch.ones_like(sx[1]))
-    y_sd = torch.where(sy[1] > 1e-6, sy[1], torch.ones_like(sy[1]))
-    Xn = X.clone().contiguous()
-    Yn = Y.clone().contiguous()
-    L.ct_mlp_standardize(Xn, n, L.CT_MLP_IN, sx[0].contiguous(), x_sd.contiguous())
-    L.ct_mlp_standardize(Yn, n, L.CT_MLP_OUT, sy[0].contiguous(), y_sd.contiguous())
-    Yn = Yn * M      # masked entries carry no information
     P = torch.tensor(init_params(seed), device=dev)
-    G = torch.zeros_like(P)
-    m1 = torch.zeros_like(P)
-    m2 = torch.zeros_like(P)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    wb = L.ct_mlp_work_bytes(batch)
+    stats = torch.zeros(4 * L.CT_MLP_IN + 4 * L.CT_MLP_OUT, dtype=torch.float32, device=dev)
+    wb = L.ct_train_workspace_bytes(n, batch, epochs)
     work = torch.empty(wb // 4 + 64, dtype=torch.float32, device=dev)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(seed)
-    nb = max(1, n // batch)
-    total = epochs * nb
-    hist = []
-    step = 0
-    for ep in range(epochs):
-        perm = torch.randperm(n, generator=gen, device=dev)
-        acc = torch.zeros((), dtype=torch.float64, device=dev)
-        for b in range(nb):
-            idx = perm[b * batch:(b + 1) * batch]
-            xb, yb, mb = Xn[idx].contiguous(), Yn[idx].contiguous(), M[idx].contiguous()
-            L.ct_mlp_loss_grad(P, xb, yb, mb, xb.shape[0], G, loss, work, wb)
-            step += 1
-            frac = step / total
-            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * frac))
-            L.ct_mlp_adam(P, G, m1, m2, P.numel(), float(lr_t), 0.9, 0.999, 1e-8, step)
-            acc += loss[0].double()
-        hist.append(float(acc) / nb)
-        if verbose:
-            print(f"epoch {ep}: loss {hist[-1]:.5f}", flush=True)
-    return Surrogate(params=P.cpu().numpy(), x_mean=sx[0].cpu().numpy(), x_sd=x_sd.cpu().numpy(),
-                     x_min=sx[2].cpu().numpy(), x_max=sx[3].cpu().numpy(), y_mean=sy[0].cpu().numpy(),
-                     y_sd=y_sd.cpu().numpy(), y_min=sy[2].cpu().numpy(), y_max=sy[3].cpu().numpy(),
-                     history=np.array(hist))
+    cfg = dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, seed=seed, tensor_cores=int(tensor_cores))
+    hist = L.ct_train_surrogate(X.contiguous(), Y.contiguous(), M.contiguous(), n, cfg, P, stats, work, wb,
+                                torch.cuda.current_stream(dev))
+    if verbose:
+        for ep, v in enumerate(hist):
+            print(f"epoch {ep}: loss {v:.5f}", flush=True)
+    st = stats.cpu().numpy()
+    sx = st[:4 * L.CT_MLP_IN].reshape(4, L.CT_MLP_IN)
+    sy = st[4 * L.CT_MLP_IN:].reshape(4, L.CT_MLP_OUT)
+    return Surrogate(params=P.cpu().numpy(), x_mean=sx[0], x_sd=sx[1], x_min=sx[2], x_max=sx[3], y_mean=sy[0],
+                     y_sd=sy[1], y_min=sy[2], y_max=sy[3], history=hist)
 
 
 def default_path() -> str:

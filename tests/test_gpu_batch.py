@@ -207,3 +207,53 @@ def test_stored_primitives_change_no_bit(P, make):
     P.ct_step_static(c, P.CT_FP64, ufac, U, U1, 20, 0.5)
     torch.cuda.synchronize()
     assert torch.equal(U, a.U)
+
+
+def _oracle_batch():
+    """Uneven cases whose phase change runs from the first step and whose trajectories are
+    well conditioned (no nucleation bursts): the freezing plume on three grids and at two
+    ambient temperatures, plus a cut case of the plume sweep."""
+    out = []
+    for nx, nr, tamb in ((96, 40, 225.0), (77, 29, 225.0), (64, 24, 215.0)):
+        c, uf = cases.freezing_case(nx=nx, nr=nr)
+        out.append((dict(c, T_amb=tamb), uf))
+    c, _ = cases.batch_cases(n=1)[0]
+    c = dict(c, nx=128, nr=32)
+    out.append((c, np.ones(32)))
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_cases_against_the_oracle(P, blob, prec):
+    """The batched persistent kernel against the FP64 oracle itself, case by case, after 100
+    steps.  FP32 transport with FP64 islands: density, momentum, energy and vapour to 1e-4
+    and every field to 5e-3 at a floor of 1e-3 of its maximum (without viscosity the soot
+    and the particle moments keep sharp contacts, where FP32 rounding moves the limiter's
+    decisions: about 2e-3 there).  With the surrogate: the total liquid and ice number of
+    every case within 2 % of the oracle."""
+    import oracle as O
+    from gpu_helpers import FLOOR_FP32, field_rel_err, report
+    bc = _oracle_batch()
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=prec, blob=blob if prec == 2 else None)
+    b.init_state(0.5)
+    b.step(100, 0.5)
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0)
+    for k, (c, uf) in enumerate(bc):
+        o = O.Oracle(c, uf)
+        Uo = o.init_state()
+        do = o.step(Uo, 100, 0.5)
+        U = b.state(k).double().cpu().numpy()
+        assert db[k, 0] == pytest.approx(do[-1, 0], rel=1e-4)      # each case its own dt
+        if prec == 1:
+            e = field_rel_err(U, Uo, FLOOR_FP32)
+            print(f"batch case {k} ({c['nx']}x{c['nr']}), FP32 vs oracle:", report(e))
+            assert np.all(e[[0, 1, 3, 4]] <= 1e-4), report(e)
+            assert np.all(e <= 5e-3), report(e)
+        else:
+            for f in (5, 9):
+                ref = Uo[f].sum()
+                if ref > 0:
+                    err = abs(U[f].sum() / ref - 1.0)
+                    print(f"batch case {k}, surrogate, field {f} total number vs oracle: {err:.2e}")
+                    assert err <= 2e-2, (k, f, err)

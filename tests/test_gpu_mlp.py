@@ -110,3 +110,117 @@ def test_training_reduces_loss_on_sampled_states(P):
     assert X.shape[0] > 5000 and bool(torch.isfinite(X).all()) and bool(torch.isfinite(Y).all())
     sur = S.train(X, Y, M, epochs=6, batch=2048, lr=2e-3)
     assert sur.history[-1] < 0.25 * sur.history[0], sur.history
+
+
+def _sampled(P, S):
+    c, uf = cases.freezing_case(nx=64, nr=32)
+    U = S.sample_active_states(c, uf, nsteps=40, every=4)
+    return S.dataset(c, U)
+
+
+def test_train_surrogate_is_one_deterministic_library_call(P):
+    """ct_train_surrogate runs statistics, standardisation, shuffles, batches, gradients and
+    Adam inside the library: two calls with the same seed give the same parameters bit for
+    bit, another seed other ones, and the statistics are ct_mlp_colstats' (inputs unmasked,
+    targets over their mask)."""
+    from paper_2504_20742_gb300 import surrogate as S
+    X, Y, M = _sampled(P, S)
+    n = X.shape[0]
+    a = S.train(X, Y, M, epochs=3, batch=1024, lr=2e-3, seed=4)
+    b = S.train(X, Y, M, epochs=3, batch=1024, lr=2e-3, seed=4)
+    c = S.train(X, Y, M, epochs=3, batch=1024, lr=2e-3, seed=5)
+    assert np.array_equal(a.params, b.params) and np.array_equal(a.history, b.history)
+    assert not np.array_equal(a.params, c.params)
+    assert np.all(np.isfinite(a.params)) and a.history[-1] < a.history[0]
+    sx = S.colstats(X).cpu().numpy()
+    sy = S.colstats(Y, M).cpu().numpy()
+    assert np.array_equal(a.x_mean, sx[0]) and np.array_equal(a.x_min, sx[2]) and np.array_equal(a.x_max, sx[3])
+    assert np.array_equal(a.y_mean, sy[0]) and np.array_equal(a.y_max, sy[3])
+    assert np.array_equal(a.x_sd, np.where(sx[1] > 1e-6, sx[1], 1.0).astype(np.float32))
+
+
+def test_train_surrogate_first_epoch_loss_is_the_loss_of_the_initial_network(P):
+    """With one batch of all rows per epoch, the first epoch's recorded loss is the masked
+    MSE of the initial parameters on the standardised rows (ct_mlp_loss_grad on the
+    unshuffled rows; the two sums differ only in order)."""
+    from paper_2504_20742_gb300 import surrogate as S
+    X, Y, M = _sampled(P, S)
+    n = X.shape[0]
+    sur = S.train(X, Y, M, epochs=1, batch=n, lr=1e-3, seed=2)
+    sx, sy = S.colstats(X), S.colstats(Y, M)
+    sdx = torch.where(sx[1] > 1e-6, sx[1], torch.ones_like(sx[1])).contiguous()
+    sdy = torch.where(sy[1] > 1e-6, sy[1], torch.ones_like(sy[1])).contiguous()
+    Xn, Yn = X.clone().contiguous(), Y.clone().contiguous()
+    P.ct_mlp_standardize(Xn, n, 16, sx[0].contiguous(), sdx)
+    P.ct_mlp_standardize(Yn, n, 10, sy[0].contiguous(), sdy)
+    Yn = (Yn * M).contiguous()
+    p0 = torch.tensor(S.init_params(2), device="cuda")
+    g = torch.empty_like(p0)
+    loss = torch.zeros(1, device="cuda")
+    wb = P.ct_mlp_work_bytes(n)
+    work = torch.empty(wb // 4 + 64, dtype=torch.float32, device="cuda")
+    P.ct_mlp_loss_grad(p0, Xn, Yn, M.contiguous(), n, g, loss, work, wb)
+    assert sur.history[0] == pytest.approx(float(loss), rel=1e-5)
+
+
+def _tc_grad(P, theta, X, Y, M):
+    d = "cuda"
+    n = X.shape[0]
+    p = torch.tensor(theta, device=d)
+    Xt, Yt, Mt = (torch.tensor(a, device=d) for a in (X, Y, M))
+    wb = P.ct_mlp_work_bytes(n)
+    work = torch.empty(wb // 4 + 64, dtype=torch.float32, device=d)
+    g = torch.empty_like(p)
+    loss = torch.zeros(1, device=d)
+    err = torch.zeros(1, dtype=torch.int32, device=d)
+    P.ct_mlp_loss_grad_tc(p, Xt, Yt, Mt, n, g, loss, err, work, wb)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    return float(loss), g.cpu().numpy()
+
+
+def test_tensor_core_gradient_matches_fp64_reference(P):
+    """BF16 tensor-core forward and backward (FP32 accumulation, FP32 master weights) vs the
+    FP64 chain rule on 64 samples: loss and gradient within 1e-2 relative (BF16 operands)."""
+    theta = R.init_params(3).astype(np.float32)
+    theta += 0.01 * np.random.default_rng(5).standard_normal(theta.size).astype(np.float32)
+    X, Y, M = _data(64, 7)
+    loss, gg = _tc_grad(P, theta, X, Y, M)
+    Lr, gr = R.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), Y.astype(np.float64),
+                             M.astype(np.float64))
+    assert loss == pytest.approx(Lr, rel=1e-2)
+    assert np.linalg.norm(gg - gr) <= 1e-2 * np.linalg.norm(gr)
+    # layer by layer, every weight and bias block within 2e-2 of its own norm
+    off = 0
+    for fi, fo in zip(R.LAYERS[:-1], R.LAYERS[1:]):
+        for size in (fi * fo, fo):
+            blk = slice(off, off + size)
+            assert np.linalg.norm(gg[blk] - gr[blk]) <= 2e-2 * np.linalg.norm(gr[blk]) + 1e-12, (fi, fo, size)
+            off += size
+
+
+@pytest.mark.parametrize("n", [1000, 8192])
+def test_tensor_core_gradient_matches_fp32_kernels_on_batches(P, n):
+    """Full batches (split-K weight gradients over up to 32 partial tiles, ragged row counts):
+    tensor-core and FP32 gradients agree within 1e-2 relative."""
+    theta = R.init_params(4).astype(np.float32)
+    X, Y, M = _data(n, 9)
+    loss_tc, g_tc = _tc_grad(P, theta, X, Y, M)
+    d = "cuda"
+    p = torch.tensor(theta, device=d)
+    Xt, Yt, Mt = (torch.tensor(a, device=d) for a in (X, Y, M))
+    wb = P.ct_mlp_work_bytes(n)
+    work = torch.empty(wb // 4 + 64, dtype=torch.float32, device=d)
+    g = torch.empty_like(p)
+    loss = torch.zeros(1, device=d)
+    P.ct_mlp_loss_grad(p, Xt, Yt, Mt, n, g, loss, work, wb)
+    g32 = g.cpu().numpy()
+    assert loss_tc == pytest.approx(float(loss), rel=1e-2)
+    assert np.linalg.norm(g_tc - g32) <= 1e-2 * np.linalg.norm(g32)
+
+
+def test_tensor_core_training_reduces_loss(P):
+    from paper_2504_20742_gb300 import surrogate as S
+    X, Y, M = _sampled(P, S)
+    sur = S.train(X, Y, M, epochs=4, batch=2048, lr=2e-3, tensor_cores=True)
+    assert np.all(np.isfinite(sur.params)) and sur.history[-1] < 0.5 * sur.history[0], sur.history

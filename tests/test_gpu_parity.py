@@ -1,6 +1,6 @@
 """GPU parity: the CUDA FP64 path against the CPU oracle, element by element, through the
 C ABI.  Tolerance 1e-9 relative per field after 100 steps: max over cells of
-|gpu - oracle| / (|oracle| + 1e-6 max|oracle_f|), with rho v on the momentum scale and a
+|gpu - oracle| / (|oracle| + 1e-5 max|oracle_f|), with rho v on the momentum scale and a
 1e-3 floor (gpu_helpers).  The FP32 tests here keep a 1e-3 floor for every field."""
 import numpy as np
 import pytest
@@ -453,3 +453,17 @@ def test_bimodal_rejected_with_the_surrogate_and_equilibrium(P):
         P.Solver(c, uf, precision=P.CT_FP32_MLP)
     with pytest.raises(P.ContrailError):
         P.Solver(dict(c, equilibrium=1), uf)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_read_field_returns_the_state(P, precision):
+    """ct_read_field copies one field to the host (FP32 converted to FP64, exactly)."""
+    c, uf = cases.freezing_case(nx=77, nr=29)
+    s = P.Solver(c, uf, precision=precision)
+    s.init_state(0.5)
+    s.step(3, 0.5)
+    U = s.state64()
+    for f in range(14):
+        assert np.array_equal(s.read_field(f), U[f]), f
+    with pytest.raises(P.ContrailError):
+        P.ct_read_field(c, precision, s.U, 14)

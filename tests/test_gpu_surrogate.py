@@ -49,64 +49,99 @@ def test_surrogate_step_conserves_and_reports_fallbacks(P, sur):
     assert 0 <= d[26] <= d[7]
 
 
-def test_surrogate_rates_on_visited_states(P, sur):
-    """log10 J_hom of the BF16 tensor-core network against the FP64 plain source on states
-    visited by FP64 runs of the nozzle and a hydrogen-like mixing layer, where J >= 1."""
+def _visited(P):
     from paper_2504_20742_gb300 import surrogate as S
     rows = []
     for c, uf, n in ((cases.nozzle_case(nx=400), None, 600), (cases.mixing_layer_case(nx=96, nr=40)[0],
                                                                cases.mixing_layer_case(nx=96, nr=40)[1], 60)):
         U = S.sample_active_states(c, uf, nsteps=n, every=3)
-        X, Y, M = S.dataset(c, U)
-        rows.append((X, Y, M))
-    X = torch.cat([r[0] for r in rows])
-    Y = torch.cat([r[1] for r in rows])
-    M = torch.cat([r[2] for r in rows])
+        rows.append(S.dataset(c, U))
+    return (torch.cat([r[q] for r in rows]) for q in range(3))
+
+
+def test_surrogate_rates_on_visited_states(P, sur):
+    """The rates the FP32 + surrogate step takes on states visited by FP64 runs of the nozzle
+    and a hydrogen-like mixing layer.  Nucleation: J_hom and J_het (Eqs. 4, 10) are closed
+    forms evaluated in the step (their exponent in FP64), so log10 J is exact; the effective
+    rate J/(1 + phi) carries the network's Kantrowitz factor, whose error in log10 stays
+    within 0.25 everywhere with J >= 1 m^-3 s^-1 and within 0.02 for 99 % of those states.
+    Growth and relaxation rates: the network's errors are reported."""
+    X, Y, M = _visited(P)
     blob = sur.blob()
     Yp = torch.empty_like(Y)
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     P.ct_mlp_infer(blob, X.contiguous(), X.shape[0], Yp, err)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    m = (M[:, 6] > 0) & (Y[:, 6] >= 0)
+    m = (M[:, 8] > 0) & (Y[:, 6] >= 0)
     assert int(m.sum()) > 1000
-    e10 = ((Yp[m, 6] - Y[m, 6]).abs() / np.log(10.0)).cpu().numpy()
-    print(f"log10 J_hom error where J >= 1: mean {e10.mean():.3f}, p90 {np.quantile(e10, 0.9):.3f}, "
-          f"p99 {np.quantile(e10, 0.99):.3f}, n {e10.size}")
-    assert e10.mean() <= 0.1
-    assert np.quantile(e10, 0.9) <= 0.25
+    e10 = ((Yp[m, 8] - Y[m, 8]).abs() / np.log(10.0)).cpu().numpy()
+    print(f"log10 J/(1+phi) error where J >= 1: max {e10.max():.3f}, p99 {np.quantile(e10, 0.99):.4f}, "
+          f"mean {e10.mean():.4f}, n {e10.size}")
+    for q, name in ((2, "asinh G_l"), (3, "asinh G_s"), (4, "ln 1/tau_l"), (5, "ln 1/tau_s")):
+        mm = M[:, q] > 0
+        d = (Yp[mm, q] - Y[mm, q]).abs().cpu().numpy()
+        print(f"{name}: mean |error| {d.mean():.3f}, p90 {np.quantile(d, 0.9):.3f}, n {d.size}")
+    assert e10.max() <= 0.25 and np.quantile(e10, 0.99) <= 0.02
 
 
-def test_surrogate_trajectory_vs_oracle_on_nozzle(P, sur):
-    """The 400-cell condensing nozzle, 300 steps: the FP32 + surrogate state against
-    the FP64 oracle, and the plain FP32 state against it, field by field."""
+def _number_errors(U, Uo, f):
+    ref, got = Uo[f].ravel(), U[f].ravel()
+    m = ref > 1e-6 * ref.max()
+    return abs(got.sum() / ref.sum() - 1.0), np.abs(got[m] - ref[m]).sum() / np.abs(ref[m]).sum()
+
+
+def test_surrogate_number_density_on_the_nozzle_at_steady_state(P, sur):
+    """The condensing nozzle's configured run (400 cells, 20,000 steps to steady state): the
+    FP32 + surrogate liquid number density against the FP64 oracle, in total and cell by
+    cell (relative L1 over cells above 1e-6 of the maximum), within 2 %; the plain FP32 path
+    within 1e-3."""
     c = cases.nozzle_case(nx=400)
     o = O.Oracle(c)
     Uo = o.init_state()
-    o.step(Uo, 300, 0.5)
+    o.step(Uo, 20000, 0.5)
     res = {}
     for name, prec in (("fp32", P.CT_FP32), ("fp32_mlp", P.CT_FP32_MLP)):
         s = _solver(P, sur, c, None, prec)
-        s.step(300, 0.5)
-        assert s.diagnostics()[8] == 0
-        U = s.state64()
-        rho_err = np.max(np.abs(U[0] - Uo[0]) / Uo[0])
-        n_tot = (U[5] * 1).sum()
-        n_ref = Uo[5].sum()
-        y_ref = Uo[8].sum()
-        res[name] = (rho_err, abs(n_tot / n_ref - 1.0), abs(U[8].sum() / y_ref - 1.0))
-    print("nozzle 300 steps, errors vs FP64 oracle (rho max rel, liquid number total, liquid mass total):", res)
-    assert res["fp32"][0] < 1e-3 and res["fp32"][2] < 1e-2
-    assert res["fp32_mlp"][0] < 5e-2
+        s.step(20000, 0.5)
+        d = s.diagnostics()
+        assert d[8] == 0
+        res[name] = _number_errors(s.state64(), Uo, 5) + (d[26] / max(d[7], 1.0),)
+    print("nozzle, 20000 steps, liquid number vs the FP64 oracle (total, cell-wise L1, fallback share):", res)
+    assert res["fp32"][0] <= 1e-3 and res["fp32"][1] <= 1e-3
+    assert res["fp32_mlp"][0] <= 2e-2 and res["fp32_mlp"][1] <= 2e-2
+
+
+def test_surrogate_number_density_on_the_freezing_plume(P, sur):
+    """The freezing plume (evaporating droplets, homogeneous and immersion freezing, ice
+    growth), 100 steps: liquid and ice number density within 2 % of the FP64 oracle, in
+    total and cell by cell."""
+    c, uf = cases.freezing_case()
+    o = O.Oracle(c, uf)
+    Uo = o.init_state()
+    o.step(Uo, 100, 0.5)
+    s = _solver(P, sur, c, uf, P.CT_FP32_MLP)
+    s.step(100, 0.5)
+    d = s.diagnostics()
+    assert d[8] == 0 and d[7] > 100
+    U = s.state64()
+    for f, name in ((5, "liquid"), (9, "ice")):
+        tot, l1 = _number_errors(U, Uo, f)
+        print(f"freezing plume, 100 steps, {name} number vs the FP64 oracle: total {tot:.2e}, cell-wise L1 {l1:.2e}")
+        assert tot <= 2e-2 and l1 <= 2e-2, (name, tot, l1)
 
 
 def test_surrogate_gain_on_an_active_workload(P, sur):
     """What the network buys: step time of the FP32 path and of the FP32 + surrogate path on
-    a hydrogen-like mixing plume whose source fires in many cells, same state and steps."""
+    a hydrogen-like mixing plume whose source fires in about half of the cells, same state
+    and steps.  On GB300 the plain FP32 source (FP32 with FP64 islands) is cheaper than the
+    network's evaluation: the surrogate step takes about 1.5 times as long.  The test holds
+    the measured ratio to that finding (below 1.8) and prints it."""
     c, uf = cases.mixing_layer_case(nx=1024, nr=256)
     times = {}
     for name, prec in (("fp32", P.CT_FP32), ("fp32_mlp", P.CT_FP32_MLP)):
         s = _solver(P, sur, c, uf, prec)
+        s.autotune(reps=2)
         s.step(3, 0.5)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -117,6 +152,7 @@ def test_surrogate_gain_on_an_active_workload(P, sur):
         d = s.diagnostics()
         assert d[8] == 0
         times[name] = (e0.elapsed_time(e1) / 20, d[7] / (1024 * 256), d[26])
-    print("ms/step, active fraction, fallbacks:", times,
-          "speedup of the surrogate path:", times["fp32"][0] / times["fp32_mlp"][0])
-    assert times["fp32_mlp"][1] > 0.02
+    ratio = times["fp32_mlp"][0] / times["fp32"][0]
+    print("ms/step, active fraction, fallbacks:", times, "surrogate / plain FP32 step time:", ratio)
+    assert times["fp32_mlp"][1] > 0.3
+    assert ratio < 1.8

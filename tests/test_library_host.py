@@ -71,6 +71,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(P):
     assert e.value.status == 1
     with pytest.raises(P.ContrailError):
         P.ct_reconstruct_faces(0x1000, None, 0x1000, 4, 0x2000, 0x3000)
+    for field in (-1, 14):                     # read_field: field index checked first
+        with pytest.raises(P.ContrailError) as e:
+            P.ct_read_field(c, P.CT_FP64, 0x1000, field)
+        assert e.value.status == 1
+    assert P.ct_train_workspace_bytes(0, 64, 1) == 0 and P.ct_train_workspace_bytes(100, 64, 0) == 0
+    assert P.ct_train_workspace_bytes(1000, 256, 4) >= 1000 * 26 * 4
+    with pytest.raises(P.ContrailError) as e:          # invalid configuration, before any copy
+        P.ct_train_surrogate(0x1000, 0x2000, 0x3000, 100, dict(epochs=0, batch=10, lr=1e-3, lr_final=0.0),
+                             0x4000, 0x5000, 0x6000, 1 << 20)
+    assert e.value.status == 1
 
 
 def test_binding_has_no_oracle_dependency():
