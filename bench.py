@@ -104,7 +104,9 @@ def _workload(name):
 # reported only for a shape counted on the current kernel.
 FP64_FLOPS_PER_CELL_STAGE = 565.1
 FP64_TRAFFIC_PER_CELL_LAUNCH = {7: 452.0, 8: 392.8}    # 16 x 16 and 16 x 14, two CTAs per SM
-FP32_TRAFFIC_PER_CELL_LAUNCH = {5: 134.3}    # 32 x 8, three CTAs per SM
+FP32_TRAFFIC_PER_CELL_LAUNCH = {5: 134.3,    # 32 x 8, three CTAs per SM
+                                9: 142.0}    # the column sweep (28 x 64 strips), four CTAs per SM
+SWEEP_SHAPE = 9   # tile shape index of the column-sweep FP32 kernel (k_sweep)
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s, 16 x 14 tile:
 # 1135.9 and 1377.4 flops)
 FP64_VISC_FLOPS_PER_CELL_STAGE = 1256.7
@@ -311,7 +313,8 @@ def run_cuda(args):
                 "frac": round(bw / peaks["hbm_gbs"], 4),
                 "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH[shape] * cells
                             if shape in FP32_TRAFFIC_PER_CELL_LAUNCH and not c.get("bimodal") else None),
-                "kernel": "ct::k_stage<float>", "peak_source": peak_kind,
+                "kernel": "ct::k_sweep<float>" if shape == SWEEP_SHAPE else "ct::k_stage<float>",
+                "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*{nf}*4 per cell per launch (mean of the two stages); "
                         f"mean launch {launch_ms_ev:.4f} ms"}
     bytes_state = cells * nf * elem

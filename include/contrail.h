@@ -266,6 +266,7 @@ typedef struct {
   float beta1, beta2, eps;   /* Adam */
   uint64_t seed;       /* per-epoch shuffles: Fisher-Yates from splitmix64 */
   int tensor_cores;    /* 1: BF16 tcgen05 GEMMs with FP32 accumulation and FP32 master weights */
+  float out_weight[16];   /* weight of each output's squared error (first CT_MLP_OUT; >= 0, not all 0) */
 } ct_train_cfg;
 
 /* Bytes of device workspace ct_train_surrogate needs for n rows (0 for invalid sizes). */
@@ -273,7 +274,8 @@ size_t ct_train_workspace_bytes(int n, int batch, int epochs);
 
 /* Train the source surrogate (the paper has no network: it stands in for the rates of
  * Sec. 2.2) in one call: column statistics of X (inputs) and of Y over its mask M
- * (targets), standardisation, then epochs of shuffled mini-batches, the masked MSE and its
+ * (targets, 0 or 1), standardisation, then epochs of shuffled mini-batches, the masked MSE
+ * with the per-output weights of cfg and its
  * gradient (ct_mlp_loss_grad, or ct_mlp_loss_grad_tc with tensor_cores) and Adam with the
  * cosine learning-rate schedule.
  * X (n x CT_MLP_IN), Y and M (n x CT_MLP_OUT): device, raw units (ct_mlp_dataset).

@@ -50,7 +50,7 @@ class CtCase(C.Structure):
 class CtTrainCfg(C.Structure):
     _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("lr_final", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64),
-                ("tensor_cores", C.c_int)]
+                ("tensor_cores", C.c_int), ("out_weight", C.c_float * 16)]
 
 
 class ContrailError(RuntimeError):
@@ -408,6 +408,9 @@ def ct_train_surrogate(X, Y, M, n, cfg: dict, params, stats, work, work_bytes, s
                    lr_final=float(cfg["lr_final"]), beta1=float(cfg.get("beta1", 0.9)),
                    beta2=float(cfg.get("beta2", 0.999)), eps=float(cfg.get("eps", 1e-8)),
                    seed=int(cfg.get("seed", 0)), tensor_cores=int(cfg.get("tensor_cores", 0)))
+    w = list(cfg.get("out_weight", [1.0] * CT_MLP_OUT))
+    for q in range(16):
+        k.out_weight[q] = float(w[q]) if q < len(w) else 0.0
     hist = (C.c_float * k.epochs)()
     _check(_L().ct_train_surrogate(_ptr(X), _ptr(Y), _ptr(M), n, C.byref(k), _ptr(params), _ptr(stats), hist,
                                    _ptr(work), work_bytes, _stream(stream)))

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcontrail.so")
 SOURCES = ("contrail.cu", "stage_32x8.cu", "stage_16x16.cu", "stage_32x16.cu", "stage_64x8.cu",
            "stage_32x8_bi.cu", "stage_16x16_bi.cu", "stage_32x16_bi.cu", "stage_64x8_bi.cu",
-           "stage_16x16_o3.cu", "stage_32x8_o3.cu", "stage_16x12_d2.cu", "stage_16x16_d2.cu", "stage_16x14_d2.cu", "mlp.cu", "mlp_infer.cu")
+           "stage_16x16_o3.cu", "stage_32x8_o3.cu", "stage_16x12_d2.cu", "stage_16x16_d2.cu", "stage_16x14_d2.cu", "stage_sweep.cu", "mlp.cu", "mlp_infer.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -333,6 +333,7 @@ const StageSet* stage_set_32x8_o3();
 const StageSet* stage_set_16x12_d2();
 const StageSet* stage_set_16x16_d2();
 const StageSet* stage_set_16x14_d2();
+const StageSet* stage_set_sweep();
 const StageSet* stage_set(int shape) {
   switch (shape) {
     case 1: return stage_set_16x16();
@@ -343,6 +344,7 @@ const StageSet* stage_set(int shape) {
     case 6: return stage_set_16x12_d2();
     case 7: return stage_set_16x16_d2();
     case 8: return stage_set_16x14_d2();
+    case 9: return stage_set_sweep();
     default: return stage_set_32x8();
   }
 }
@@ -386,8 +388,11 @@ static int shape_for(const ct_case* c, int precision) {
   auto it = g_shape.find(shape_key(c, precision));
   return it == g_shape.end() ? 0 : it->second;
 }
-static bool shape_usable(int shape, int variant) {
-  return shape >= 0 && shape < NSHAPES && stage_set(shape)->stage[variant][0] != nullptr;
+static bool shape_usable(int shape, int variant, const ct_case* c) {
+  if (shape < 0 || shape >= NSHAPES) return false;
+  const StageSet* ss = stage_set(shape);
+  if (ss->plume_inviscid_only && (c->geom != 1 || c->viscous)) return false;
+  return ss->stage[variant][0] != nullptr;
 }
 
 static ct_status validate(const ct_case* c, int precision) {
@@ -687,7 +692,7 @@ static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U
                                cudaStream_t st, bool prims, const void* blob = nullptr, int shape = -1) {
   const int p = variant_of(c, precision);
   if (shape < 0) shape = shape_for(c, precision);
-  if (!shape_usable(shape, p)) shape = 0;
+  if (!shape_usable(shape, p, c)) shape = 0;
   ct_status s = set_stage_attrs(shape, p);
   if (s != CT_OK) return s;
   const StageSet* ss = stage_set(shape);
@@ -939,7 +944,8 @@ ct_status ct_set_tile_shape(const ct_case* c, int precision, int shape) {
     g_shape.erase(shape_key(c, precision));
     return CT_OK;
   }
-  if (!shape_usable(shape, variant_of(c, precision))) return fail(CT_ERR_ARG, "tile shape not available for this precision");
+  if (!shape_usable(shape, variant_of(c, precision), c))
+    return fail(CT_ERR_ARG, "tile shape not available for this precision or case");
   g_shape[shape_key(c, precision)] = shape;
   return CT_OK;
 }
@@ -957,7 +963,7 @@ ct_status ct_autotune(const ct_case* c, int precision, const void* U, void* U1, 
   float best_ms = 0.0f;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     float ms = -1.0f;
-    if (shape_usable(sh, p)) {
+    if (shape_usable(sh, p, c)) {
       if ((s = set_stage_attrs(sh, p)) != CT_OK) return s;
       const StageSet* ss = stage_set(sh);
       DevCase d = make_dev(c, work, sh, uses_prims(c, precision));

@@ -244,15 +244,22 @@ __global__ void k_silu_bwd(float* __restrict__ dH, const float* __restrict__ Z, 
   }
 }
 
-// masked MSE: dY = 2 m (yhat - y) / count, per-block partial sums of m (yhat - y)^2 and m
+// per-output weights of the squared errors (all 1: the plain masked MSE)
+struct OutW {
+  float w[CT_MLP_OUT];
+};
+
+// masked, weighted MSE: dY = 2 w_q m (yhat - y) / count, per-block partial sums of
+// w_q m (yhat - y)^2 and m (the mask m is 0 or 1; count = sum m)
 __global__ void k_mse(const float* __restrict__ Yh, const float* __restrict__ Y, const float* __restrict__ Mk, size_t n,
-                      float* __restrict__ dY, double* __restrict__ part) {
+                      OutW ow, float* __restrict__ dY, double* __restrict__ part) {
   __shared__ double s0[256], s1[256];
   double a = 0.0, c = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float wq = ow.w[i % CT_MLP_OUT];
     const float r = (Yh[i] - Y[i]) * Mk[i];
-    dY[i] = r;
-    a += (double)r * r;
+    dY[i] = wq * r;
+    a += (double)wq * ((double)r * r);
     c += Mk[i];
   }
   s0[threadIdx.x] = a;
@@ -474,14 +481,20 @@ static void forward(const float* P, const float* X, int n, const Work& w, cudaSt
   }
 }
 
+static OutW ones_w() {
+  OutW o;
+  for (int q = 0; q < CT_MLP_OUT; ++q) o.w[q] = 1.0f;
+  return o;
+}
+
 // Masked MSE and its gradient (forward, loss, backward through the five layers).
 static void loss_grad(const float* params, const float* X, const float* Y, const float* M, int n, float* grad,
-                      float* loss, const Work& w, cudaStream_t st) {
+                      float* loss, const Work& w, const OutW& ow, cudaStream_t st) {
   forward(params, X, n, w, st);
   // dL/dyhat into g0 (n x 10)
   const size_t ny = (size_t)n * CT_MLP_OUT;
   const int nb = (int)((ny + 255) / 256 < 256 ? (ny + 255) / 256 : 256);
-  k_mse<<<nb, 256, 0, st>>>(w.Z[NL - 1], Y, M, ny, w.g0, w.part);
+  k_mse<<<nb, 256, 0, st>>>(w.Z[NL - 1], Y, M, ny, ow, w.g0, w.part);
   k_mse_finish<<<nb, 256, 0, st>>>(w.part, nb, w.g0, ny, loss);
   float* g = w.g0;     // gradient wrt the current layer's output (pre-activation for the last)
   float* gn = w.g1;
@@ -522,11 +535,11 @@ static void forward_tc(const float* P, const float* X, int n, const Work& w, int
 }
 
 static void loss_grad_tc(const float* params, const float* X, const float* Y, const float* M, int n, float* grad,
-                         float* loss, const Work& w, int* err, cudaStream_t st) {
+                         float* loss, const Work& w, int* err, const OutW& ow, cudaStream_t st) {
   forward_tc(params, X, n, w, err, st);
   const size_t ny = (size_t)n * CT_MLP_OUT;
   const int nb = (int)((ny + 255) / 256 < 256 ? (ny + 255) / 256 : 256);
-  k_mse<<<nb, 256, 0, st>>>(w.Z[NL - 1], Y, M, ny, w.g0, w.part);
+  k_mse<<<nb, 256, 0, st>>>(w.Z[NL - 1], Y, M, ny, ow, w.g0, w.part);
   k_mse_finish<<<nb, 256, 0, st>>>(w.part, nb, w.g0, ny, loss);
   const int splits = n / 256 < 1 ? 1 : (n / 256 > TC_SPLIT_MAX ? TC_SPLIT_MAX : n / 256);
   float* g = w.g0;
@@ -577,7 +590,7 @@ ct_status ct_mlp_loss_grad(const float* params, const float* X, const float* Y, 
                            float* loss, void* work, size_t wbytes, void* stream) {
   if (!params || !X || !Y || !M || !grad || !work || n <= 0) return fail(CT_ERR_ARG, "ct_mlp_loss_grad: bad argument");
   if (wbytes < work_bytes(n)) return fail(CT_ERR_SIZE, "ct_mlp_loss_grad: work too small (ct_mlp_work_bytes)");
-  loss_grad(params, X, Y, M, n, grad, loss, carve((float*)work, n), (cudaStream_t)stream);
+  loss_grad(params, X, Y, M, n, grad, loss, carve((float*)work, n), ones_w(), (cudaStream_t)stream);
   return check("ct_mlp_loss_grad");
 }
 
@@ -586,7 +599,7 @@ ct_status ct_mlp_loss_grad_tc(const float* params, const float* X, const float* 
   if (!params || !X || !Y || !M || !grad || !err_flag || !work || n <= 0)
     return fail(CT_ERR_ARG, "ct_mlp_loss_grad_tc: bad argument");
   if (wbytes < work_bytes(n)) return fail(CT_ERR_SIZE, "ct_mlp_loss_grad_tc: work too small (ct_mlp_work_bytes)");
-  loss_grad_tc(params, X, Y, M, n, grad, loss, carve((float*)work, n), err_flag, (cudaStream_t)stream);
+  loss_grad_tc(params, X, Y, M, n, grad, loss, carve((float*)work, n), err_flag, ones_w(), (cudaStream_t)stream);
   return check("ct_mlp_loss_grad_tc");
 }
 
@@ -659,6 +672,14 @@ extern "C" ct_status ct_train_surrogate(const float* X, const float* Y, const fl
       !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) || !(cfg->eps > 0.0f))
     return fail(CT_ERR_ARG, "ct_train_surrogate: invalid configuration");
   if (cfg->tensor_cores != 0 && cfg->tensor_cores != 1) return fail(CT_ERR_ARG, "ct_train_surrogate: tensor_cores must be 0 or 1");
+  OutW ow;
+  float wsum = 0.0f;
+  for (int q = 0; q < CT_MLP_OUT; ++q) {
+    if (!(cfg->out_weight[q] >= 0.0f)) return fail(CT_ERR_ARG, "ct_train_surrogate: output weights must be >= 0");
+    ow.w[q] = cfg->out_weight[q];
+    wsum += ow.w[q];
+  }
+  if (!(wsum > 0.0f)) return fail(CT_ERR_ARG, "ct_train_surrogate: output weights all zero");
   if (wbytes < train_ws_bytes(n, cfg->batch, cfg->epochs))
     return fail(CT_ERR_SIZE, "ct_train_surrogate: workspace too small (ct_train_workspace_bytes)");
   cudaStream_t st = (cudaStream_t)stream;
@@ -721,8 +742,8 @@ extern "C" ct_status ct_train_surrogate(const float* X, const float* Y, const fl
       return check("ct_train_surrogate shuffle");
     for (int b = 0; b < nb; ++b) {
       k_gather_rows<<<ggrid, 256, 0, st>>>(perm_d + (size_t)b * rows, rows, Xn, Yn, M, xb, yb, mb);
-      if (cfg->tensor_cores) loss_grad_tc(params, xb, yb, mb, rows, G, loss, w, w.err, st);
-      else loss_grad(params, xb, yb, mb, rows, G, loss, w, st);
+      if (cfg->tensor_cores) loss_grad_tc(params, xb, yb, mb, rows, G, loss, w, w.err, ow, st);
+      else loss_grad(params, xb, yb, mb, rows, G, loss, w, ow, st);
       ++step;
       const double frac = (double)step / (double)total;
       const float lr_t = (float)(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + std::cos(M_PI * frac)));

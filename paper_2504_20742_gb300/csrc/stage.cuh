@@ -1276,6 +1276,7 @@ struct StageSet {
   const void* stage[NVARIANT][2];   // k_stage, stages 1 and 2
   const void* stage_sp[2];          // FP64 k_stage with the stored primitives (variant 0)
   const void* batch[NVARIANT][2];   // k_batch_stage (FP32 variants only)
+  bool plume_inviscid_only;         // kernels for axisymmetric cases without diffusive fluxes only
 };
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
 
@@ -1366,7 +1367,7 @@ StageSet make_stage_set_fp64() {
 }
 
 // the tile shapes the library is built with (one translation unit each)
-constexpr int NSHAPES = 9;
+constexpr int NSHAPES = 10;
 // 0: 32x8 (default), 1: 16x16, 2: 32x16, 3: 64x8, 4: 16x16 and 5: 32x8 with three FP32 CTAs
 // per SM, 6: 16x12, 7: 16x16 and 8: 16x14 with two FP64 CTAs per SM
 const StageSet* stage_set(int shape);

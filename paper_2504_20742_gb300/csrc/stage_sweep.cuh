@@ -1,0 +1,396 @@
+// stage_sweep.cuh -- the plain FP32 stage of an axisymmetric plume as column sweeps.
+//
+// The same SSP-RK2 stage as stage_tile (Sec. 3.2: MUSCL/van Leer, Roe fluxes, axisymmetric
+// source, phase-change source, RK combine, partials), organised for the instruction issue
+// of sm_103a instead of shared-memory staging.  A warp owns a strip of 28 cells in x (lanes
+// 2..29; lanes 0, 1, 30 and 31 carry the two-column halo) and sweeps R rows in r, one row
+// per iteration:
+//   - x direction inside the warp: neighbour values by shuffles, one x-face flux per lane;
+//   - r direction in registers: the row's primitive vector, the upper face state of the
+//     previous row's slope and the south-face flux stay in the thread from one row to the
+//     next, so every r face is reconstructed and fluxed once, with no shared memory and no
+//     barrier.
+// Every cell value is computed by the same expressions in the same order as in stage_tile,
+// so the state is bitwise that of the other tile shapes; only the summation order of the
+// FP64 totals differs (compensated FP32 sums per lane, FP64 from the warp on).  Variant:
+// FP32, axisymmetric, without the diffusive fluxes, one liquid set, plain source.
+#pragma once
+#include "stage.cuh"
+
+namespace ct {
+
+template <int W_, int R_, int MINB_>
+struct SweepTile {
+  static constexpr int W = W_, R = R_, MINB = MINB_;
+  static constexpr int TX = 28, TY = W * R, NT = 32 * W;
+};
+
+// Kahan-compensated FP32 running sum of one lane's cells
+struct KSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+template <class ST, int STAGE>
+__global__ void __launch_bounds__(ST::NT, ST::MINB)
+    k_sweep(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
+            const unsigned char* __restrict__ blob) {
+  using T = float;
+  using V = float2;
+  constexpr int NP = NF / 2;
+  constexpr int R = ST::R;
+  __shared__ double red[ST::W][NPART];
+  __shared__ double fin[NPART];
+  // per warp, per lane: the primitive vectors of three consecutive rows (a ring indexed by
+  // row mod 3), row j's upper r-face state, the flux of the face below row j, row j's x
+  // divergence, and (lane 0) the running residual maxima
+  __shared__ float2 s_q[ST::W][3][NP][32];
+  __shared__ float2 s_fhi[ST::W][NP][32], s_fs[ST::W][NP][32], s_acc[ST::W][NP][32];
+  __shared__ float s_rmax[ST::W][NF];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int by = blockIdx.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
+  const int nx = dc.nx, nr = dc.nr;
+  const size_t N = (size_t)nx * nr;
+  const int i0 = blockIdx.x * ST::TX;
+  const int i = i0 - 2 + lane;                       // this lane's column
+  const int jb = by * ST::TY + warp * R;             // the warp's first row
+  const int je = min(jb + R, nr);                    // one past its last row
+  const double dtd = dc.hdr->dt_cur;
+  const T dt = T(dtd);
+  const Geo<T> g = geo_of(dc, T(0));
+  const bool xin = i >= 0 && i < nx;
+  const bool cell_col = lane >= 2 && lane < 30 && i < nx;   // the lane owns cells of this column
+  const bool wall = g.wall_len > T(0) && (T(i) + T(0.5)) * g.dx < g.wall_len;
+  const bool edge = i0 == 0 || i0 + ST::TX >= nx;           // the strip touches x = 0 or x = L_x
+  const int lm = lane > 0 ? lane - 1 : 0, lp = lane < 31 ? lane + 1 : 31;
+  const auto slot = [](int j) { return (j + 3) % 3; };   // j >= -2
+
+  // primitive vector (stage_tile's phase A) of cell (i, j) of the stencil; zero where no
+  // cell of the strip needs it (corners, columns beyond the halo)
+  const auto load_q = [&](int j, V* q) {
+    const bool rin = j >= 0 && j < nr;
+    if ((xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1) {
+      T u14[NF];
+      if (xin && rin) {
+        const size_t n = (size_t)j * nx + i;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+      } else {
+        load_ghost<T, NF>(dc, Uin, N, i, j, u14);
+      }
+      Prim<T> w;
+      cons_to_prim<T, false>(u14, w);
+      T qv[NF];
+      prim_vector<T, false>(w, qv);
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) q[k2] = p_make(qv[2 * k2], qv[2 * k2 + 1]);
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) q[k2] = p_make(T(0), T(0));
+    }
+  };
+
+  // running partials of this lane's cells
+  KSum sM, sW, sE;
+  T bm = T(0), bw = T(0), be = T(0);
+  T dtmin = T(INFINITY);
+  T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
+  int nactive = 0, nbad = 0;
+  if (lane < NF) s_rmax[warp][lane] = T(0);
+
+  if (jb < je) {
+    // rows jb-2 .. jb+1: the upper face state of row jb-1, row jb's lower face state, and the
+    // flux of the face between rows jb-1 and jb; rows jb-1 .. jb+1 stay in the ring
+    {
+      V qm[NP], q0[NP], q1[NP], q2[NP];
+      load_q(jb - 2, qm);
+      load_q(jb - 1, q0);
+      load_q(jb, q1);
+      load_q(jb + 1, q2);
+      T qL[NF], qR[NF], F[NF];
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) {
+        V lo, hi;
+        vl_faces2(qm[k2], q0[k2], q1[k2], lo, hi);     // row jb-1
+        qL[2 * k2] = hi.x;
+        qL[2 * k2 + 1] = hi.y;
+        vl_faces2(q0[k2], q1[k2], q2[k2], lo, hi);     // row jb
+        qR[2 * k2] = lo.x;
+        qR[2 * k2 + 1] = lo.y;
+        s_fhi[warp][k2][lane] = hi;
+        s_q[warp][slot(jb - 1)][k2][lane] = q0[k2];
+        s_q[warp][slot(jb)][k2][lane] = q1[k2];
+        s_q[warp][slot(jb + 1)][k2][lane] = q2[k2];
+      }
+      roe_flux<T, 1, NF>(qL, qR, F);
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) s_fs[warp][k2][lane] = p_make(F[2 * k2], F[2 * k2 + 1]);
+    }
+    __syncwarp();
+    // invariant at the top of iteration j: rows j-1, j, j+1 in the ring; row j's upper face
+    // state and the flux of the face between rows j-1 and j in shared memory
+    for (int j = jb; j < je; ++j) {
+      const int sj = slot(j), sj1 = slot(j + 1), sj2 = slot(j + 2);
+      // x direction, row j: slopes from the neighbours' values, the face i+1/2 per lane,
+      // the divergence from the west neighbour's face
+      {
+        T qL[NF], qR[NF], F[NF];
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          V lo, hi;
+          vl_faces2(s_q[warp][sj][k2][lm], s_q[warp][sj][k2][lane], s_q[warp][sj][k2][lp], lo, hi);
+          const V r = shfl_down2(lo);
+          qL[2 * k2] = hi.x;
+          qL[2 * k2 + 1] = hi.y;
+          qR[2 * k2] = r.x;
+          qR[2 * k2 + 1] = r.y;
+        }
+        roe_flux<T, 0, NF>(qL, qR, F);
+        const V cw2 = p_make(g.idx, g.idx), nce2 = p_make(-g.idx, -g.idx);
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const V fe = p_make(F[2 * k2], F[2 * k2 + 1]);
+          s_acc[warp][k2][lane] = p_fma(cw2, shfl_up2(fe), p_mul(nce2, fe));
+        }
+        if (edge) {   // boundary inflow rates of the inflow and outflow columns
+          const T area = (T(j) + T(0.5)) * g.dr * g.dr;
+          const T w0 = __shfl_up_sync(0xffffffffu, F[0], 1), w3 = __shfl_up_sync(0xffffffffu, F[3], 1);
+          const T w4 = __shfl_up_sync(0xffffffffu, F[4], 1), w8 = __shfl_up_sync(0xffffffffu, F[8], 1);
+          const T w12 = __shfl_up_sync(0xffffffffu, F[12], 1);
+          if (cell_col) {
+            if (i == 0) {
+              bm += area * w0;
+              bw += area * (w4 + T(k::YL3) * w8 + T(k::YS3) * w12);
+              be += area * w3;
+            }
+            if (i == nx - 1) {
+              bm -= area * F[0];
+              bw -= area * (F[4] + T(k::YL3) * F[8] + T(k::YS3) * F[12]);
+              be -= area * F[3];
+            }
+          }
+        }
+      }
+      // r direction: row j+2 into the ring (over row j-1), row j+1's slope, face j+1/2
+      V Fn[NP];
+      {
+        V qc[NP];
+        load_q(j + 2, qc);
+        T qL[NF], qR[NF], F[NF];
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          V lo, hi;
+          vl_faces2(s_q[warp][sj][k2][lane], s_q[warp][sj1][k2][lane], qc[k2], lo, hi);
+          const V fl = s_fhi[warp][k2][lane];
+          qL[2 * k2] = fl.x;
+          qL[2 * k2 + 1] = fl.y;
+          qR[2 * k2] = lo.x;
+          qR[2 * k2 + 1] = lo.y;
+          s_fhi[warp][k2][lane] = hi;   // row j+1's upper face state, for the next iteration
+        }
+        __syncwarp();                   // every lane has read row j's values above
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) s_q[warp][sj2][k2][lane] = qc[k2];
+        roe_flux<T, 1, NF>(qL, qR, F);
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) Fn[k2] = p_make(F[2 * k2], F[2 * k2 + 1]);
+      }
+      // cell (i, j): r divergence, sources, RK combine, partials (stage_tile's phase E)
+      T rf[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) rf[f] = T(0);
+      if (cell_col) {
+        const size_t n = (size_t)j * nx + i;
+        T u14[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+        Prim<T> w;
+        cons_to_prim<T, false>(u14, w);
+        T acc[NF];
+        const T ijh = trcp(T(j) + T(0.5));
+        const T cs = T(j) * ijh * g.idr;
+        const T cn = T(j + 1) * ijh * g.idr;
+        const bool wall_s = wall && j == dc.jw, wall_n = wall && j == dc.jw - 1;
+        {
+          const V cs2 = p_make(cs, cs), ncn2 = p_make(-cn, -cn);
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            V fs = s_fs[warp][k2][lane], fn = Fn[k2];
+            if (wall_n) fn = p_make(k2 == 1 ? w.p : T(0), T(0));
+            if (wall_s) fs = p_make(k2 == 1 ? w.p : T(0), T(0));
+            const V a = p_add(s_acc[warp][k2][lane], p_fma(cs2, fs, p_mul(ncn2, fn)));
+            acc[2 * k2] = a.x;
+            acc[2 * k2 + 1] = a.y;
+          }
+        }
+        acc[2] += w.p * ijh * g.idr;
+        if (j == nr - 1) {
+          const T An = T(nr) * g.dr * g.dx;
+          bm -= An * Fn[0].x;
+          bw -= An * (Fn[2].x + T(k::YL3) * Fn[4].x + T(k::YS3) * Fn[6].x);
+          be -= An * Fn[1].y;
+        }
+        {
+          T Q[NF];
+          double lnJ2[2];
+          if (phase_source<T, false>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr)) {
+            nactive += 1;
+            lnJh = fmaxf(lnJh, T(lnJ2[0]));
+            lnJt = fmaxf(lnJt, T(lnJ2[1]));
+#pragma unroll
+            for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+          }
+        }
+        T out[NF];
+        const V dt2 = p_make(dt, dt);
+        if (STAGE == 1) {
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+            out[2 * k2] = o.x;
+            out[2 * k2 + 1] = o.y;
+          }
+        } else {
+          const V half2 = p_make(T(0.5), T(0.5));
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            const V un2 = p_make(Un[(2 * k2) * N + n], Un[(2 * k2 + 1) * N + n]);
+            const V t = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+            const V o = p_fma(half2, un2, p_mul(half2, t));
+            out[2 * k2] = o.x;
+            out[2 * k2 + 1] = o.y;
+            rf[2 * k2] = m_fabs(o.x - un2.x);
+            rf[2 * k2 + 1] = m_fabs(o.y - un2.y);
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          Uout[f * N + n] = out[f];
+          nbad += finite_bits(out[f]) ? 0 : 1;
+        }
+        if (STAGE == 2) {
+          Prim<T> wn;
+          cons_to_prim<T, false>(out, wn);
+          const T cdt = cell_dt<T>(dc, g, wn);
+          dtmin = cdt < dtmin ? cdt : dtmin;
+          const T vol = (T(j) + T(0.5)) * g.dr * g.dr * g.dx;
+          sM.add(vol * out[0]);
+          sW.add(vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]));
+          sE.add(vol * out[3]);
+        }
+      }
+      if (STAGE == 2) {   // residual maxima of the row: one warp reduction per field
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const T m = warp_max_nonneg(rf[f]);
+          if (lane == 0) s_rmax[warp][f] = m > s_rmax[warp][f] ? m : s_rmax[warp][f];
+        }
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < NP; ++k2) s_fs[warp][k2][lane] = Fn[k2];
+      __syncwarp();
+    }
+  }
+
+  // warp partials in FP64 (one conversion per lane), CTA record in a fixed order
+  {
+    const double b0 = warp_sum(double(bm)), b1 = warp_sum(double(bw)), b2 = warp_sum(double(be));
+    if (lane == 0) {
+      for (int q = 0; q < NPART; ++q) red[warp][q] = 0.0;
+      red[warp][4] = b0;
+      red[warp][5] = b1;
+      red[warp][6] = b2;
+    }
+    if (STAGE == 2) {
+      const double m = warp_sum(double(sM.s) - double(sM.c));
+      const double wt = warp_sum(double(sW.s) - double(sW.c));
+      const double e = warp_sum(double(sE.s) - double(sE.c));
+      const T dmin = warp_min_nonneg(dtmin);
+      const int na = warp_count(nactive), nb = warp_count(nbad);
+      const T jh = warp_max_any(lnJh), jt = warp_max_any(lnJt);
+      if (lane == 0) {
+        red[warp][0] = double(dmin);
+        red[warp][1] = m;
+        red[warp][2] = wt;
+        red[warp][3] = e;
+        red[warp][7] = double(na);
+        red[warp][8] = double(nb);
+        // residual max-norms |dU|/dt: the maximum scaled once (rounding is monotone)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) red[warp][9 + f] = double(s_rmax[warp][f] * trcp(dt));
+        red[warp][23] = double(jh);
+        red[warp][24] = double(jt);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NPART) {
+    const int q = threadIdx.x, kind = slot_kind(q);
+    double a = red[0][q];
+    for (int w2 = 1; w2 < ST::W; ++w2) {
+      const double v = red[w2][q];
+      a = kind == 0 ? a + v : (kind == 1 ? (v > a ? v : a) : (v < a ? v : a));
+    }
+    dc.partials[(size_t)tile * NPART + q] = a;
+  }
+  if (!tile_reduce(dc, by, fin)) return;
+  if (threadIdx.x == 0) {
+    WsHeader* h = dc.hdr;
+    if (STAGE == 1) {
+      h->b1[0] = fin[4];
+      h->b1[1] = fin[5];
+      h->b1[2] = fin[6];
+      h->b1[3] = fin[26];
+    } else {
+      double* d = h->diag;
+      d[0] = dtd;
+      d[1] = fin[1];
+      d[2] = fin[2];
+      d[3] = fin[3];
+      d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
+      d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
+      d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
+      d[7] = fin[7];
+      d[8] = fin[8];
+      for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
+      d[23] = fin[23] * (1.0 / 2.302585092994045684);
+      d[24] = fin[24] * (1.0 / 2.302585092994045684);
+      const double dtn = dc.cfl * fin[0];
+      d[25] = dtn;
+      d[26] = fin[25];
+      h->steps += 1.0;
+      d[27] = h->steps;
+      d[28] = h->b1[3] + fin[26];
+      h->dt_cur = dtn;
+    }
+  }
+}
+
+template <class ST>
+StageSet make_stage_set_sweep() {
+  StageSet s;
+  memset(&s, 0, sizeof(s));
+  s.tx = ST::TX;
+  s.ty = ST::TY;
+  s.nt = ST::NT;
+  s.smem[1] = 0;
+  s.minb[1] = ST::MINB;
+  s.stage[1][0] = (const void*)k_sweep<ST, 1>;
+  s.stage[1][1] = (const void*)k_sweep<ST, 2>;
+  s.plume_inviscid_only = true;
+  return s;
+}
+
+}  // namespace ct

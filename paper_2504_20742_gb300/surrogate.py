@@ -125,7 +125,7 @@ class Surrogate:
 
 def train(X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int = 20, batch: int = 8192,
           lr: float = 2e-3, seed: int = 0, lr_final: float = 5e-5, tensor_cores: bool = False,
-          verbose: bool = False) -> Surrogate:
+          out_weight=None, verbose: bool = False) -> Surrogate:
     """Adam on the masked MSE of standardised targets with a cosine learning-rate decay, run
     entirely by the library (ct_train_surrogate: statistics, standardisation, shuffles,
     batches, gradients and Adam); this wrapper allocates the device buffers."""
@@ -135,7 +135,8 @@ def train(X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int = 20, b
     stats = torch.zeros(4 * L.CT_MLP_IN + 4 * L.CT_MLP_OUT, dtype=torch.float32, device=dev)
     wb = L.ct_train_workspace_bytes(n, batch, epochs)
     work = torch.empty(wb // 4 + 64, dtype=torch.float32, device=dev)
-    cfg = dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, seed=seed, tensor_cores=int(tensor_cores))
+    cfg = dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, seed=seed, tensor_cores=int(tensor_cores),
+               out_weight=list(out_weight) if out_weight is not None else [1.0] * L.CT_MLP_OUT)
     hist = L.ct_train_surrogate(X.contiguous(), Y.contiguous(), M.contiguous(), n, cfg, P, stats, work, wb,
                                 torch.cuda.current_stream(dev))
     if verbose:

@@ -96,7 +96,7 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     ctas = [P.ct_tile_shape_ctas(s, P.CT_FP32) for s in range(n)]
     ctas64 = [P.ct_tile_shape_ctas(s, P.CT_FP64) for s in range(n)]
     assert shapes[0] == (32, 8) and len(set(zip(shapes, ctas, ctas64))) == n
-    assert set(ctas) == {0, 1, 2, 3} and set(ctas64) == {0, 1, 2} and P.ct_tile_shape_ctas(n, P.CT_FP32) == 0
+    assert set(ctas) == {0, 1, 2, 3, 4} and set(ctas64) == {0, 1, 2} and P.ct_tile_shape_ctas(n, P.CT_FP32) == 0
     assert P.ct_tile_shape_ctas(0, 7) == 0
     c, _ = cases.plume_case(nx=64, nr=16)
     # a shape takes a precision exactly when it has kernels for it
@@ -124,6 +124,15 @@ def test_tile_shapes_and_registry_without_a_gpu(P):
     for prec in (P.CT_FP64, P.CT_FP32_MLP):
         with pytest.raises(P.ContrailError):
             P.ct_set_tile_shape(c, prec, k3)
+    # the column-sweep shape (28-cell strips): plain FP32 axisymmetric cases without the
+    # diffusive fluxes only
+    ks = shapes.index((28, 64))
+    assert ctas[ks] == 4 and ctas64[ks] == 0
+    P.ct_set_tile_shape(c, P.CT_FP32, ks)
+    P.ct_set_tile_shape(c, P.CT_FP32, -1)
+    for bad in (dict(c, viscous=1, nu_t=0.1), cases.nozzle_case(nx=64), dict(c, bimodal=1)):
+        with pytest.raises(P.ContrailError):
+            P.ct_set_tile_shape(bad, P.CT_FP32, ks)
     # the workspace holds the partials of the shape with the most tiles
     ragged, _ = cases.plume_case(nx=40, nr=24)
     tiles = max(-(-40 // tx) * -(-24 // ty) for tx, ty in shapes)
