@@ -303,6 +303,9 @@ def run_cuda(args):
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (FP64 has no entry in MEASURED_PEAKS.json)",
                 "note": f"{per_cell} FP64 flops per cell-stage executed (a DFMA counts 2, a DADD or DMUL 1; "
                         "the FP64 pipe was 76-78 % busy on the plume in the ncu capture, profiles/); "
+                        "the peak is cuBLAS DGEMM timed in this run; traffic (DRAM bytes of the ncu capture) "
+                        "exceeds the 280 algorithmic bytes per cell-launch because the kernel reads and "
+                        "writes the stored primitive planes on purpose (DRAM 2-3 % busy); "
                         f"mean launch {launch_ms_ev:.4f} ms"
                         + ("; figure of the dormant plume, a lower bound where the source fires"
                            if args.workload.startswith("active") else "")}
@@ -341,6 +344,8 @@ def run_cuda(args):
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(c, uf, args.cpu_seconds)
+    if args.workload == "fp64" and world == 1 and not args.no_surrogate:
+        line["surrogate"] = surrogate_record(dev)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
