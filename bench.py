@@ -385,13 +385,16 @@ def surrogate_record(dev, steps=20, err_steps=10):
             if ref is None:
                 ref = U
             else:
-                e = []
-                mom = max(np.abs(ref[1]).max(), np.abs(ref[2]).max())
-                for f in range(14):
-                    m = np.abs(ref[f]).max() if f != 2 else mom
-                    e.append(0.0 if m == 0 else float(np.max(np.abs(U[f] - ref[f]) / (np.abs(ref[f]) + 1e-3 * m))))
-                errs[name] = {"max_over_fields": round(max(e), 6), "rho": round(e[0], 8), "rho_E": round(e[3], 8),
-                              "liquid_number": round(e[5], 6), "ice_number": round(e[9], 6)}
+                # domain totals (cell-level fields of a nucleating mixing layer are chaotic:
+                # whether a marginal cell nucleates within the first steps differs between
+                # any two implementations), and the bulk fields cell by cell
+                def tot(f):
+                    return round(float(abs(U[f].sum() / ref[f].sum() - 1.0)), 8) if ref[f].sum() != 0 else None
+                def cell(f):
+                    return round(float(np.max(np.abs(U[f] - ref[f]) / (np.abs(ref[f]) + 1e-3 * np.abs(ref[f]).max()))), 8)
+                errs[name] = {"total_liquid_number": tot(5), "total_ice_number": tot(9),
+                              "total_liquid_mass": tot(8), "total_ice_mass": tot(12), "total_vapour": tot(4),
+                              "cell_rho": cell(0), "cell_rho_E": cell(3)}
             s.step(3, 0.5)
             stream.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -409,9 +412,29 @@ def surrogate_record(dev, steps=20, err_steps=10):
             torch.cuda.empty_cache()
     out["err_vs_fp64_after_steps"] = err_steps
     out["err_vs_fp64"] = errs
+    # the stated error: the condensing nozzle's configured run (400 cells, 20,000 steps to
+    # steady state), FP32 + surrogate against the FP64 path (itself held to the oracle at
+    # 1e-9), liquid number in total and cell by cell
+    cn = cases.nozzle_case(nx=400)
+    nz = {}
+    for name, prec in (("fp64", P.CT_FP64), ("fp32_mlp", P.CT_FP32_MLP)):
+        with torch.cuda.stream(stream):
+            s = P.Solver(cn, None, precision=prec, device=dev, stream=stream)
+            s.init_state(0.5)
+            if prec == P.CT_FP32_MLP:
+                s.attach_surrogate(blob)
+            s.step(20000, 0.5)
+            nz[name] = s.state64()[5].ravel()
+    ref5, got5 = nz["fp64"], nz["fp32_mlp"]
+    m = ref5 > 1e-6 * ref5.max()
+    out["nozzle_steady_state"] = {
+        "steps": 20000, "liquid_number_total": round(float(abs(got5.sum() / ref5.sum() - 1.0)), 6),
+        "liquid_number_cell_l1": round(float(np.abs(got5[m] - ref5[m]).sum() / np.abs(ref5[m]).sum()), 6),
+        "target": 0.02}
     out["speedup_fp32_mlp_over_fp64"] = round(out["fp64"]["ms_per_step"] / out["fp32_mlp"]["ms_per_step"], 3)
     out["speedup_fp32_mlp_over_fp32"] = round(out["fp32"]["ms_per_step"] / out["fp32_mlp"]["ms_per_step"], 3)
-    out["error_metric"] = "max over cells of |x - x_fp64| / (|x_fp64| + 1e-3 max|x_fp64|), per field"
+    out["error_metric"] = ("total_*: |sum x / sum x_fp64 - 1| over the domain; cell_*: max over cells of "
+                           "|x - x_fp64| / (|x_fp64| + 1e-3 max|x_fp64|)")
     return out
 
 
