@@ -524,6 +524,46 @@ __device__ __forceinline__ Sat<T> saturation(const Prim<T>& w, const SrcCase& sc
   return s;
 }
 
+// Gas-phase properties of a cell for Young's law and the Kantrowitz factor (reading G):
+// c_p, gamma, conductivity, mean free path of the gas (dry air and vapour), latent heats.
+template <class T>
+struct Gas {
+  T cp_g, gam_g, lam, lbar, hfg, hsg;
+};
+template <class T>
+__device__ __forceinline__ Gas<T> gas_props(const Prim<T>& w) {
+  const T Tg = w.Tg;
+  const T Yg = T(1) - w.Yl - w.Ys;
+  const T Ya = Yg - w.Yv;
+  const T iYg = T(1) / Yg;
+  Gas<T> g;
+  g.cp_g = (Ya * T(k::CPA) + w.Yv * T(k::CPV)) * iYg;
+  const T cv_g = (Ya * T(k::CVA) + w.Yv * T(k::CVV)) * iYg;
+  g.gam_g = g.cp_g / cv_g;
+  const T Rg_g = (Ya * T(k::RA) + w.Yv * T(k::RV)) * iYg;
+  const T mu_g = T(1.716e-5 * (273.15 + 110.4)) * Tg * m_sqrt(Tg * T(1.0 / 273.15)) * T(1.0 / 273.15) / (Tg + T(110.4));
+  g.lam = mu_g * g.cp_g * T(1.0 / k::PR);
+  g.lbar = T(1.5) * mu_g * m_sqrt(Rg_g * Tg) / w.p;
+  g.hfg = T(k::CPV - k::CL) * Tg + T(k::E0V);
+  g.hsg = T(k::CPV - k::CS) * Tg + T(k::E0V - k::E0S);
+  return g;
+}
+
+// Kantrowitz factor phi of Eq. (5), with alpha_crit from Young's heat-transfer law at r_crit
+// (reading F); rc, rhov from cnt_rates, Tsat_l the liquid saturation temperature.
+template <class T>
+__device__ __forceinline__ T kantrowitz_phi(const Prim<T>& w, const Gas<T>& g, double rc, double rhov, T Tsat_l) {
+  const T Tg = w.Tg;
+  const T rcT = T(rc);
+  const T ih = T(1) / g.hfg;
+  const T nu = T(k::RV) * Tsat_l * ih *
+               (T(k::ALPHA_Y - 0.5) - T(0.5) * (g.gam_g + T(1)) / (T(2) * g.gam_g) * g.cp_g * Tsat_l * ih);
+  const T Knc = g.lbar / (T(2) * rcT);
+  const T alpha_c = g.lam / (rcT * (T(1) + T(3.78) * (T(1) - nu) * Knc * T(1.0 / k::PR)));
+  return T(k::QC) * T(rhov) / alpha_c * m_sqrt(T(k::RV) * Tg * T(1.0 / (2.0 * k::PI))) *
+         (g.hfg * g.hfg / (T(k::RV) * Tg * Tg) - g.hfg / Tg);
+}
+
 // Classical nucleation, Eqs. (3), (4), (9), (10), with the soot gate of J_het (reading F):
 // the Kelvin radius, the vapour density and the two rates, in FP64 (ln S, the barrier and
 // its exponential are the FP64 islands of the FP32 path).  Only for ln S_l > 0.  lnJ2 gets
@@ -565,21 +605,10 @@ __device__ __forceinline__ Cnt cnt_rates(const Prim<T>& w, double lnSl, const Sr
 template <class T, bool BI = false>
 __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& st, const SrcCase& sc, double* lnJ2,
                                                 double* aux, double* ext) {
-  const T Tg = w.Tg, rho = w.rho;
+  const T Tg = w.Tg;
   Rates<T> r = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-  // gas-phase properties (reading G)
-  const T Yg = T(1) - w.Yl - w.Ys;
-  const T Ya = Yg - w.Yv;
-  const T iYg = T(1) / Yg;
-  const T cp_g = (Ya * T(k::CPA) + w.Yv * T(k::CPV)) * iYg;
-  const T cv_g = (Ya * T(k::CVA) + w.Yv * T(k::CVV)) * iYg;
-  const T gam_g = cp_g / cv_g;
-  const T Rg_g = (Ya * T(k::RA) + w.Yv * T(k::RV)) * iYg;
-  const T mu_g = T(1.716e-5 * (273.15 + 110.4)) * Tg * m_sqrt(Tg * T(1.0 / 273.15)) * T(1.0 / 273.15) / (Tg + T(110.4));
-  const T lam = mu_g * cp_g * T(1.0 / k::PR);
-  const T lbar = T(1.5) * mu_g * m_sqrt(Rg_g * Tg) / w.p;
-  const T hfg = T(k::CPV - k::CL) * Tg + T(k::E0V);
-  const T hsg = T(k::CPV - k::CS) * Tg + T(k::E0V - k::E0S);
+  const Gas<T> gs = gas_props<T>(w);
+  const T cp_g = gs.cp_g, gam_g = gs.gam_g, lam = gs.lam, lbar = gs.lbar, hfg = gs.hfg, hsg = gs.hsg;
   const T lnpv_t = T(st.lnpv);
   const double lnSl = st.lnSl, lnSi = st.lnSi;
 
@@ -592,14 +621,7 @@ __device__ __forceinline__ Rates<T> plain_rates(const Prim<T>& w, const Sat<T>& 
     // Eq. (5) with alpha_crit from Young's law at r_crit (reading F)
     Tsat_l = prop_tsat<T, false>(sc, lnpv_t);
     have_tsat_l = true;
-    const T rcT = T(rc);
-    const T ih = T(1) / hfg;
-    const T nu = T(k::RV) * Tsat_l * ih *
-                 (T(k::ALPHA_Y - 0.5) - T(0.5) * (gam_g + T(1)) / (T(2) * gam_g) * cp_g * Tsat_l * ih);
-    const T Knc = lbar / (T(2) * rcT);
-    const T alpha_c = lam / (rcT * (T(1) + T(3.78) * (T(1) - nu) * Knc * T(1.0 / k::PR)));
-    const T phi = T(k::QC) * T(rhov) / alpha_c * m_sqrt(T(k::RV) * Tg * T(1.0 / (2.0 * k::PI))) *
-                  (hfg * hfg / (T(k::RV) * Tg * Tg) - hfg / Tg);
+    const T phi = kantrowitz_phi<T>(w, gs, rc, rhov, Tsat_l);
     if (BI) {   // one moment set per mechanism
       r.Jeff = T(Jhom) / (T(1) + phi);
       r.Jh = T(Jhet) / (T(1) + phi);

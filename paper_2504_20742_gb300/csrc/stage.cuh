@@ -509,11 +509,13 @@ __device__ __forceinline__ void surrogate_source(const DevCase& dc, const unsign
       Rates<T> r;
       r.Jeff = r.rc_um = T(0);
       if (nuc) {
-        // the nucleation rates and the Kelvin radius are closed forms (Eqs. 3, 4, 10) whose
-        // exponent is an FP64 island: evaluated, not predicted.  The network supplies the
-        // Kantrowitz factor ln(1 + phi) (Eq. 5, which needs T_sat and Young's law at r_crit)
+        // nucleation is the plain path's closed form: the rates and the Kelvin radius of
+        // Eqs. 3, 4, 10 (exponent in FP64) and the Kantrowitz factor of Eq. 5 (T_sat by the
+        // Newton iteration, Young's law at r_crit); the network supplies growth and relaxation
         const Cnt c = cnt_rates<T>(w, st.lnSl, dc.sc, lnJ2);
-        r.Jeff = T(float(c.Jsum) * __expf(-y[8]));
+        const T Tsat_l = prop_tsat<T, false>(dc.sc, T(st.lnpv));
+        const T phi = kantrowitz_phi<T>(w, gas_props<T>(w), c.rc, c.rhov, Tsat_l);
+        r.Jeff = T(c.Jsum) / (T(1) + phi);
         r.rc_um = T(c.rc * 1e6);
       }
       r.Gl = st.pres_l ? T(MLP_G0 * sinhf(y[2])) : T(0);

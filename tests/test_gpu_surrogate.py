@@ -61,11 +61,11 @@ def _visited(P):
 
 def test_surrogate_rates_on_visited_states(P, sur):
     """The rates the FP32 + surrogate step takes on states visited by FP64 runs of the nozzle
-    and a hydrogen-like mixing layer.  Nucleation: J_hom and J_het (Eqs. 4, 10) are closed
-    forms evaluated in the step (their exponent in FP64), so log10 J is exact; the effective
-    rate J/(1 + phi) carries the network's Kantrowitz factor, whose error in log10 stays
-    within 0.25 everywhere with J >= 1 m^-3 s^-1 and within 0.02 for 99 % of those states.
-    Growth and relaxation rates: the network's errors are reported."""
+    and a hydrogen-like mixing layer.  Nucleation is the plain path's closed form (Eqs. 3-5,
+    10: the rates, the Kelvin radius and the Kantrowitz factor), so log10 J is exact; the
+    network supplies the growth rates asinh(G / 1 um/s) and the logs of the stage relaxation
+    rates.  The shipped network's errors on these states: 0.08-0.18 on average (8-18 %), up to
+    0.5 for 90 % of them; the test holds them there (mean 0.2, p90 0.55) and prints them."""
     X, Y, M = _visited(P)
     blob = sur.blob()
     Yp = torch.empty_like(Y)
@@ -73,16 +73,12 @@ def test_surrogate_rates_on_visited_states(P, sur):
     P.ct_mlp_infer(blob, X.contiguous(), X.shape[0], Yp, err)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    m = (M[:, 8] > 0) & (Y[:, 6] >= 0)
-    assert int(m.sum()) > 1000
-    e10 = ((Yp[m, 8] - Y[m, 8]).abs() / np.log(10.0)).cpu().numpy()
-    print(f"log10 J/(1+phi) error where J >= 1: max {e10.max():.3f}, p99 {np.quantile(e10, 0.99):.4f}, "
-          f"mean {e10.mean():.4f}, n {e10.size}")
     for q, name in ((2, "asinh G_l"), (3, "asinh G_s"), (4, "ln 1/tau_l"), (5, "ln 1/tau_s")):
         mm = M[:, q] > 0
+        assert int(mm.sum()) > 1000
         d = (Yp[mm, q] - Y[mm, q]).abs().cpu().numpy()
-        print(f"{name}: mean |error| {d.mean():.3f}, p90 {np.quantile(d, 0.9):.3f}, n {d.size}")
-    assert e10.max() <= 0.25 and np.quantile(e10, 0.99) <= 0.02
+        print(f"{name}: mean |error| {d.mean():.3f}, p90 {np.quantile(d, 0.9):.3f}, max {d.max():.2f}, n {d.size}")
+        assert d.mean() <= 0.2 and np.quantile(d, 0.9) <= 0.55, name
 
 
 def _number_errors(U, Uo, f):
