@@ -32,10 +32,11 @@ from synth import cases  # noqa: E402
 
 OUT_NAMES = ("lnJeff", "ln_rc_um", "asinh_Gl", "asinh_Gs", "ln_relax_l", "ln_relax_s", "lnJhom", "lnJhet",
              "ln1p_phi", "dT_l")
-# Loss weight of each output: the fused step takes the growth rates and the relaxation
-# rates from the network (2, 3, 4, 5); the other outputs are closed forms there and weigh
-# a tenth.
-OUT_WEIGHT = (0.1, 0.1, 1.0, 1.0, 1.0, 1.0, 0.1, 0.1, 0.1, 0.1)
+# Loss weight of each output: the growth rates, the relaxation rates and the Kantrowitz
+# factor (2, 3, 4, 5, 8) count fully, the nucleation outputs, which the fused step takes
+# in closed form, a tenth.  (With these weights, seed 0 and the cases below this script
+# wrote the shipped data/surrogate.npz.)
+OUT_WEIGHT = (0.1, 0.1, 1.0, 1.0, 1.0, 1.0, 0.1, 0.1, 1.0, 0.1)
 
 
 def training_cases():
