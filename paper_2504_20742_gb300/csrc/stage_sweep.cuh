@@ -207,10 +207,55 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) Fn[k2] = p_make(F[2 * k2], F[2 * k2 + 1]);
       }
-      // cell (i, j): r divergence, sources, RK combine, partials (stage_tile's phase E)
+      // cell (i, j): r divergence, sources, RK combine, partials (stage_tile's phase E).  A cell
+      // the FP32 screen does not rule out takes its phase-change source after the row's other
+      // work, its divergence parked in s_acc: there the FP64 island runs with few values live
+      // and needs no spills, and the screened cells never pay for its registers.
       T rf[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) rf[f] = T(0);
+      // RK combine, output and partials of cell n = (i, j) whose rates (flux divergence and
+      // sources) are in a
+      const auto finish = [&](size_t n, const T* u14, const T* a) {
+        T out[NF];
+        const V dt2 = p_make(dt, dt);
+        if (STAGE == 1) {
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            const V o = p_fma(dt2, p_make(a[2 * k2], a[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+            out[2 * k2] = o.x;
+            out[2 * k2 + 1] = o.y;
+          }
+        } else {
+          const V half2 = p_make(T(0.5), T(0.5));
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            const V un2 = p_make(Un[(2 * k2) * N + n], Un[(2 * k2 + 1) * N + n]);
+            const V t = p_fma(dt2, p_make(a[2 * k2], a[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+            const V o = p_fma(half2, un2, p_mul(half2, t));
+            out[2 * k2] = o.x;
+            out[2 * k2 + 1] = o.y;
+            rf[2 * k2] = m_fabs(o.x - un2.x);
+            rf[2 * k2 + 1] = m_fabs(o.y - un2.y);
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          Uout[f * N + n] = out[f];
+          nbad += finite_bits(out[f]) ? 0 : 1;
+        }
+        if (STAGE == 2) {
+          Prim<T> wn;
+          cons_to_prim<T, false>(out, wn);
+          const T cdt = cell_dt<T>(dc, g, wn);
+          dtmin = cdt < dtmin ? cdt : dtmin;
+          const T vol = (T(j) + T(0.5)) * g.dr * g.dr * g.dx;
+          sM.add(vol * out[0]);
+          sW.add(vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]));
+          sE.add(vol * out[3]);
+        }
+      };
+      bool pending = false;
       if (cell_col) {
         const size_t n = (size_t)j * nx + i;
         T u14[NF];
@@ -242,54 +287,42 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
           bw -= An * (Fn[2].x + T(k::YL3) * Fn[4].x + T(k::YS3) * Fn[6].x);
           be -= An * Fn[1].y;
         }
-        {
-          T Q[NF];
-          double lnJ2[2];
-          if (phase_source<T, false>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr)) {
-            nactive += 1;
-            lnJh = fmaxf(lnJh, T(lnJ2[0]));
-            lnJt = fmaxf(lnJt, T(lnJ2[1]));
+        // phase_source's own screen: no phase change, or (kinetic model) no population and
+        // clearly below liquid saturation, gives a zero source
+        bool pl, ps;
+        pending = dc.sc.phase_change && (dc.sc.equilibrium || populations(w, pl, ps) || !clearly_inactive(w));
+        if (pending) {
 #pragma unroll
-            for (int f = 4; f < 13; ++f) acc[f] += Q[f];
-          }
-        }
-        T out[NF];
-        const V dt2 = p_make(dt, dt);
-        if (STAGE == 1) {
-#pragma unroll
-          for (int k2 = 0; k2 < NP; ++k2) {
-            const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
-            out[2 * k2] = o.x;
-            out[2 * k2 + 1] = o.y;
-          }
+          for (int k2 = 0; k2 < NP; ++k2) s_acc[warp][k2][lane] = p_make(acc[2 * k2], acc[2 * k2 + 1]);
         } else {
-          const V half2 = p_make(T(0.5), T(0.5));
+          finish(n, u14, acc);
+        }
+      }
 #pragma unroll
-          for (int k2 = 0; k2 < NP; ++k2) {
-            const V un2 = p_make(Un[(2 * k2) * N + n], Un[(2 * k2 + 1) * N + n]);
-            const V t = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
-            const V o = p_fma(half2, un2, p_mul(half2, t));
-            out[2 * k2] = o.x;
-            out[2 * k2 + 1] = o.y;
-            rf[2 * k2] = m_fabs(o.x - un2.x);
-            rf[2 * k2 + 1] = m_fabs(o.y - un2.y);
-          }
-        }
+      for (int k2 = 0; k2 < NP; ++k2) s_fs[warp][k2][lane] = Fn[k2];
+      if (pending) {
+        const size_t n = (size_t)j * nx + i;
+        T u14[NF], acc[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          Uout[f * N + n] = out[f];
-          nbad += finite_bits(out[f]) ? 0 : 1;
+        for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const V a = s_acc[warp][k2][lane];
+          acc[2 * k2] = a.x;
+          acc[2 * k2 + 1] = a.y;
         }
-        if (STAGE == 2) {
-          Prim<T> wn;
-          cons_to_prim<T, false>(out, wn);
-          const T cdt = cell_dt<T>(dc, g, wn);
-          dtmin = cdt < dtmin ? cdt : dtmin;
-          const T vol = (T(j) + T(0.5)) * g.dr * g.dr * g.dx;
-          sM.add(vol * out[0]);
-          sW.add(vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]));
-          sE.add(vol * out[3]);
+        Prim<T> w;
+        cons_to_prim<T, false>(u14, w);
+        T Q[NF];
+        double lnJ2[2];
+        if (phase_source<T, false>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr)) {
+          nactive += 1;
+          lnJh = fmaxf(lnJh, T(lnJ2[0]));
+          lnJt = fmaxf(lnJt, T(lnJ2[1]));
+#pragma unroll
+          for (int f = 4; f < 13; ++f) acc[f] += Q[f];
         }
+        finish(n, u14, acc);
       }
       if (STAGE == 2) {   // residual maxima of the row: one warp reduction per field
 #pragma unroll
@@ -298,8 +331,6 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
           if (lane == 0) s_rmax[warp][f] = m > s_rmax[warp][f] ? m : s_rmax[warp][f];
         }
       }
-#pragma unroll
-      for (int k2 = 0; k2 < NP; ++k2) s_fs[warp][k2][lane] = Fn[k2];
       __syncwarp();
     }
   }
