@@ -85,34 +85,32 @@ __device__ __forceinline__ bool less(double a, double b) {
 // Thermodynamics of a reconstructed face state (frozen composition): gamma, total enthalpy,
 // formation energy and frozen sound speed squared.  One reciprocal, E = 1/(rho R_g c_v),
 // gives T = p c_v E, R_g/c_v = rho R_g^2 E, and H = (c_v + R_g) T + e_f + |u|^2/2.
+// Where the state carries no liquid and no ice (the third moments are +-0) the terms of Y_l
+// and Y_s drop out exactly (x - 0 = x and fma(0, c, x) = x for x != 0), so that case skips
+// them: FP64 tests the moments' bits per state; FP32 takes the short form when the caller
+// knows the moments are zero (DRY).
 template <class T>
 struct FaceThermo {
   T g, H, ef, c2;
 };
-template <class T, bool BI = false>
+template <class T, bool BI = false, bool DRY = false>
 __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
   T Ya, cv, ef;
+  bool zero = DRY;
   if constexpr (std::is_same<T, double>::value) {
-    // FP64, rounding pinned term by term.  Where the state carries no liquid and no ice (the
-    // third moments are +-0) the terms of Y_l and Y_s drop out exactly (x - 0 = x and
-    // fma(0, c, x) = x for x != 0), so that case skips them on the FP64 pipe.
     const long long z3 = __double_as_longlong(q[8]) | __double_as_longlong(q[12]) |
                          (BI ? __double_as_longlong(q[17]) : 0LL);
-    if ((z3 << 1) == 0) {
-      Ya = 1.0 - q[4];
-      cv = fma(q[4], k::CVV, Ya * k::CVA);
-      ef = q[4] * k::E0V;
-    } else {
-      const double Yl = BI ? k::YL3 * (q[8] + q[17]) : k::YL3 * q[8], Ys = k::YS3 * q[12];
-      Ya = ((1.0 - q[4]) - Yl) - Ys;
-      cv = fma(Ys, k::CS, fma(Yl, k::CL, fma(q[4], k::CVV, Ya * k::CVA)));
-      ef = fma(Ys, k::E0S, q[4] * k::E0V);
-    }
+    zero = (z3 << 1) == 0;
+  }
+  if (zero) {
+    Ya = T(1) - q[4];
+    cv = rn_fma(q[4], T(k::CVV), Ya * T(k::CVA));
+    ef = q[4] * T(k::E0V);
   } else {
     const T Yl = BI ? T(k::YL3) * (q[8] + q[17]) : T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
-    Ya = T(1) - q[4] - Yl - Ys;
-    cv = Ya * T(k::CVA) + q[4] * T(k::CVV) + Yl * T(k::CL) + Ys * T(k::CS);
-    ef = q[4] * T(k::E0V) + Ys * T(k::E0S);
+    Ya = ((T(1) - q[4]) - Yl) - Ys;
+    cv = rn_fma(Ys, T(k::CS), rn_fma(Yl, T(k::CL), rn_fma(q[4], T(k::CVV), Ya * T(k::CVA))));
+    ef = rn_fma(Ys, T(k::E0S), q[4] * T(k::E0V));
   }
   const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
   const T rR = q[0] * Rg;
@@ -129,10 +127,11 @@ __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
 // Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns
 // (bimodal: 14..17 the second liquid set).  Roe flux in direction DIR (0: normal velocity u,
 // 1: normal velocity v) -> F[NFX].
-template <class T, int DIR, int NFX = NF>
+// DRY (FP32): the moment fields of both states are +0.
+template <class T, int DIR, int NFX = NF, bool DRY = false>
 __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
   constexpr bool BI = NFX == NF_BI;
-  const FaceThermo<T> tL = face_thermo<T, BI>(qL), tR = face_thermo<T, BI>(qR);
+  const FaceThermo<T> tL = face_thermo<T, BI, DRY>(qL), tR = face_thermo<T, BI, DRY>(qR);
   const T gL = tL.g, gR = tR.g, HL = tL.H, HR = tR.H, efL = tL.ef, efR = tR.ef, c2L = tL.c2, c2R = tR.c2;
   const T unL = DIR == 0 ? qL[1] : qL[2], utL = DIR == 0 ? qL[2] : qL[1];
   const T unR = DIR == 0 ? qR[1] : qR[2], utR = DIR == 0 ? qR[2] : qR[1];
@@ -205,12 +204,15 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
     }
   } else {
     // fields 4.. in pairs; the upwind values selected one by one (a selected pointer would
-    // put both face states in local memory)
+    // put both face states in local memory).  DRY: the moment pairs (6, 7) .. (10, 11) are
+    // +0 on both sides, so no selection is needed
     const bool up = fm >= T(0);
     const auto fm2 = p_make(fm, fm);
 #pragma unroll
     for (int k = 2; k < NFX / 2; ++k) {
-      const auto v = p_mul(fm2, p_make(up ? qL[2 * k] : qR[2 * k], up ? qL[2 * k + 1] : qR[2 * k + 1]));
+      const auto v = (DRY && k >= 3 && k <= 5)
+                         ? p_mul(fm2, p_make(T(0), T(0)))
+                         : p_mul(fm2, p_make(up ? qL[2 * k] : qR[2 * k], up ? qL[2 * k + 1] : qR[2 * k + 1]));
       F[2 * k] = v.x;
       F[2 * k + 1] = v.y;
     }

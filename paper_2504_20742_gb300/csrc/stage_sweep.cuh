@@ -12,8 +12,12 @@
 //     barrier.
 // Every cell value is computed by the same expressions in the same order as in stage_tile,
 // so the state is bitwise that of the other tile shapes; only the summation order of the
-// FP64 totals differs (compensated FP32 sums per lane, FP64 from the warp on).  Variant:
-// FP32, axisymmetric, without the diffusive fluxes, one liquid set, plain source.
+// FP64 totals differs (compensated FP32 sums per lane, FP64 from the warp on).  Rows whose
+// particle moments are +0 in all 32 columns (dry air: most of a plume outside its mixing
+// layer) skip the reconstruction of the three all-moment field pairs, whose face states are
+// then +0, and the Y_l, Y_s terms of the face thermodynamics, which drop out exactly; the
+// bits are those of the full formulas.  Variant: FP32, axisymmetric, without the diffusive
+// fluxes, one liquid set, plain source.
 #pragma once
 #include "stage.cuh"
 
@@ -42,6 +46,9 @@ __device__ __forceinline__ float2 shfl_up2(float2 v) {
 __device__ __forceinline__ float2 shfl_down2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
+
+// pairs of state fields that hold only particle moments: (6, 7), (8, 9), (10, 11)
+__host__ __device__ constexpr bool moment_pair(int k2) { return k2 >= 3 && k2 <= 5; }
 
 template <class ST, int STAGE>
 __global__ void __launch_bounds__(ST::NT, ST::MINB)
@@ -78,8 +85,10 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   const auto slot = [](int j) { return (j + 3) % 3; };   // j >= -2
 
   // primitive vector (stage_tile's phase A) of cell (i, j) of the stencil; zero where no
-  // cell of the strip needs it (corners, columns beyond the halo)
-  const auto load_q = [&](int j, V* q) {
+  // cell of the strip needs it (corners, columns beyond the halo).  Returns whether the row
+  // is dry: every moment field (5..12) of the primitive vectors of the warp's 32 columns
+  // is +0.
+  const auto load_q = [&](int j, V* q) -> bool {
     const bool rin = j >= 0 && j < nr;
     if ((xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1) {
       T u14[NF];
@@ -87,8 +96,11 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
         const size_t n = (size_t)j * nx + i;
 #pragma unroll
         for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
-      } else {
-        load_ghost<T, NF>(dc, Uin, N, i, j, u14);
+      } else {   // out of line, through its own array: u14 stays in registers
+        T g14[NF];
+        load_ghost<T, NF>(dc, Uin, N, i, j, g14);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u14[f] = g14[f];
       }
       Prim<T> w;
       cons_to_prim<T, false>(u14, w);
@@ -100,6 +112,10 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) q[k2] = p_make(T(0), T(0));
     }
+    unsigned zb = 0;
+#pragma unroll
+    for (int k2 = 2; k2 < NP; ++k2) zb |= (k2 == 2 ? 0u : __float_as_uint(q[k2].x)) | (k2 == 6 ? 0u : __float_as_uint(q[k2].y));
+    return __all_sync(0xffffffffu, zb == 0u);
   };
 
   // running partials of this lane's cells
@@ -110,15 +126,18 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   int nactive = 0, nbad = 0;
   if (lane < NF) s_rmax[warp][lane] = T(0);
 
+  // dry rows around the current row j: bit 0 row j-1, bit 1 row j, bit 2 row j+1, bit 3
+  // row j+2 (warp-uniform)
+  unsigned rowdry = 0;
   if (jb < je) {
     // rows jb-2 .. jb+1: the upper face state of row jb-1, row jb's lower face state, and the
     // flux of the face between rows jb-1 and jb; rows jb-1 .. jb+1 stay in the ring
     {
       V qm[NP], q0[NP], q1[NP], q2[NP];
       load_q(jb - 2, qm);
-      load_q(jb - 1, q0);
-      load_q(jb, q1);
-      load_q(jb + 1, q2);
+      rowdry = load_q(jb - 1, q0) ? 1u : 0u;
+      rowdry |= load_q(jb, q1) ? 2u : 0u;
+      rowdry |= load_q(jb + 1, q2) ? 4u : 0u;
       T qL[NF], qR[NF], F[NF];
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) {
@@ -144,11 +163,17 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
     for (int j = jb; j < je; ++j) {
       const int sj = slot(j), sj1 = slot(j + 1), sj2 = slot(j + 2);
       // x direction, row j: slopes from the neighbours' values, the face i+1/2 per lane,
-      // the divergence from the west neighbour's face
-      {
+      // the divergence from the west neighbour's face.  A dry row: the all-moment pairs have
+      // zero slopes and +0 face states (vl_faces2 of three +0 values gives hi = +0, lo = +0)
+      const auto xphase = [&](auto dry_tag) {
+        constexpr bool DRY = decltype(dry_tag)::value;
         T qL[NF], qR[NF], F[NF];
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
+          if (DRY && moment_pair(k2)) {
+            qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
+            continue;
+          }
           V lo, hi;
           vl_faces2(s_q[warp][sj][k2][lm], s_q[warp][sj][k2][lane], s_q[warp][sj][k2][lp], lo, hi);
           const V r = shfl_down2(lo);
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
           qR[2 * k2] = r.x;
           qR[2 * k2 + 1] = r.y;
         }
-        roe_flux<T, 0, NF>(qL, qR, F);
+        roe_flux<T, 0, NF, DRY>(qL, qR, F);
         const V cw2 = p_make(g.idx, g.idx), nce2 = p_make(-g.idx, -g.idx);
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
@@ -182,15 +207,27 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
             }
           }
         }
-      }
-      // r direction: row j+2 into the ring (over row j-1), row j+1's slope, face j+1/2
+      };
+      if (rowdry & 2u)
+        xphase(std::true_type{});
+      else
+        xphase(std::false_type{});
+      // r direction: row j+2 into the ring (over row j-1), row j+1's slope, face j+1/2.
+      // Rows j-1 .. j+2 dry: the all-moment pairs of both face states are +0 (row j's upper
+      // face state came from rows j-1 .. j+1)
       V Fn[NP];
-      {
-        V qc[NP];
-        load_q(j + 2, qc);
+      V qc[NP];
+      rowdry |= load_q(j + 2, qc) ? 8u : 0u;
+      const auto rphase = [&](auto dry_tag) {
+        constexpr bool DRY = decltype(dry_tag)::value;
         T qL[NF], qR[NF], F[NF];
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
+          if (DRY && moment_pair(k2)) {
+            qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
+            s_fhi[warp][k2][lane] = p_make(T(0), T(0));
+            continue;
+          }
           V lo, hi;
           vl_faces2(s_q[warp][sj][k2][lane], s_q[warp][sj1][k2][lane], qc[k2], lo, hi);
           const V fl = s_fhi[warp][k2][lane];
@@ -203,10 +240,14 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
         __syncwarp();                   // every lane has read row j's values above
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) s_q[warp][sj2][k2][lane] = qc[k2];
-        roe_flux<T, 1, NF>(qL, qR, F);
+        roe_flux<T, 1, NF, DRY>(qL, qR, F);
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) Fn[k2] = p_make(F[2 * k2], F[2 * k2 + 1]);
-      }
+      };
+      if ((rowdry & 15u) == 15u)
+        rphase(std::true_type{});
+      else
+        rphase(std::false_type{});
       // cell (i, j): r divergence, sources, RK combine, partials (stage_tile's phase E).  A cell
       // the FP32 screen does not rule out takes its phase-change source after the row's other
       // work, its divergence parked in s_acc: there the FP64 island runs with few values live
@@ -331,6 +372,7 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
           if (lane == 0) s_rmax[warp][f] = m > s_rmax[warp][f] ? m : s_rmax[warp][f];
         }
       }
+      rowdry >>= 1;
       __syncwarp();
     }
   }
