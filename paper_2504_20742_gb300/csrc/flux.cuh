@@ -103,26 +103,31 @@ __device__ __forceinline__ FaceThermo<T> face_thermo(const T* q) {
     zero = (z3 << 1) == 0;
   }
   if (zero) {
-    Ya = T(1) - q[4];
-    cv = rn_fma(q[4], T(k::CVV), Ya * T(k::CVA));
-    ef = q[4] * T(k::E0V);
+    Ya = rn_sub(T(1), q[4]);
+    cv = rn_fma(q[4], T(k::CVV), rn_mul(Ya, T(k::CVA)));
+    ef = rn_mul(q[4], T(k::E0V));
   } else {
-    const T Yl = BI ? T(k::YL3) * (q[8] + q[17]) : T(k::YL3) * q[8], Ys = T(k::YS3) * q[12];
-    Ya = ((T(1) - q[4]) - Yl) - Ys;
-    cv = rn_fma(Ys, T(k::CS), rn_fma(Yl, T(k::CL), rn_fma(q[4], T(k::CVV), Ya * T(k::CVA))));
-    ef = rn_fma(Ys, T(k::E0S), q[4] * T(k::E0V));
+    const T Yl = rn_mul(T(k::YL3), BI ? rn_add(q[8], q[17]) : q[8]), Ys = rn_mul(T(k::YS3), q[12]);
+    Ya = rn_sub(rn_sub(rn_sub(T(1), q[4]), Yl), Ys);
+    cv = rn_fma(Ys, T(k::CS), rn_fma(Yl, T(k::CL), rn_fma(q[4], T(k::CVV), rn_mul(Ya, T(k::CVA)))));
+    ef = rn_fma(Ys, T(k::E0S), rn_mul(q[4], T(k::E0V)));
   }
-  const T Rg = Ya * T(k::RA) + q[4] * T(k::RV);
-  const T rR = q[0] * Rg;
-  const T E = trcp(rR * cv);
-  const T Tg = q[3] * cv * E;
+  // the rest with its rounding pinned too, so that the kernels that inline this function
+  // all get the same bits whatever their surroundings
+  const T Rg = rn_fma(q[4], T(k::RV), rn_mul(Ya, T(k::RA)));
+  const T rR = rn_mul(q[0], Rg);
+  const T E = trcp(rn_mul(rR, cv));
+  const T Tg = rn_mul(rn_mul(q[3], cv), E);
   FaceThermo<T> t;
   t.ef = ef;
-  t.g = T(1) + Rg * rR * E;
-  t.H = (cv + Rg) * Tg + t.ef + T(0.5) * (q[1] * q[1] + q[2] * q[2]);
-  t.c2 = t.g * Rg * Tg;
+  t.g = rn_fma(rn_mul(Rg, rR), E, T(1));
+  t.H = rn_fma(T(0.5), rn_fma(q[1], q[1], rn_mul(q[2], q[2])), rn_fma(rn_add(cv, Rg), Tg, t.ef));
+  t.c2 = rn_mul(rn_mul(t.g, Rg), Tg);
   return t;
 }
+
+// pairs of state fields (one liquid set) that hold only particle moments: (6, 7) .. (10, 11)
+__host__ __device__ constexpr bool moment_pair(int k2) { return k2 >= 3 && k2 <= 5; }
 
 // Reconstructed face primitive vector: 0 rho, 1 u, 2 v, 3 p, 4 Y_v, 5..8 ml, 9..12 ms, 13 ns
 // (bimodal: 14..17 the second liquid set).  Roe flux in direction DIR (0: normal velocity u,
@@ -210,7 +215,7 @@ __device__ __forceinline__ void roe_flux(const T* qL, const T* qR, T* F) {
     const auto fm2 = p_make(fm, fm);
 #pragma unroll
     for (int k = 2; k < NFX / 2; ++k) {
-      const auto v = (DRY && k >= 3 && k <= 5)
+      const auto v = (DRY && moment_pair(k))
                          ? p_mul(fm2, p_make(T(0), T(0)))
                          : p_mul(fm2, p_make(up ? qL[2 * k] : qR[2 * k], up ? qL[2 * k + 1] : qR[2 * k + 1]));
       F[2 * k] = v.x;

@@ -626,7 +626,10 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   }
 
   // phase A: halo primitives.  A thread owns up to NA halo cells; the interior loads of all
-  // of them are issued before any is converted, so their latencies overlap.
+  // of them are issued before any is converted, so their latencies overlap.  FP32, one
+  // liquid set: zb collects the bits of the halo's moment fields (5..12).
+  constexpr bool DRY_OK = !IS64 && !BI;
+  unsigned zb = 0;
   {
     constexpr int NA = (HX * HY + NT - 1) / NT;
     T u14[NA][NFX];
@@ -670,30 +673,48 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       }
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) qs2[k2][hj][hi] = p_make(qv[2 * k2], qv[2 * k2 + 1]);
+      if constexpr (DRY_OK) {
+#pragma unroll
+        for (int f = 5; f < 13; ++f) zb |= __float_as_uint(float(qv[f]));
+      }
     }
   }
-  __syncthreads();
+  // A dry tile: every moment field of the halo's primitive vectors is +0 (dry air, most of
+  // a plume outside its mixing layer).  Its reconstruction skips the three all-moment pairs,
+  // whose slopes are zero and face states +0, and its Roe fluxes the condensate terms of the
+  // face thermodynamics, which vanish exactly: the bits of the full formulas.
+  const bool dry = DRY_OK ? __syncthreads_and(zb == 0u) != 0 : (__syncthreads(), false);
 
   const T dt = s_dt;
 
   // phase B1: limited x slopes, once per cell, written as the states of its two faces
   // (tile-local cell c in [-1, TX]; face f lies between cells f-1 and f)
-  for (int p = tid; p < (TX + 2) * TY; p += NT) {
-    const int c = p % (TX + 2) - 1, hj = p / (TX + 2);
-    const int i = i0 + c, j = j0 + hj;
-    if (i > nx || j >= nr) continue;
+  const auto phase_b1 = [&](auto dry_tag) {
+    constexpr bool DRY = decltype(dry_tag)::value;
+    for (int p = tid; p < (TX + 2) * TY; p += NT) {
+      const int c = p % (TX + 2) - 1, hj = p / (TX + 2);
+      const int i = i0 + c, j = j0 + hj;
+      if (i > nx || j >= nr) continue;
 #pragma unroll
-    for (int k2 = 0; k2 < NP; ++k2) {
-      const V am = qs2[k2][hj + 2][c + 1], a0 = qs2[k2][hj + 2][c + 2], a1 = qs2[k2][hj + 2][c + 3];
-      V flo, fhi;
-      vl_faces2(am, a0, a1, flo, fhi);
-      if (c < TX) fL2[k2][hj * (TX + 1) + c + 1] = fhi;
-      if (c >= 0) fR2[k2][hj * (TX + 1) + c] = flo;
+      for (int k2 = 0; k2 < NP; ++k2) {
+        if (DRY && moment_pair(k2)) continue;   // +0 face states, not stored
+        const V am = qs2[k2][hj + 2][c + 1], a0 = qs2[k2][hj + 2][c + 2], a1 = qs2[k2][hj + 2][c + 3];
+        V flo, fhi;
+        vl_faces2(am, a0, a1, flo, fhi);
+        if (c < TX) fL2[k2][hj * (TX + 1) + c + 1] = fhi;
+        if (c >= 0) fR2[k2][hj * (TX + 1) + c] = flo;
+      }
     }
-  }
+  };
+  if (dry)
+    phase_b1(std::true_type{});
+  else
+    phase_b1(std::false_type{});
   __syncthreads();
 
   // phase B2: x-face Roe fluxes
+  const auto phase_b2 = [&](auto dry_tag) {
+    constexpr bool DRY = decltype(dry_tag)::value;
   for (int p = tid; p < (TX + 1) * TY; p += NT) {
     const int fx = p % (TX + 1), hj = p / (TX + 1);
     const int i = i0 + fx, j = j0 + hj;
@@ -701,13 +722,17 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
     for (int k2 = 0; k2 < NP; ++k2) {
+      if (DRY && moment_pair(k2)) {
+        qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
+        continue;
+      }
       const V a = fL2[k2][p], b = fR2[k2][p];
       qL[2 * k2] = a.x;
       qL[2 * k2 + 1] = a.y;
       qR[2 * k2] = b.x;
       qR[2 * k2 + 1] = b.y;
     }
-    roe_flux<T, 0, NFX>(qL, qR, F);
+    roe_flux<T, 0, NFX, DRY>(qL, qR, F);
     // walls are adiabatic, impermeable and slip: nothing diffuses through them
     if (dc.viscous && !((i == 0 && dc.bc_xlo == 1) || (i == nx && dc.bc_xhi == 1))) {
       const auto q = [&](int f, int side) -> T { return qs(f, hj + 2, fx + 1 + side); };
@@ -716,17 +741,24 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
     for (int k2 = 0; k2 < NP; ++k2) fb2[k2][p] = p_make(F[2 * k2], F[2 * k2 + 1]);
   }
+  };
+  if (dry)
+    phase_b2(std::true_type{});
+  else
+    phase_b2(std::false_type{});
   __syncthreads();
 
   const int ci = tid % TX, cj = tid / TX;
   const int i = i0 + ci, j = j0 + cj;
   const bool cell = tid < NCELL && i < nx && j < nr;
   // limited r slope of tile-local row c in [-1, TY] at column hi -> states of its r faces
-  const auto r_slope = [&](int hi, int c) {
+  const auto r_slope = [&](int hi, int c, auto dry_tag) {
+    constexpr bool DRY = decltype(dry_tag)::value;
     const int ii = i0 + hi, jj = j0 + c;
     if (ii >= nx || jj > nr) return;
 #pragma unroll
     for (int k2 = 0; k2 < NP; ++k2) {
+      if (DRY && moment_pair(k2)) continue;   // +0 face states, not stored
       const V am = qs2[k2][c + 1][hi + 2], a0 = qs2[k2][c + 2][hi + 2], a1 = qs2[k2][c + 3][hi + 2];
       V flo, fhi;
       vl_faces2(am, a0, a1, flo, fhi);
@@ -808,12 +840,23 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
   }
 
   if (dc.geom == 1) {
-    if (ROWM1_EARLY && tid >= NCELL && tid - NCELL < TX) r_slope(tid - NCELL, -1);
+    if (ROWM1_EARLY && tid >= NCELL && tid - NCELL < TX) {
+      if (dry)
+        r_slope(tid - NCELL, -1, std::true_type{});
+      else
+        r_slope(tid - NCELL, -1, std::false_type{});
+    }
     __syncthreads();
     // phase D1: limited r slopes (tile-local row c in [-1, TY]) -> states of the r faces
-    for (int p = tid + (ROWM1_EARLY ? TX : 0); p < TX * (TY + 2); p += NT) r_slope(p % TX, p / TX - 1);
+    if (dry) {
+      for (int p = tid + (ROWM1_EARLY ? TX : 0); p < TX * (TY + 2); p += NT) r_slope(p % TX, p / TX - 1, std::true_type{});
+    } else {
+      for (int p = tid + (ROWM1_EARLY ? TX : 0); p < TX * (TY + 2); p += NT) r_slope(p % TX, p / TX - 1, std::false_type{});
+    }
     __syncthreads();
     // phase D2: r-face Roe fluxes (face fy lies between tile rows fy-1 and fy)
+    const auto phase_d2 = [&](auto dry_tag) {
+      constexpr bool DRY = decltype(dry_tag)::value;
     for (int p = tid; p < TX * (TY + 1); p += NT) {
       const int hi = p % TX, fy = p / TX;
       const int ii = i0 + hi, jj = j0 + fy;
@@ -821,13 +864,17 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
       T qL[NFX], qR[NFX], F[NFX];
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) {
+        if (DRY && moment_pair(k2)) {
+          qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
+          continue;
+        }
         const V a = (TL::ROWM1_EARLY && p < TX) ? fLm1[k2][p] : fL2[k2][p], b = fR2[k2][p];
         qL[2 * k2] = a.x;
         qL[2 * k2 + 1] = a.y;
         qR[2 * k2] = b.x;
         qR[2 * k2 + 1] = b.y;
       }
-      roe_flux<T, 1, NFX>(qL, qR, F);
+      roe_flux<T, 1, NFX, DRY>(qL, qR, F);
       if (dc.viscous && !(jj == nr && dc.bc_rhi == 1)) {
         const auto q = [&](int f, int side) -> T { return qs(f, fy + 1 + side, hi + 2); };
         sub_diffusive_flux<T, NFX>(q, g.idr, g.nu_t, F);
@@ -835,6 +882,11 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) fb2[k2][p] = p_make(F[2 * k2], F[2 * k2 + 1]);
     }
+    };
+    if (dry)
+      phase_d2(std::true_type{});
+    else
+      phase_d2(std::false_type{});
     __syncthreads();
   }
 

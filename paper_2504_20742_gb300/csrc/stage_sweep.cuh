@@ -47,9 +47,6 @@ __device__ __forceinline__ float2 shfl_down2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
-// pairs of state fields that hold only particle moments: (6, 7), (8, 9), (10, 11)
-__host__ __device__ constexpr bool moment_pair(int k2) { return k2 >= 3 && k2 <= 5; }
-
 template <class ST, int STAGE>
 __global__ void __launch_bounds__(ST::NT, ST::MINB)
     k_sweep(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
