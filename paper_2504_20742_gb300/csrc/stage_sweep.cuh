@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   __shared__ float2 s_q[ST::W][3][NP][32];
   __shared__ float2 s_fhi[ST::W][NP][32], s_fs[ST::W][NP][32], s_acc[ST::W][NP][32];
   __shared__ float s_rmax[ST::W][NF];
+  // per warp, per lane: the temperature of the three rows of the ring (the cell update's
+  // source screen takes the primitive variables from the ring instead of recomputing them)
+  __shared__ float s_T[ST::W][3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int by = blockIdx.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
   const int nx = dc.nx, nr = dc.nr;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   // cell of the strip needs it (corners, columns beyond the halo).  Returns whether the row
   // is dry: every moment field (5..12) of the primitive vectors of the warp's 32 columns
   // is +0.
-  const auto load_q = [&](int j, V* q) -> bool {
+  const auto load_q = [&](int j, V* q, T& Tg) -> bool {
     const bool rin = j >= 0 && j < nr;
     if ((xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1) {
       T u14[NF];
@@ -105,9 +108,11 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
       prim_vector<T, false>(w, qv);
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) q[k2] = p_make(qv[2 * k2], qv[2 * k2 + 1]);
+      Tg = w.Tg;
     } else {
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) q[k2] = p_make(T(0), T(0));
+      Tg = T(0);
     }
     unsigned zb = 0;
 #pragma unroll
@@ -131,10 +136,14 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
     // flux of the face between rows jb-1 and jb; rows jb-1 .. jb+1 stay in the ring
     {
       V qm[NP], q0[NP], q1[NP], q2[NP];
-      load_q(jb - 2, qm);
-      rowdry = load_q(jb - 1, q0) ? 1u : 0u;
-      rowdry |= load_q(jb, q1) ? 2u : 0u;
-      rowdry |= load_q(jb + 1, q2) ? 4u : 0u;
+      T Tm, T0, T1, T2;
+      load_q(jb - 2, qm, Tm);
+      rowdry = load_q(jb - 1, q0, T0) ? 1u : 0u;
+      rowdry |= load_q(jb, q1, T1) ? 2u : 0u;
+      rowdry |= load_q(jb + 1, q2, T2) ? 4u : 0u;
+      s_T[warp][slot(jb - 1)][lane] = T0;
+      s_T[warp][slot(jb)][lane] = T1;
+      s_T[warp][slot(jb + 1)][lane] = T2;
       T qL[NF], qR[NF], F[NF];
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) {
@@ -214,7 +223,8 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
       // face state came from rows j-1 .. j+1)
       V Fn[NP];
       V qc[NP];
-      rowdry |= load_q(j + 2, qc) ? 8u : 0u;
+      T Tc;
+      rowdry |= load_q(j + 2, qc, Tc) ? 8u : 0u;
       const auto rphase = [&](auto dry_tag) {
         constexpr bool DRY = decltype(dry_tag)::value;
         T qL[NF], qR[NF], F[NF];
@@ -237,6 +247,7 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
         __syncwarp();                   // every lane has read row j's values above
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) s_q[warp][sj2][k2][lane] = qc[k2];
+        s_T[warp][sj2][lane] = Tc;
         roe_flux<T, 1, NF, DRY>(qL, qR, F);
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) Fn[k2] = p_make(F[2 * k2], F[2 * k2 + 1]);
@@ -299,8 +310,27 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
         T u14[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) u14[f] = Uin[f * N + n];
+        // the primitive variables the update and the screen use, from the ring: the bits
+        // cons_to_prim gave for this cell's values when the row entered it
         Prim<T> w;
-        cons_to_prim<T, false>(u14, w);
+        {
+          T qv[NF];
+#pragma unroll
+          for (int k2 = 0; k2 < NP; ++k2) {
+            const V a = s_q[warp][sj][k2][lane];
+            qv[2 * k2] = a.x;
+            qv[2 * k2 + 1] = a.y;
+          }
+          w.rho = qv[0];
+          w.p = qv[3];
+          w.Yv = qv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            w.ml[q] = qv[5 + q];
+            w.ms[q] = qv[9 + q];
+          }
+          w.Tg = s_T[warp][sj][lane];
+        }
         T acc[NF];
         const T ijh = trcp(T(j) + T(0.5));
         const T cs = T(j) * ijh * g.idr;
