@@ -124,7 +124,10 @@ typedef struct {
 /* Bytes of device workspace needed by a case at a precision (boundary states, reduction
  * partials, time step and diagnostics; for CT_FP64 without the bimodal liquid also the
  * primitive variables of U and U1 with the temperature and c_v, 2 x 16 x N doubles, which
- * each stage writes for the next one so that no cell is converted twice).  Returns 0 for an invalid case. */
+ * each stage writes for the next one so that no cell is converted twice; for CT_FP32_MLP on
+ * an inviscid axisymmetric case also the surrogate queue of the column-sweep step, a cell
+ * index and 14 floats per cell plus 4096 reduction records, about 60 bytes per cell).
+ * Returns 0 for an invalid case. */
 size_t ct_workspace_bytes(const ct_case *c, int precision);
 
 /* Validate the case and prepare the workspace: inflow profile per row (row velocity
@@ -312,7 +315,10 @@ ct_status ct_mlp_infer(const void *blob, const float *X, int n, float *Y, int *e
  * BF16 tensor-core network in `blob` (ct_mlp_pack) instead of the plain source (Sec. 2.2);
  * cells outside the hull use the plain source (counted in diagnostics slot 26).  The moment
  * assembly, freezing, limiters and water bookkeeping are the plain path's, so conservation
- * is unaffected.  U, U1, work as for ct_step (workspace set up with CT_FP32_MLP). */
+ * is unaffected.  U, U1, work as for ct_step (workspace set up with CT_FP32_MLP: with the
+ * column-sweep tile shape the stage kernel queues the cells its source screen keeps in the
+ * workspace, and a second kernel per stage runs the network on them).  Every tile shape
+ * gives the same state bit for bit. */
 ct_status ct_step_surrogate(const ct_case *c, void *U, void *U1, void *work, const void *blob, int nsteps, double cfl,
                             void *stream);
 

@@ -430,8 +430,18 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // instead of converting the conserved variables again (the FP64 pipe bounds these kernels).
 static bool uses_prims(const ct_case* c, int precision) { return precision == CT_FP64 && !c->bimodal; }
 static size_t prim_bytes(const ct_case* c) { return 2 * (size_t)NPLANE * c->nx * case_nr(c) * sizeof(double); }
+// FP32 + surrogate cases the column sweep can step keep the surrogate kernel's queue in the
+// workspace: a cell index and 14 rates per cell at most, and its CTAs' partial records.
+static bool uses_queue(const ct_case* c, int precision) {
+  return precision == CT_FP32_MLP && c->geom == 1 && !c->viscous;
+}
+static size_t queue_bytes(const ct_case* c) {
+  const size_t n = (size_t)c->nx * case_nr(c);
+  return align256(n * sizeof(unsigned int)) + align256((size_t)NF * n * sizeof(float)) +
+         align256((size_t)QUEUE_GRID_MAX * NPART * sizeof(double));
+}
 
-static size_t ws_bytes(const ct_case* c, bool prims = false) {
+static size_t ws_bytes(const ct_case* c, bool prims = false, bool queue = false) {
   const size_t nr = (size_t)case_nr(c);
   size_t b = HDR_BYTES;
   b += align256(nr * case_nf(c) * sizeof(double));
@@ -440,6 +450,7 @@ static size_t ws_bytes(const ct_case* c, bool prims = false) {
   b += align256((size_t)max_rows(c) * sizeof(unsigned int));
   b += align256((size_t)max_rows(c) * NPART * sizeof(double));
   if (prims) b += align256(prim_bytes(c));
+  if (queue) b += queue_bytes(c);
   return b;
 }
 
@@ -469,7 +480,7 @@ static ct_status property_tables(const double** tab, const float** tabf) {
   return CT_OK;
 }
 
-static DevCase make_dev(const ct_case* c, void* work, int shape = 0, bool prims = false) {
+static DevCase make_dev(const ct_case* c, void* work, int shape = 0, bool prims = false, bool queue = false) {
   DevCase d;
   memset(&d, 0, sizeof(d));
   d.geom = c->geom;
@@ -525,6 +536,8 @@ static DevCase make_dev(const ct_case* c, void* work, int shape = 0, bool prims 
   d.row_part = (double*)(base + off);
   off += align256((size_t)max_rows(c) * NPART * sizeof(double));
   d.prims = prims && work ? (double*)(base + off) : nullptr;
+  if (prims) off += align256(prim_bytes(c));
+  if (queue) d.qoff = (int)(off / 256);   // off is a multiple of 256
   d.nblocks = num_blocks(c, shape);
   d.tiles_x = tiles_x(c, shape);
   d.tiles_y = tiles_y(c, shape);
@@ -554,16 +567,19 @@ extern "C" {
 
 size_t ct_workspace_bytes(const ct_case* c, int precision) {
   if (validate(c, precision) != CT_OK) return 0;
-  return ws_bytes(c, uses_prims(c, precision));
+  return ws_bytes(c, uses_prims(c, precision), uses_queue(c, precision));
 }
 
-ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host, void* work, size_t work_bytes,
-                   void* stream) {
+// queue: the workspace holds the surrogate queue (single-case FP32 + surrogate steps through
+// the column sweep; a batch's cases step through the batched kernel and hold none)
+static ct_status setup_case(const ct_case* c, int precision, const double* ufac_rows_host, void* work,
+                            size_t work_bytes, void* stream, bool queue) {
   ct_status s = validate(c, precision);
   if (s != CT_OK) return s;
   if (!work) return fail(CT_ERR_ARG, "null workspace");
   if (((uintptr_t)work & 255) != 0) return fail(CT_ERR_ARG, "workspace must be 256-byte aligned");
-  if (work_bytes < ws_bytes(c, uses_prims(c, precision))) return fail(CT_ERR_SIZE, "workspace too small (see ct_workspace_bytes)");
+  if (work_bytes < ws_bytes(c, uses_prims(c, precision), queue))
+    return fail(CT_ERR_SIZE, "workspace too small (see ct_workspace_bytes)");
   cudaStream_t st = (cudaStream_t)stream;
   DevCase d = make_dev(c, work);
   WsHeader h;
@@ -590,6 +606,11 @@ ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host
   // the header copy and the profile kernel read host memory that must outlive them
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check("ct_setup sync");
   return cuda_check("ct_setup");
+}
+
+ct_status ct_setup(const ct_case* c, int precision, const double* ufac_rows_host, void* work, size_t work_bytes,
+                   void* stream) {
+  return setup_case(c, precision, ufac_rows_host, work, work_bytes, stream, uses_queue(c, precision));
 }
 
 static ct_status check_setup(const ct_case* c, void* work, void* stream) {
@@ -652,6 +673,24 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   return launch_dt(c, precision, work, U, cfl, st, uses_prims(c, precision));
 }
 
+// CTAs of a launch of the surrogate queue kernel: as many as the GPU keeps resident
+// (persistent; the queue's length is known on the device only), found once per device.
+static std::mutex g_qgrid_mu;
+static int g_qgrid[64];
+static int queue_grid(const void* fn, size_t smem) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(g_qgrid_mu);
+  if (g_qgrid[dev] == 0) {
+    int per_sm = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QueueTile::NT, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm <= 0 || nsm <= 0)
+      return 0;
+    g_qgrid[dev] = std::min(QUEUE_GRID_MAX, per_sm * nsm);
+  }
+  return g_qgrid[dev];
+}
+
 static std::mutex g_attr_mu;
 static bool g_attr_done[NSHAPES][NVARIANT];
 
@@ -668,8 +707,12 @@ static ct_status set_stage_attrs(int shape, int p) {
       e = cudaFuncSetAttribute(ss->batch[p][st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
     if (e == cudaSuccess && p == 0 && ss->stage_sp[st])
       e = cudaFuncSetAttribute(ss->stage_sp[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
+    if (e == cudaSuccess && p == 2 && ss->queue[st])
+      e = cudaFuncSetAttribute(ss->queue[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->queue_smem);
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
+  if (p == 2 && ss->queue[0] && queue_grid(ss->queue[0], ss->queue_smem) <= 0)
+    return fail(CT_ERR_CUDA, "no resident CTA for the surrogate queue kernel");
   g_attr_done[shape][p] = true;
   return CT_OK;
 }
@@ -686,6 +729,11 @@ static void launch_stage(const StageSet* ss, int p, int stage, const DevCase& d,
   // FP64 with the stored primitives in the workspace: the kernel that reads and writes them
   const void* fn = (p == 0 && d.prims) ? ss->stage_sp[stage - 1] : ss->stage[p][stage - 1];
   cudaLaunchKernel(fn, grid, dim3(ss->nt), args, ss->smem[p], st);
+  // FP32 + surrogate through the column sweep: the surrogate kernel on the queued cells
+  if (p == 2 && ss->queue[stage - 1] && d.qoff > 0) {
+    const int qgrid = queue_grid(ss->queue[stage - 1], ss->queue_smem);
+    if (qgrid > 0) cudaLaunchKernel(ss->queue[stage - 1], dim3(qgrid), dim3(QueueTile::NT), args, ss->queue_smem, st);
+  }
 }
 
 static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U1, void* work, int nsteps, double cfl,
@@ -696,7 +744,7 @@ static ct_status enqueue_steps(const ct_case* c, int precision, void* U, void* U
   ct_status s = set_stage_attrs(shape, p);
   if (s != CT_OK) return s;
   const StageSet* ss = stage_set(shape);
-  DevCase d = make_dev(c, work, shape, prims);
+  DevCase d = make_dev(c, work, shape, prims, uses_queue(c, precision));
   d.cfl = cfl;
   dim3 grid(tiles_x(c, shape), tiles_y(c, shape));
   for (int k2 = 0; k2 < nsteps; ++k2) {
@@ -966,7 +1014,7 @@ ct_status ct_autotune(const ct_case* c, int precision, const void* U, void* U1, 
     if (shape_usable(sh, p, c)) {
       if ((s = set_stage_attrs(sh, p)) != CT_OK) return s;
       const StageSet* ss = stage_set(sh);
-      DevCase d = make_dev(c, work, sh, uses_prims(c, precision));
+      DevCase d = make_dev(c, work, sh, uses_prims(c, precision), uses_queue(c, precision));
       const dim3 grid(tiles_x(c, sh), tiles_y(c, sh));
       // stage 1 only: it reads U and writes the scratch state U1, so U is left as it was
       auto launch = [&]() { launch_stage(ss, p, 1, d, grid, U, nullptr, U1, blob, st); };
@@ -1142,8 +1190,8 @@ ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const
   // per-case workspace: header, inflow profile and ambient state
   for (int k = 0; k < ncases && s == CT_OK; ++k) {
     const ct_case* c = &cases[k];
-    s = ct_setup(c, precision, ufac_rows_host ? ufac_rows_host + row : nullptr, b->work + b->case_off[k],
-                 ws_bytes(c), stream);
+    s = setup_case(c, precision, ufac_rows_host ? ufac_rows_host + row : nullptr, b->work + b->case_off[k],
+                   ws_bytes(c), stream, false);
     row += (size_t)case_nr(c);
   }
   if (s == CT_OK && cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), b->stream) != cudaSuccess)

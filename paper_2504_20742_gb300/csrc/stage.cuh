@@ -43,6 +43,9 @@ struct WsHeader {
   unsigned int setup_magic;
   int nblocks;
   int pad;
+  unsigned int qcount;    // cells queued for the surrogate kernel in the current stage
+  unsigned int qticket;   // that kernel's last-block-done ticket
+  double pre[NPART];      // the column sweep's record of a stage whose queue is pending
 };
 constexpr unsigned int SETUP_MAGIC = 0x43544231u;
 constexpr size_t HDR_BYTES = 1024;
@@ -52,6 +55,8 @@ struct DevCase {
   int geom, nx, nr, bc_xlo, bc_xhi, bc_rhi, jw, nblocks;
   int tiles_x, tiles_y;   // tile grid of the shape in use (nblocks = tiles_x * tiles_y)
   int viscous;            // viscous and diffusive fluxes
+  int qoff;               // FP32 + surrogate through the column sweep: the surrogate queue's
+                          // place in the workspace, in 256-byte units from its start (0: none)
   double nu_t;            // turbulent kinematic viscosity
   float fnu_t;
   double dx, dr, idx, idr, cfl;
@@ -71,6 +76,19 @@ struct DevCase {
   // stage converts its halo cells and its own cells itself
   double* prims;
 };
+
+// The surrogate queue of a workspace (stage_sweep.cuh): for at most N cells, their indices,
+// their 14 rates (field-major, stride N), then the queue kernel's partial records.
+__device__ __forceinline__ unsigned int* queue_cells(const DevCase& dc) {
+  return reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(dc.hdr) + (size_t)dc.qoff * 256);
+}
+__device__ __forceinline__ size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+__device__ __forceinline__ float* queue_rates(const DevCase& dc, size_t N) {
+  return reinterpret_cast<float*>(reinterpret_cast<char*>(queue_cells(dc)) + round256(N * sizeof(unsigned int)));
+}
+__device__ __forceinline__ double* queue_partials(const DevCase& dc, size_t N) {
+  return reinterpret_cast<double*>(reinterpret_cast<char*>(queue_rates(dc, N)) + round256((size_t)NF * N * sizeof(float)));
+}
 
 // Tile of TX x TY cells per CTA with a two-cell halo (HX x HY).  NT threads: the larger of
 // the x-face ((TX+1) x TY) and r-face (TX x (TY+1)) counts rounded up to whole warps, so that
@@ -349,11 +367,51 @@ __device__ inline bool tile_reduce(const DevCase& dc, int by, double* out) {
   return true;
 }
 
+// Publish a stage's reduced record (thread 0 of the block that reduced it): stage 1 the
+// boundary inflow rates and the timeouts, stage 2 the diagnostics record and the next time
+// step (cfl times the stable step).
+__device__ inline void publish_stage(WsHeader* h, const double* fin, int stage, double dtd, double cfl) {
+  if (stage == 1) {
+    h->b1[0] = fin[4];
+    h->b1[1] = fin[5];
+    h->b1[2] = fin[6];
+    h->b1[3] = fin[26];
+  } else {
+    double* d = h->diag;
+    d[0] = dtd;
+    d[1] = fin[1];
+    d[2] = fin[2];
+    d[3] = fin[3];
+    d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
+    d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
+    d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
+    d[7] = fin[7];
+    d[8] = fin[8];
+    for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
+    d[23] = fin[23] * (1.0 / 2.302585092994045684);
+    d[24] = fin[24] * (1.0 / 2.302585092994045684);
+    const double dtn = cfl * fin[0];
+    d[25] = dtn;
+    d[26] = fin[25];
+    h->steps += 1.0;
+    d[27] = h->steps;
+    d[28] = h->b1[3] + fin[26];
+    h->dt_cur = dtn;
+  }
+}
+
 // ---- the fused stage kernel ---------------------------------------------------------------
 // shared memory of the surrogate phase, reusing the (then dead) stencil buffers:
 // activations, streamed weights, outputs, blob header, per-thread results
 constexpr size_t SM_A = 0, SM_W = SM_A + mlp::ABYTES, SM_OUT = SM_W + 32768, SM_HDR = SM_OUT + 128 * 10 * 4,
                  SM_RES = SM_HDR + mlp::NFLOAT * 4;
+// the surrogate queue kernel of the column sweep (stage_sweep.cuh): threads, shared memory,
+// CTAs of a launch at most (the room of its partial records in the workspace)
+struct QueueTile {
+  static constexpr int NT = 256;
+};
+constexpr size_t QUEUE_SMEM = SM_RES + (size_t)QueueTile::NT * 40;
+constexpr int QUEUE_GRID_MAX = 4096;
 template <class TL>
 constexpr size_t stage_smem_surr() {
   return TL::template smem<float>() > SM_RES + (size_t)TL::NT * 40 ? TL::template smem<float>()
@@ -1188,36 +1246,7 @@ __device__ __forceinline__ void stage_tile(const DevCase& dc, int bx, int by, in
     dc.partials[(size_t)tile * NPART + tid] = double(acc2);
   }
   if (!tile_reduce(dc, by, fin)) return;
-  if (tid == 0) {
-    WsHeader* h = dc.hdr;
-    if (STAGE == 1) {
-      h->b1[0] = fin[4];
-      h->b1[1] = fin[5];
-      h->b1[2] = fin[6];
-      h->b1[3] = fin[26];
-    } else {
-      double* d = h->diag;
-      d[0] = dtd;
-      d[1] = fin[1];
-      d[2] = fin[2];
-      d[3] = fin[3];
-      d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
-      d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
-      d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
-      d[7] = fin[7];
-      d[8] = fin[8];
-      for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
-      d[23] = fin[23] * (1.0 / 2.302585092994045684);
-      d[24] = fin[24] * (1.0 / 2.302585092994045684);
-      const double dtn = cfl * fin[0];
-      d[25] = dtn;
-      d[26] = fin[25];
-      h->steps += 1.0;
-      d[27] = h->steps;
-      d[28] = h->b1[3] + fin[26];
-      h->dt_cur = dtn;
-    }
-  }
+  if (tid == 0) publish_stage(dc.hdr, fin, STAGE, dtd, cfl);
 }
 
 // Register budget from __launch_bounds__: the register file is split between the SM's four
@@ -1331,6 +1360,8 @@ struct StageSet {
   const void* stage_sp[2];          // FP64 k_stage with the stored primitives (variant 0)
   const void* batch[NVARIANT][2];   // k_batch_stage (FP32 variants only)
   bool plume_inviscid_only;         // kernels for axisymmetric cases without diffusive fluxes only
+  const void* queue[2];             // FP32 + surrogate: the kernel after each stage kernel (or null)
+  size_t queue_smem;                // its dynamic shared memory
 };
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
 

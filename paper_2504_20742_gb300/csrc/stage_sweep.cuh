@@ -47,7 +47,10 @@ __device__ __forceinline__ float2 shfl_down2(float2 v) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
-template <class ST, int STAGE>
+// Q (FP32 + surrogate): the cells the screen keeps are not finished here but queued, with
+// their flux divergence, for k_sweep_queue, which runs the surrogate on them; the stage's
+// record then waits in the header (pre) for that kernel to complete and publish it.
+template <class ST, int STAGE, bool Q = false>
 __global__ void __launch_bounds__(ST::NT, ST::MINB)
     k_sweep(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
             const unsigned char* __restrict__ blob) {
@@ -368,7 +371,26 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
       }
 #pragma unroll
       for (int k2 = 0; k2 < NP; ++k2) s_fs[warp][k2][lane] = Fn[k2];
-      if (pending) {
+      if constexpr (Q) {
+        // queue the row's kept cells: one atomic per warp, slots in lane order
+        const unsigned pm = __ballot_sync(0xffffffffu, pending);
+        if (pm != 0u) {
+          unsigned base = 0u;
+          if (lane == 0) base = atomicAdd(&dc.hdr->qcount, (unsigned)__popc(pm));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (pending) {
+            const unsigned k = base + (unsigned)__popc(pm & ((1u << lane) - 1u));
+            queue_cells(dc)[k] = (unsigned)((size_t)j * nx + i);
+            float* qacc = queue_rates(dc, N);
+#pragma unroll
+            for (int k2 = 0; k2 < NP; ++k2) {
+              const V a = s_acc[warp][k2][lane];
+              qacc[(size_t)(2 * k2) * N + k] = a.x;
+              qacc[(size_t)(2 * k2 + 1) * N + k] = a.y;
+            }
+          }
+        }
+      } else if (pending) {
         const size_t n = (size_t)j * nx + i;
         T u14[NF], acc[NF];
 #pragma unroll
@@ -447,34 +469,183 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   }
   if (!tile_reduce(dc, by, fin)) return;
   if (threadIdx.x == 0) {
-    WsHeader* h = dc.hdr;
-    if (STAGE == 1) {
-      h->b1[0] = fin[4];
-      h->b1[1] = fin[5];
-      h->b1[2] = fin[6];
-      h->b1[3] = fin[26];
+    if (Q) {
+      for (int q = 0; q < NPART; ++q) dc.hdr->pre[q] = fin[q];
     } else {
-      double* d = h->diag;
-      d[0] = dtd;
-      d[1] = fin[1];
-      d[2] = fin[2];
-      d[3] = fin[3];
-      d[4] = 0.5 * dtd * (h->b1[0] + fin[4]);
-      d[5] = 0.5 * dtd * (h->b1[1] + fin[5]);
-      d[6] = 0.5 * dtd * (h->b1[2] + fin[6]);
-      d[7] = fin[7];
-      d[8] = fin[8];
-      for (int f = 0; f < NF; ++f) d[9 + f] = fin[9 + f];
-      d[23] = fin[23] * (1.0 / 2.302585092994045684);
-      d[24] = fin[24] * (1.0 / 2.302585092994045684);
-      const double dtn = dc.cfl * fin[0];
-      d[25] = dtn;
-      d[26] = fin[25];
-      h->steps += 1.0;
-      d[27] = h->steps;
-      d[28] = h->b1[3] + fin[26];
-      h->dt_cur = dtn;
+      publish_stage(dc.hdr, fin, STAGE, dtd, dc.cfl);
     }
+  }
+}
+
+// ---- the surrogate kernel of the FP32 + surrogate step through the column sweep ----------
+// The cells k_sweep<..., Q = true> queued (those its screen keeps), 256 at a time, take the
+// fused path's source (surrogate_source: the features, the BF16 tensor-core network inside
+// the training hull, the plain source outside it, the exact tail), then the RK combine, the
+// output and the partials; the last CTA merges its record with the sweep's and publishes
+// the stage.  A persistent grid: the queue's length is known on the device only.
+template <int STAGE>
+__global__ void __launch_bounds__(QueueTile::NT, 2)
+    k_sweep_queue(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
+                  const unsigned char* __restrict__ blob) {
+  using T = float;
+  using V = float2;
+  constexpr int NT = QueueTile::NT, NP = NF / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[NT / 32][NPART];
+  __shared__ double fin[NPART];
+  __shared__ unsigned int s_ticket;
+  // tensor-core resources up front (a CTA that has given up its allocation permit may not
+  // allocate again)
+  TcCtx tcx;
+  tcx.tmem = tc_acquire();
+  tcx.phase = 0;
+  tcx.wphase = 0;
+  tcx.ready = true;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nx = dc.nx;
+  const size_t N = (size_t)nx * dc.nr;
+  const unsigned count = dc.hdr->qcount;
+  const double dtd = dc.hdr->dt_cur;
+  const T dt = T(dtd);
+  const Geo<T> g = geo_of(dc, T(0));
+  KSum sM, sW, sE;
+  T dtmin = T(INFINITY);
+  T rmax[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) rmax[f] = T(0);
+  T lnJh = T(-INFINITY), lnJt = T(-INFINITY);
+  int nactive = 0, nbad = 0, nfallback = 0, ntimeout = 0;
+  for (unsigned base = blockIdx.x * NT; base < count; base += gridDim.x * NT) {   // uniform
+    const unsigned k = base + tid;
+    const bool cell = k < count;
+    size_t n = 0;
+    T u14[NF], acc[NF];
+    Prim<T> w{};
+    if (cell) {
+      n = queue_cells(dc)[k];
+      const float* qacc = queue_rates(dc, N);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        u14[f] = Uin[f * N + n];
+        acc[f] = qacc[(size_t)f * N + k];
+      }
+      cons_to_prim<T, false>(u14, w);
+    } else {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) u14[f] = acc[f] = T(0);
+    }
+    int na = 0, nf = 0;
+    T jh = T(-INFINITY), jt = T(-INFINITY);
+    surrogate_source<QueueTile, T>(dc, blob, cell, w, u14, acc, dt, na, nf, ntimeout, jh, jt, smem_raw, &tcx);
+    if (cell) {
+      nactive += na;
+      nfallback += nf;
+      lnJh = fmaxf(lnJh, jh);
+      lnJt = fmaxf(lnJt, jt);
+      // the sweep's RK combine, output and partials
+      T out[NF];
+      const V dt2 = p_make(dt, dt);
+      if (STAGE == 1) {
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const V o = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+          out[2 * k2] = o.x;
+          out[2 * k2 + 1] = o.y;
+        }
+      } else {
+        const V half2 = p_make(T(0.5), T(0.5));
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const V un2 = p_make(Un[(2 * k2) * N + n], Un[(2 * k2 + 1) * N + n]);
+          const V t = p_fma(dt2, p_make(acc[2 * k2], acc[2 * k2 + 1]), p_make(u14[2 * k2], u14[2 * k2 + 1]));
+          const V o = p_fma(half2, un2, p_mul(half2, t));
+          out[2 * k2] = o.x;
+          out[2 * k2 + 1] = o.y;
+          const T r0 = m_fabs(o.x - un2.x), r1 = m_fabs(o.y - un2.y);
+          rmax[2 * k2] = r0 > rmax[2 * k2] ? r0 : rmax[2 * k2];
+          rmax[2 * k2 + 1] = r1 > rmax[2 * k2 + 1] ? r1 : rmax[2 * k2 + 1];
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Uout[f * N + n] = out[f];
+        nbad += finite_bits(out[f]) ? 0 : 1;
+      }
+      if (STAGE == 2) {
+        Prim<T> wn;
+        cons_to_prim<T, false>(out, wn);
+        const T cdt = cell_dt<T>(dc, g, wn);
+        dtmin = cdt < dtmin ? cdt : dtmin;
+        const int j = (int)(n / (size_t)nx);
+        const T vol = (T(j) + T(0.5)) * g.dr * g.dr * g.dx;
+        sM.add(vol * out[0]);
+        sW.add(vol * (out[4] + T(k::YL3) * out[8] + T(k::YS3) * out[12]));
+        sE.add(vol * out[3]);
+      }
+    }
+  }
+  tc_release(tcx.tmem);
+  // warp records in FP64, the CTA's record in a fixed order (the sweep's layout)
+  {
+    const int nt = warp_count(ntimeout);
+    if (lane == 0) {
+      for (int q = 0; q < NPART; ++q) red[warp][q] = 0.0;
+      red[warp][26] = double(nt);
+    }
+    if (STAGE == 2) {
+      const double m = warp_sum(double(sM.s) - double(sM.c));
+      const double wt = warp_sum(double(sW.s) - double(sW.c));
+      const double e = warp_sum(double(sE.s) - double(sE.c));
+      const T dmin = warp_min_nonneg(dtmin);
+      const int na = warp_count(nactive), nb = warp_count(nbad), nfb = warp_count(nfallback);
+      const T jh = warp_max_any(lnJh), jt = warp_max_any(lnJt);
+      T rm[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) rm[f] = warp_max_nonneg(rmax[f]);
+      if (lane == 0) {
+        red[warp][0] = double(dmin);
+        red[warp][1] = m;
+        red[warp][2] = wt;
+        red[warp][3] = e;
+        red[warp][7] = double(na);
+        red[warp][8] = double(nb);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) red[warp][9 + f] = double(rm[f] * trcp(dt));
+        red[warp][23] = double(jh);
+        red[warp][24] = double(jt);
+        red[warp][25] = double(nfb);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < NPART) {
+    const int kind = slot_kind(tid);
+    double a = red[0][tid];
+    for (int w2 = 1; w2 < NT / 32; ++w2) {
+      const double v = red[w2][tid];
+      a = kind == 0 ? a + v : (kind == 1 ? (v > a ? v : a) : (v < a ? v : a));
+    }
+    queue_partials(dc, N)[(size_t)blockIdx.x * NPART + tid] = a;
+  }
+  // the last CTA to finish merges the records with the sweep's and publishes the stage
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_ticket = atomicAdd(&dc.hdr->qticket, 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  reduce_records(queue_partials(dc, N), gridDim.x, fin);
+  if (tid == 0) {
+    WsHeader* h = dc.hdr;
+    double m[NPART];
+    for (int q = 0; q < NPART; ++q) {
+      const int kind = slot_kind(q);
+      const double a = h->pre[q], b = fin[q];
+      m[q] = kind == 0 ? a + b : (kind == 1 ? (b > a ? b : a) : (b < a ? b : a));
+    }
+    publish_stage(h, m, STAGE, dtd, dc.cfl);
+    h->qcount = 0u;
+    h->qticket = 0u;
   }
 }
 
@@ -489,6 +660,14 @@ StageSet make_stage_set_sweep() {
   s.minb[1] = ST::MINB;
   s.stage[1][0] = (const void*)k_sweep<ST, 1>;
   s.stage[1][1] = (const void*)k_sweep<ST, 2>;
+  // FP32 + surrogate: the sweep queues the cells the screen keeps for k_sweep_queue
+  s.smem[2] = 0;
+  s.minb[2] = ST::MINB;
+  s.stage[2][0] = (const void*)k_sweep<ST, 1, true>;
+  s.stage[2][1] = (const void*)k_sweep<ST, 2, true>;
+  s.queue[0] = (const void*)k_sweep_queue<1>;
+  s.queue[1] = (const void*)k_sweep_queue<2>;
+  s.queue_smem = QUEUE_SMEM;
   s.plume_inviscid_only = true;
   return s;
 }
