@@ -673,20 +673,19 @@ ct_status ct_load_state(const ct_case* c, int precision, void* work, const void*
   return launch_dt(c, precision, work, U, cfl, st, uses_prims(c, precision));
 }
 
-// CTAs of a launch of the surrogate queue kernel: as many as the GPU keeps resident
-// (persistent; the queue's length is known on the device only), found once per device.
+// CTAs of a launch of the surrogate queue kernel: two per SM, what its registers and shared
+// memory are budgeted for (persistent; the queue's length is known on the device only).
+// The kernel never waits on another CTA, so CTAs beyond those resident only start later.
 static std::mutex g_qgrid_mu;
 static int g_qgrid[64];
-static int queue_grid(const void* fn, size_t smem) {
+static int queue_grid() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lk(g_qgrid_mu);
   if (g_qgrid[dev] == 0) {
-    int per_sm = 0, nsm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QueueTile::NT, smem) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm <= 0 || nsm <= 0)
-      return 0;
-    g_qgrid[dev] = std::min(QUEUE_GRID_MAX, per_sm * nsm);
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) return 0;
+    g_qgrid[dev] = std::min(QUEUE_GRID_MAX, 2 * nsm);
   }
   return g_qgrid[dev];
 }
@@ -709,9 +708,11 @@ static ct_status set_stage_attrs(int shape, int p) {
       e = cudaFuncSetAttribute(ss->stage_sp[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->smem[p]);
     if (e == cudaSuccess && p == 2 && ss->queue[st])
       e = cudaFuncSetAttribute(ss->queue[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->queue_smem);
+    if (e == cudaSuccess && p == 2 && ss->queue[st])   // two CTAs per SM need most of the SM's shared memory
+      e = cudaFuncSetAttribute(ss->queue[st], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
-  if (p == 2 && ss->queue[0] && queue_grid(ss->queue[0], ss->queue_smem) <= 0)
+  if (p == 2 && ss->queue[0] && queue_grid() <= 0)
     return fail(CT_ERR_CUDA, "no resident CTA for the surrogate queue kernel");
   g_attr_done[shape][p] = true;
   return CT_OK;
@@ -731,7 +732,7 @@ static void launch_stage(const StageSet* ss, int p, int stage, const DevCase& d,
   cudaLaunchKernel(fn, grid, dim3(ss->nt), args, ss->smem[p], st);
   // FP32 + surrogate through the column sweep: the surrogate kernel on the queued cells
   if (p == 2 && ss->queue[stage - 1] && d.qoff > 0) {
-    const int qgrid = queue_grid(ss->queue[stage - 1], ss->queue_smem);
+    const int qgrid = queue_grid();
     if (qgrid > 0) cudaLaunchKernel(ss->queue[stage - 1], dim3(qgrid), dim3(QueueTile::NT), args, ss->queue_smem, st);
   }
 }
