@@ -710,6 +710,10 @@ static ct_status set_stage_attrs(int shape, int p) {
       e = cudaFuncSetAttribute(ss->queue[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->queue_smem);
     if (e == cudaSuccess && p == 2 && ss->queue[st])   // two CTAs per SM need most of the SM's shared memory
       e = cudaFuncSetAttribute(ss->queue[st], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess && p == 2 && ss->batch_queue[st])
+      e = cudaFuncSetAttribute(ss->batch_queue[st], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss->queue_smem);
+    if (e == cudaSuccess && p == 2 && ss->batch_queue[st])
+      e = cudaFuncSetAttribute(ss->batch_queue[st], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   if (e != cudaSuccess) return fail(CT_ERR_CUDA, cudaGetErrorString(e));
   if (p == 2 && ss->queue[0] && queue_grid() <= 0)
@@ -1101,7 +1105,8 @@ static ct_status batch_upload(ct_batch* b) {
   for (int k = 0; k < n; ++k) {
     h.tiles_x[k] = tiles_x(&b->cases[k], b->shape);
     h.state_off[k] = b->state_off[k];
-    h.cases[k] = make_dev(&b->cases[k], b->work + b->case_off[k], b->shape);
+    h.cases[k] = make_dev(&b->cases[k], b->work + b->case_off[k], b->shape, false,
+                          uses_queue(&b->cases[k], CT_FP32_MLP));
   }
   // persistent grid: every SM full, never more CTAs than tiles
   const int p = variant_of(&b->cases[0], b->precision);
@@ -1118,8 +1123,9 @@ static ct_status batch_upload(ct_batch* b) {
       cudaSuccess)
     return cuda_check("occupancy");
   per_sm = std::max(1, per_sm);
-  if (b->precision == CT_FP32_MLP) {
-    // CTAs that finish often, so that every SM keeps per_sm of them resident
+  if (b->precision == CT_FP32_MLP && !ss->plume_inviscid_only) {
+    // CTAs that finish often, so that every SM keeps per_sm of them resident (the column
+    // sweep holds no TMEM: its queue kernel does, in a launch of its own)
     b->max_tiles = 4;
     b->grid = (t + b->max_tiles - 1) / b->max_tiles;
   } else {
@@ -1142,6 +1148,11 @@ static void batch_launch(ct_batch* b, int stage, const void* Uin, const void* Un
   int a6 = b->max_tiles;
   void* args[] = {b->table.data(), &ctr, &a1, &a2, &a3, &a4, &a5, &a6};
   cudaLaunchKernel(ss->batch[p][stage - 1], dim3(b->grid), dim3(ss->nt), args, ss->smem[p], st);
+  // FP32 + surrogate through the column sweep: every case's queue
+  if (p == 2 && ss->batch_queue[stage - 1]) {
+    void* qargs[] = {b->table.data(), &a1, &a2, &a3, &a4, &a5};
+    cudaLaunchKernel(ss->batch_queue[stage - 1], dim3(queue_grid()), dim3(QueueTile::NT), qargs, ss->queue_smem, st);
+  }
 }
 
 __global__ void k_batch_diag(const __grid_constant__ BatchTable bt, double* __restrict__ out) {
@@ -1151,10 +1162,14 @@ __global__ void k_batch_diag(const __grid_constant__ BatchTable bt, double* __re
 
 extern "C" {
 
+// A batch case's workspace: that of a single case, with the surrogate queue of the column
+// sweep wherever the sweep can step the case (FP32 + surrogate batches use it).
+static size_t batch_case_bytes(const ct_case* c) { return align256(ws_bytes(c, false, uses_queue(c, CT_FP32_MLP))); }
+
 size_t ct_batch_workspace_bytes(const ct_case* cases, int ncases) {
   if (batch_validate(cases, ncases, CT_FP32) != CT_OK) return 0;
   size_t b = batch_head_bytes(ncases);
-  for (int k = 0; k < ncases; ++k) b += align256(ws_bytes(&cases[k]));
+  for (int k = 0; k < ncases; ++k) b += batch_case_bytes(&cases[k]);
   return b;
 }
 
@@ -1185,14 +1200,14 @@ ct_status ct_batch_create(const ct_case* cases, int ncases, int precision, const
   for (int k = 0; k < ncases; ++k) {
     b->case_off.push_back(off);
     b->state_off.push_back(so);
-    off += align256(ws_bytes(&cases[k]));
+    off += batch_case_bytes(&cases[k]);
     so += (long long)case_nf(&cases[k]) * cases[k].nx * case_nr(&cases[k]);
   }
   // per-case workspace: header, inflow profile and ambient state
   for (int k = 0; k < ncases && s == CT_OK; ++k) {
     const ct_case* c = &cases[k];
     s = setup_case(c, precision, ufac_rows_host ? ufac_rows_host + row : nullptr, b->work + b->case_off[k],
-                   ws_bytes(c), stream, false);
+                   batch_case_bytes(c), stream, uses_queue(c, CT_FP32_MLP));
     row += (size_t)case_nr(c);
   }
   if (s == CT_OK && cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), b->stream) != cudaSuccess)
@@ -1236,10 +1251,20 @@ ct_status ct_batch_load_state(ct_batch* b, const void* U_src, void* U, double cf
   return CT_OK;
 }
 
+// a shape whose batched kernels exist for the batch's variant and suit all its cases
+static bool batch_shape_usable(const ct_batch* b, int shape) {
+  if (shape < 0 || shape >= NSHAPES) return false;
+  const StageSet* ss = stage_set(shape);
+  if (!ss->batch[variant_of(&b->cases[0], b->precision)][0]) return false;
+  if (ss->plume_inviscid_only)
+    for (const ct_case& c : b->cases)
+      if (c.geom != 1 || c.viscous) return false;
+  return true;
+}
+
 ct_status ct_batch_set_tile_shape(ct_batch* b, int shape) {
   if (!b) return fail(CT_ERR_ARG, "null batch");
-  if (shape < 0 || shape >= NSHAPES || !stage_set(shape)->batch[variant_of(&b->cases[0], b->precision)][0])
-    return fail(CT_ERR_ARG, "tile shape not available");
+  if (!batch_shape_usable(b, shape)) return fail(CT_ERR_ARG, "tile shape not available");
   if (shape == b->shape) return CT_OK;
   const int old = b->shape;
   b->shape = shape;
@@ -1261,7 +1286,7 @@ ct_status ct_batch_autotune(ct_batch* b, const void* U, void* U1, const void* bl
   ct_status s = CT_OK;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     float ms = -1.0f;
-    if (stage_set(sh)->batch[variant_of(&b->cases[0], b->precision)][0]) {
+    if (batch_shape_usable(b, sh)) {
       if ((s = ct_batch_set_tile_shape(b, sh)) != CT_OK) return s;
       // stage 1 only: it reads U and writes the scratch state U1
       auto launch = [&]() { batch_launch(b, 1, U, nullptr, U1, blob, 0.5, b->stream); };

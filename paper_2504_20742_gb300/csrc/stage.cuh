@@ -1361,7 +1361,8 @@ struct StageSet {
   const void* batch[NVARIANT][2];   // k_batch_stage (FP32 variants only)
   bool plume_inviscid_only;         // kernels for axisymmetric cases without diffusive fluxes only
   const void* queue[2];             // FP32 + surrogate: the kernel after each stage kernel (or null)
-  size_t queue_smem;                // its dynamic shared memory
+  const void* batch_queue[2];       // the same after each batched stage kernel
+  size_t queue_smem;                // their dynamic shared memory
 };
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;   // opt-in limit minus the static shared memory
 

@@ -50,10 +50,10 @@ __device__ __forceinline__ float2 shfl_down2(float2 v) {
 // Q (FP32 + surrogate): the cells the screen keeps are not finished here but queued, with
 // their flux divergence, for k_sweep_queue, which runs the surrogate on them; the stage's
 // record then waits in the header (pre) for that kernel to complete and publish it.
-template <class ST, int STAGE, bool Q = false>
-__global__ void __launch_bounds__(ST::NT, ST::MINB)
-    k_sweep(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
-            const unsigned char* __restrict__ blob) {
+// One strip tile (bx, by) of a case; `tile` = by * tiles_x + bx indexes the partial records.
+template <class ST, int STAGE, bool Q>
+__device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, int tile, const float* __restrict__ Uin,
+                                           const float* Un, float* Uout, double cfl) {
   using T = float;
   using V = float2;
   constexpr int NP = NF / 2;
@@ -70,10 +70,9 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
   // source screen takes the primitive variables from the ring instead of recomputing them)
   __shared__ float s_T[ST::W][3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int by = blockIdx.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
   const int nx = dc.nx, nr = dc.nr;
   const size_t N = (size_t)nx * nr;
-  const int i0 = blockIdx.x * ST::TX;
+  const int i0 = bx * ST::TX;
   const int i = i0 - 2 + lane;                       // this lane's column
   const int jb = by * ST::TY + warp * R;             // the warp's first row
   const int je = min(jb + R, nr);                    // one past its last row
@@ -403,14 +402,14 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
         }
         Prim<T> w;
         cons_to_prim<T, false>(u14, w);
-        T Q[NF];
+        T Qs[NF];
         double lnJ2[2];
-        if (phase_source<T, false>(w, u14, acc, dt, dc.sc, Q, lnJ2, nullptr)) {
+        if (phase_source<T, false>(w, u14, acc, dt, dc.sc, Qs, lnJ2, nullptr)) {
           nactive += 1;
           lnJh = fmaxf(lnJh, T(lnJ2[0]));
           lnJt = fmaxf(lnJt, T(lnJ2[1]));
 #pragma unroll
-          for (int f = 4; f < 13; ++f) acc[f] += Q[f];
+          for (int f = 4; f < 13; ++f) acc[f] += Qs[f];
         }
         finish(n, u14, acc);
       }
@@ -472,7 +471,53 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
     if (Q) {
       for (int q = 0; q < NPART; ++q) dc.hdr->pre[q] = fin[q];
     } else {
-      publish_stage(dc.hdr, fin, STAGE, dtd, dc.cfl);
+      publish_stage(dc.hdr, fin, STAGE, dtd, cfl);
+    }
+  }
+}
+
+template <class ST, int STAGE, bool Q = false>
+__global__ void __launch_bounds__(ST::NT, ST::MINB)
+    k_sweep(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
+            const unsigned char* __restrict__ blob) {
+  sweep_tile<ST, STAGE, Q>(dc, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, Uin, Un, Uout, dc.cfl);
+}
+
+// The batched persistent form (k_batch_stage's work list: CTAs take strip tiles of any case
+// from an atomic counter, largest cases first; the last CTA to leave resets the counter).
+template <class ST, int STAGE, bool Q>
+__global__ void __launch_bounds__(ST::NT, ST::MINB)
+    k_batch_sweep(const __grid_constant__ BatchTable bt, BatchCounters* __restrict__ ctr, const float* __restrict__ Uin,
+                  const float* Un, float* Uout, const unsigned char* __restrict__ blob, double cfl, int max_tiles) {
+  __shared__ int s_t, s_slot;
+  const int tid = threadIdx.x;
+  const int ncases = bt.ncases, total = bt.total_tiles;
+  for (int taken = 0; taken < max_tiles; ++taken) {
+    if (tid == 0) {
+      const int t = (int)atomicAdd(&ctr->next_tile, 1u);
+      int lo = 0, hi = ncases;   // slot with tile_start[slot] <= t < tile_start[slot + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bt.tile_start[mid] <= t) lo = mid; else hi = mid;
+      }
+      s_t = t;
+      s_slot = lo;
+    }
+    __syncthreads();
+    const int t = s_t, slot = s_slot;
+    if (t >= total) break;
+    const int k = bt.case_of[slot];
+    const int lt = t - bt.tile_start[slot], tx = bt.tiles_x[k];
+    const long long off = bt.state_off[k];
+    sweep_tile<ST, STAGE, Q>(bt.cases[k], lt % tx, lt / tx, lt, Uin + off, Un ? Un + off : nullptr, Uout + off, cfl);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr->exited, 1u) == gridDim.x - 1) {   // every CTA has left the loop
+      ctr->next_tile = 0u;
+      ctr->exited = 0u;
+      __threadfence();
     }
   }
 }
@@ -483,29 +528,27 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
 // the training hull, the plain source outside it, the exact tail), then the RK combine, the
 // output and the partials; the last CTA merges its record with the sweep's and publishes
 // the stage.  A persistent grid: the queue's length is known on the device only.
+// The queue of one case (all threads of every CTA of the launch; tcx: the CTA's tensor-core
+// resources, taken once per launch).
 template <int STAGE>
-__global__ void __launch_bounds__(QueueTile::NT, 2)
-    k_sweep_queue(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
-                  const unsigned char* __restrict__ blob) {
+__device__ __forceinline__ void queue_case(const DevCase& dc, const float* __restrict__ Uin, const float* Un,
+                                           float* Uout, const unsigned char* __restrict__ blob, double cfl,
+                                           TcCtx* tcx, unsigned char* smem_raw) {
   using T = float;
   using V = float2;
   constexpr int NT = QueueTile::NT, NP = NF / 2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[NT / 32][NPART];
   __shared__ double fin[NPART];
   __shared__ unsigned int s_ticket;
-  // tensor-core resources up front (a CTA that has given up its allocation permit may not
-  // allocate again)
-  TcCtx tcx;
-  tcx.tmem = tc_acquire();
-  tcx.phase = 0;
-  tcx.wphase = 0;
-  tcx.ready = true;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nx = dc.nx;
   const size_t N = (size_t)nx * dc.nr;
   const unsigned count = dc.hdr->qcount;
   const double dtd = dc.hdr->dt_cur;
+  if (count == 0u) {   // nothing queued: the sweep's record is the stage's (merging adds nothing)
+    if (blockIdx.x == 0 && tid == 0) publish_stage(dc.hdr, dc.hdr->pre, STAGE, dtd, cfl);
+    return;
+  }
   const T dt = T(dtd);
   const Geo<T> g = geo_of(dc, T(0));
   KSum sM, sW, sE;
@@ -536,7 +579,7 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
     }
     int na = 0, nf = 0;
     T jh = T(-INFINITY), jt = T(-INFINITY);
-    surrogate_source<QueueTile, T>(dc, blob, cell, w, u14, acc, dt, na, nf, ntimeout, jh, jt, smem_raw, &tcx);
+    surrogate_source<QueueTile, T>(dc, blob, cell, w, u14, acc, dt, na, nf, ntimeout, jh, jt, smem_raw, tcx);
     if (cell) {
       nactive += na;
       nfallback += nf;
@@ -584,7 +627,6 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
       }
     }
   }
-  tc_release(tcx.tmem);
   // warp records in FP64, the CTA's record in a fixed order (the sweep's layout)
   {
     const int nt = warp_count(ntimeout);
@@ -643,10 +685,46 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
       const double a = h->pre[q], b = fin[q];
       m[q] = kind == 0 ? a + b : (kind == 1 ? (b > a ? b : a) : (b < a ? b : a));
     }
-    publish_stage(h, m, STAGE, dtd, dc.cfl);
+    publish_stage(h, m, STAGE, dtd, cfl);
     h->qcount = 0u;
     h->qticket = 0u;
   }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(QueueTile::NT, 2)
+    k_sweep_queue(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
+                  const unsigned char* __restrict__ blob) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // tensor-core resources up front (a CTA that has given up its allocation permit may not
+  // allocate again)
+  TcCtx tcx;
+  tcx.tmem = tc_acquire();
+  tcx.phase = 0;
+  tcx.wphase = 0;
+  tcx.ready = true;
+  queue_case<STAGE>(dc, Uin, Un, Uout, blob, dc.cfl, &tcx, smem_raw);
+  tc_release(tcx.tmem);
+}
+
+// The batched form: the queues of every case of a batch in turn (cases without one skip).
+template <int STAGE>
+__global__ void __launch_bounds__(QueueTile::NT, 2)
+    k_batch_queue(const __grid_constant__ BatchTable bt, const float* __restrict__ Uin, const float* Un, float* Uout,
+                  const unsigned char* __restrict__ blob, double cfl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcCtx tcx;
+  tcx.tmem = tc_acquire();
+  tcx.phase = 0;
+  tcx.wphase = 0;
+  tcx.ready = true;
+  for (int k = 0; k < bt.ncases; ++k) {
+    if (bt.cases[k].qoff == 0) continue;
+    const long long off = bt.state_off[k];
+    queue_case<STAGE>(bt.cases[k], Uin + off, Un ? Un + off : nullptr, Uout + off, blob, cfl, &tcx, smem_raw);
+    __syncthreads();
+  }
+  tc_release(tcx.tmem);
 }
 
 template <class ST>
@@ -668,6 +746,13 @@ StageSet make_stage_set_sweep() {
   s.queue[0] = (const void*)k_sweep_queue<1>;
   s.queue[1] = (const void*)k_sweep_queue<2>;
   s.queue_smem = QUEUE_SMEM;
+  // batches: the persistent sweep over every case's strips, and the queues of every case
+  s.batch[1][0] = (const void*)k_batch_sweep<ST, 1, false>;
+  s.batch[1][1] = (const void*)k_batch_sweep<ST, 2, false>;
+  s.batch[2][0] = (const void*)k_batch_sweep<ST, 1, true>;
+  s.batch[2][1] = (const void*)k_batch_sweep<ST, 2, true>;
+  s.batch_queue[0] = (const void*)k_batch_queue<1>;
+  s.batch_queue[1] = (const void*)k_batch_queue<2>;
   s.plume_inviscid_only = true;
   return s;
 }

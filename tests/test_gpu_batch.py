@@ -113,6 +113,28 @@ def test_batch_matches_single_case_steps(P, blob, prec):
             assert abs(db[k, q] - d[q]) <= 1e-12 * abs(d[q])
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batched_column_sweep_matches_single_case_steps(P, blob, prec):
+    """The batch through the column-sweep shape (the persistent sweep over every case's
+    strips; FP32 + surrogate: then the queue kernel over every case's kept cells) against
+    each case stepped alone with the default shape: bit for bit."""
+    sweep = [k for k in range(P.ct_tile_shape_count()) if P.ct_tile_shape(k) == (28, 64)][0]
+    bc = _small_batch()
+    b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=prec, blob=blob if prec == 2 else None)
+    b.set_tile_shape(sweep)
+    b.init_state(0.5)
+    b.step(4, 0.5)
+    b.step(4, 0.5)
+    db = b.diagnostics()
+    assert np.all(db[:, 8] == 0)
+    for k, (c, uf) in enumerate(bc):
+        ref, d = _single(P, c, uf, prec, 8, blob)
+        assert torch.equal(b.state(k).view(torch.int32), ref.view(torch.int32)), k
+        assert db[k, 0] == d[0] and db[k, 7] == d[7] and db[k, 26] == d[26] and db[k, 27] == d[27]
+        for q in (1, 2, 3):
+            assert abs(db[k, q] - d[q]) <= 1e-6 * abs(d[q])
+
+
 def test_batch_shapes_autotune_and_recapture(P, blob):
     bc = _small_batch(4)
     b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32_MLP, blob=blob)
