@@ -314,11 +314,15 @@ def run_cuda(args):
         roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(bw / peaks["hbm_gbs"], 4),
                 "traffic": (FP32_TRAFFIC_PER_CELL_LAUNCH[shape] * cells
-                            if shape in FP32_TRAFFIC_PER_CELL_LAUNCH and not c.get("bimodal") else None),
-                "kernel": "ct::k_sweep<float>" if shape == SWEEP_SHAPE else "ct::k_stage<float>",
+                            if shape in FP32_TRAFFIC_PER_CELL_LAUNCH and not c.get("bimodal") and prec == 1
+                            else None),
+                "kernel": (("ct::k_sweep<float, queue> + ct::k_sweep_queue" if prec == 2 else "ct::k_sweep<float>")
+                           if shape == SWEEP_SHAPE else "ct::k_stage<float>"),
                 "peak_source": peak_kind,
                 "note": f"algorithmic bytes 2.5*{nf}*4 per cell per launch (mean of the two stages); "
-                        f"mean launch {launch_ms_ev:.4f} ms"}
+                        f"mean launch {launch_ms_ev:.4f} ms"
+                        + ("; a launch is the stage kernel and its surrogate queue kernel"
+                           if prec == 2 and shape == SWEEP_SHAPE else "")}
     bytes_state = cells * nf * elem
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -335,7 +339,7 @@ def run_cuda(args):
         "roofline": roof,
         "e2e": {"value": round(world * cells / e2e_s / 1e9, 5), "unit": UNIT,
                 "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps * (2 if prec == 2 and shape == SWEEP_SHAPE else 1),
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
         "diag": {"dt": d[0], "active_cells": d[7], "active_frac": round(d[7] / cells, 5), "nonfinite": d[8],
@@ -522,12 +526,13 @@ def run_batch(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(bw / peaks["hbm_gbs"], 4), "traffic": None,
-                     "kernel": "ct::k_batch_stage<float, surrogate>", "peak_source": peak_kind,
+                     "kernel": ("ct::k_batch_sweep<float, queue> + ct::k_batch_queue" if shape == SWEEP_SHAPE
+                                else "ct::k_batch_stage<float, surrogate>"), "peak_source": peak_kind,
                      "note": f"algorithmic bytes 2.5*14*4 per cell per launch (mean of the two stages); "
                              f"mean launch {launch_ms:.4f} ms"},
         "e2e": {"value": round(cells / e2e_s / 1e9, 5), "unit": UNIT,
                 "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps * (2 if shape == SWEEP_SHAPE else 1),
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
         "diag": {"dt_min": float(d[:, 0].min()), "dt_max": float(d[:, 0].max()),
