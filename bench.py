@@ -466,7 +466,11 @@ def run_batch(args):
         b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=P.CT_FP32_MLP, device=dev, stream=stream,
                     blob=blob)
         b.init_state(cfl)
-        shape, tune_ms = b.autotune(reps=2)
+        if args.tile_shape >= 0:                 # a given tile shape instead of the autotuner's pick
+            shape, tune_ms = args.tile_shape, []
+            b.set_tile_shape(shape)
+        else:
+            shape, tune_ms = b.autotune(reps=2)
         for _ in range(args.warmup):
             b.step(1, cfl)
         stream.synchronize()
@@ -520,8 +524,8 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic", "impl": "cuda",
         "config": {"workload": BATCH_DESC, "cases": len(bc) * world, "cells": cells, "cfl": cfl,
-                   "tile": f"{tx}x{ty}, {ctas} CTAs/SM (autotuned; ms per stage-1 launch per shape: "
-                           f"{[round(m, 4) for m in tune_ms]})",
+                   "tile": (f"{tx}x{ty}, {ctas} CTAs/SM (autotuned; ms per stage-1 launch per shape: "
+                            f"{[round(m, 4) for m in tune_ms]})" if tune_ms else f"{tx}x{ty}, {ctas} CTAs/SM (given)"),
                    "l2": "inputs larger than L2 (1.25 GB per FP32 state copy)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -612,8 +616,7 @@ def main():
                              "active_fp32_bimodal", "active_mlp", "active_fp64", "active_fp64_tables",
                              "active_fp64_bimodal", "batch64"))
     ap.add_argument("--tile-shape", type=int, default=-1,
-                    help="stage-kernel tile shape (ct_tile_shape index) instead of the autotuner's pick "
-                         "(single-case workloads)")
+                    help="stage-kernel tile shape (ct_tile_shape index) instead of the autotuner's pick")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="leave out the FP64 / FP32 / FP32+surrogate record of the default workload")

@@ -529,11 +529,12 @@ __global__ void __launch_bounds__(ST::NT, ST::MINB)
 // output and the partials; the last CTA merges its record with the sweep's and publishes
 // the stage.  A persistent grid: the queue's length is known on the device only.
 // The queue of one case (all threads of every CTA of the launch; tcx: the CTA's tensor-core
-// resources, taken once per launch).
+// resources, taken once per launch; pub: the CTA that publishes the stage when nothing is
+// queued).
 template <int STAGE>
 __device__ __forceinline__ void queue_case(const DevCase& dc, const float* __restrict__ Uin, const float* Un,
                                            float* Uout, const unsigned char* __restrict__ blob, double cfl,
-                                           TcCtx* tcx, unsigned char* smem_raw) {
+                                           TcCtx* tcx, unsigned char* smem_raw, int pub) {
   using T = float;
   using V = float2;
   constexpr int NT = QueueTile::NT, NP = NF / 2;
@@ -546,7 +547,7 @@ __device__ __forceinline__ void queue_case(const DevCase& dc, const float* __res
   const unsigned count = dc.hdr->qcount;
   const double dtd = dc.hdr->dt_cur;
   if (count == 0u) {   // nothing queued: the sweep's record is the stage's (merging adds nothing)
-    if (blockIdx.x == 0 && tid == 0) publish_stage(dc.hdr, dc.hdr->pre, STAGE, dtd, cfl);
+    if ((int)blockIdx.x == pub && tid == 0) publish_stage(dc.hdr, dc.hdr->pre, STAGE, dtd, cfl);
     return;
   }
   const T dt = T(dtd);
@@ -696,6 +697,10 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
     k_sweep_queue(DevCase dc, const float* __restrict__ Uin, const float* Un, float* Uout,
                   const unsigned char* __restrict__ blob) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (dc.hdr->qcount == 0u) {   // nothing queued: publish the sweep's record, take no TMEM
+    if (blockIdx.x == 0 && threadIdx.x == 0) publish_stage(dc.hdr, dc.hdr->pre, STAGE, dc.hdr->dt_cur, dc.cfl);
+    return;
+  }
   // tensor-core resources up front (a CTA that has given up its allocation permit may not
   // allocate again)
   TcCtx tcx;
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
   tcx.phase = 0;
   tcx.wphase = 0;
   tcx.ready = true;
-  queue_case<STAGE>(dc, Uin, Un, Uout, blob, dc.cfl, &tcx, smem_raw);
+  queue_case<STAGE>(dc, Uin, Un, Uout, blob, dc.cfl, &tcx, smem_raw, 0);
   tc_release(tcx.tmem);
 }
 
@@ -713,6 +718,19 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
     k_batch_queue(const __grid_constant__ BatchTable bt, const float* __restrict__ Uin, const float* Un, float* Uout,
                   const unsigned char* __restrict__ blob, double cfl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // nothing queued in any case: each case's record is published by one CTA, no TMEM taken.
+  // (Every CTA reads the counts before any is reset: a count is reset only after all CTAs
+  // have passed that case.)
+  int any = 0;
+  for (int k = threadIdx.x; k < bt.ncases; k += blockDim.x)
+    any |= (bt.cases[k].qoff != 0 && bt.cases[k].hdr->qcount != 0u) ? 1 : 0;
+  if (!__syncthreads_or(any)) {
+    if (threadIdx.x == 0)
+      for (int k = blockIdx.x; k < bt.ncases; k += gridDim.x)
+        if (bt.cases[k].qoff != 0)
+          publish_stage(bt.cases[k].hdr, bt.cases[k].hdr->pre, STAGE, bt.cases[k].hdr->dt_cur, cfl);
+    return;
+  }
   TcCtx tcx;
   tcx.tmem = tc_acquire();
   tcx.phase = 0;
@@ -721,7 +739,8 @@ __global__ void __launch_bounds__(QueueTile::NT, 2)
   for (int k = 0; k < bt.ncases; ++k) {
     if (bt.cases[k].qoff == 0) continue;
     const long long off = bt.state_off[k];
-    queue_case<STAGE>(bt.cases[k], Uin + off, Un ? Un + off : nullptr, Uout + off, blob, cfl, &tcx, smem_raw);
+    queue_case<STAGE>(bt.cases[k], Uin + off, Un ? Un + off : nullptr, Uout + off, blob, cfl, &tcx, smem_raw,
+                      k % (int)gridDim.x);
     __syncthreads();
   }
   tc_release(tcx.tmem);

@@ -117,16 +117,18 @@ def test_batch_matches_single_case_steps(P, blob, prec):
 def test_batched_column_sweep_matches_single_case_steps(P, blob, prec):
     """The batch through the column-sweep shape (the persistent sweep over every case's
     strips; FP32 + surrogate: then the queue kernel over every case's kept cells) against
-    each case stepped alone with the default shape: bit for bit."""
+    each case stepped alone with the default shape: bit for bit.  The mixing layer's source
+    fires, so its kept cells go through the queue."""
     sweep = [k for k in range(P.ct_tile_shape_count()) if P.ct_tile_shape(k) == (28, 64)][0]
     bc = _small_batch()
+    bc.append(cases.mixing_layer_case(nx=100, nr=44))   # a case whose source fires: queued cells
     b = P.Batch([c for c, _ in bc], [u for _, u in bc], precision=prec, blob=blob if prec == 2 else None)
     b.set_tile_shape(sweep)
     b.init_state(0.5)
     b.step(4, 0.5)
     b.step(4, 0.5)
     db = b.diagnostics()
-    assert np.all(db[:, 8] == 0)
+    assert np.all(db[:, 8] == 0) and db[-1, 7] > 0
     for k, (c, uf) in enumerate(bc):
         ref, d = _single(P, c, uf, prec, 8, blob)
         assert torch.equal(b.state(k).view(torch.int32), ref.view(torch.int32)), k
