@@ -88,9 +88,9 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
 
   // primitive vector (stage_tile's phase A) of cell (i, j) of the stencil; zero where no
   // cell of the strip needs it (corners, columns beyond the halo).  Returns whether the row
-  // is dry: every moment field (5..12) of the primitive vectors of the warp's 32 columns
-  // is +0.
-  const auto load_q = [&](int j, V* q, T& Tg) -> bool {
+  // is dry (1: every moment field (5..12) of the primitive vectors of the warp's 32 columns
+  // is +0; 2: the soot field too, as in the air around a plume's core) or not (0).
+  const auto load_q = [&](int j, V* q, T& Tg) -> int {
     const bool rin = j >= 0 && j < nr;
     if ((xin || rin) && i >= -2 && i <= nx + 1 && j >= -2 && j <= nr + 1) {
       T u14[NF];
@@ -119,7 +119,9 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
     unsigned zb = 0;
 #pragma unroll
     for (int k2 = 2; k2 < NP; ++k2) zb |= (k2 == 2 ? 0u : __float_as_uint(q[k2].x)) | (k2 == 6 ? 0u : __float_as_uint(q[k2].y));
-    return __all_sync(0xffffffffu, zb == 0u);
+    const unsigned zs = __float_as_uint(q[6].y);   // soot
+    const int dry = __all_sync(0xffffffffu, zb == 0u) ? 1 : 0;
+    return dry + (__all_sync(0xffffffffu, (zb | zs) == 0u) ? 1 : 0);
   };
 
   // running partials of this lane's cells
@@ -132,7 +134,7 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
 
   // dry rows around the current row j: bit 0 row j-1, bit 1 row j, bit 2 row j+1, bit 3
   // row j+2 (warp-uniform)
-  unsigned rowdry = 0;
+  unsigned rowdry = 0, rowsoot = 0;   // rowsoot: the same bits for the soot-free rows
   if (jb < je) {
     // rows jb-2 .. jb+1: the upper face state of row jb-1, row jb's lower face state, and the
     // flux of the face between rows jb-1 and jb; rows jb-1 .. jb+1 stay in the ring
@@ -140,9 +142,9 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
       V qm[NP], q0[NP], q1[NP], q2[NP];
       T Tm, T0, T1, T2;
       load_q(jb - 2, qm, Tm);
-      rowdry = load_q(jb - 1, q0, T0) ? 1u : 0u;
-      rowdry |= load_q(jb, q1, T1) ? 2u : 0u;
-      rowdry |= load_q(jb + 1, q2, T2) ? 4u : 0u;
+      const int l0 = load_q(jb - 1, q0, T0), l1 = load_q(jb, q1, T1), l2 = load_q(jb + 1, q2, T2);
+      rowdry = (l0 > 0 ? 1u : 0u) | (l1 > 0 ? 2u : 0u) | (l2 > 0 ? 4u : 0u);
+      rowsoot = (l0 > 1 ? 1u : 0u) | (l1 > 1 ? 2u : 0u) | (l2 > 1 ? 4u : 0u);
       s_T[warp][slot(jb - 1)][lane] = T0;
       s_T[warp][slot(jb)][lane] = T1;
       s_T[warp][slot(jb + 1)][lane] = T2;
@@ -174,11 +176,12 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
       // the divergence from the west neighbour's face.  A dry row: the all-moment pairs have
       // zero slopes and +0 face states (vl_faces2 of three +0 values gives hi = +0, lo = +0)
       const auto xphase = [&](auto dry_tag) {
-        constexpr bool DRY = decltype(dry_tag)::value;
+        constexpr int LEVEL = decltype(dry_tag)::value;
+        constexpr bool DRY = LEVEL > 0;
         T qL[NF], qR[NF], F[NF];
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
-          if (DRY && moment_pair(k2)) {
+          if ((DRY && moment_pair(k2)) || (LEVEL == 2 && k2 == NP - 1)) {
             qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
             continue;
           }
@@ -216,23 +219,30 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
           }
         }
       };
-      if (rowdry & 2u)
-        xphase(std::true_type{});
+      if (rowsoot & 2u)
+        xphase(std::integral_constant<int, 2>{});
+      else if (rowdry & 2u)
+        xphase(std::integral_constant<int, 1>{});
       else
-        xphase(std::false_type{});
+        xphase(std::integral_constant<int, 0>{});
       // r direction: row j+2 into the ring (over row j-1), row j+1's slope, face j+1/2.
       // Rows j-1 .. j+2 dry: the all-moment pairs of both face states are +0 (row j's upper
       // face state came from rows j-1 .. j+1)
       V Fn[NP];
       V qc[NP];
       T Tc;
-      rowdry |= load_q(j + 2, qc, Tc) ? 8u : 0u;
+      {
+        const int lc = load_q(j + 2, qc, Tc);
+        rowdry |= lc > 0 ? 8u : 0u;
+        rowsoot |= lc > 1 ? 8u : 0u;
+      }
       const auto rphase = [&](auto dry_tag) {
-        constexpr bool DRY = decltype(dry_tag)::value;
+        constexpr int LEVEL = decltype(dry_tag)::value;
+        constexpr bool DRY = LEVEL > 0;
         T qL[NF], qR[NF], F[NF];
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
-          if (DRY && moment_pair(k2)) {
+          if ((DRY && moment_pair(k2)) || (LEVEL == 2 && k2 == NP - 1)) {
             qL[2 * k2] = qL[2 * k2 + 1] = qR[2 * k2] = qR[2 * k2 + 1] = T(0);
             s_fhi[warp][k2][lane] = p_make(T(0), T(0));
             continue;
@@ -254,10 +264,12 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) Fn[k2] = p_make(F[2 * k2], F[2 * k2 + 1]);
       };
-      if ((rowdry & 15u) == 15u)
-        rphase(std::true_type{});
+      if ((rowsoot & 15u) == 15u)
+        rphase(std::integral_constant<int, 2>{});
+      else if ((rowdry & 15u) == 15u)
+        rphase(std::integral_constant<int, 1>{});
       else
-        rphase(std::false_type{});
+        rphase(std::integral_constant<int, 0>{});
       // cell (i, j): r divergence, sources, RK combine, partials (stage_tile's phase E).  A cell
       // the FP32 screen does not rule out takes its phase-change source after the row's other
       // work, its divergence parked in s_acc: there the FP64 island runs with few values live
@@ -421,6 +433,7 @@ __device__ __forceinline__ void sweep_tile(const DevCase& dc, int bx, int by, in
         }
       }
       rowdry >>= 1;
+      rowsoot >>= 1;
       __syncwarp();
     }
   }
