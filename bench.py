@@ -104,7 +104,7 @@ def _workload(name):
 # reported only for a shape counted on the current kernel.
 FP64_FLOPS_PER_CELL_STAGE = 565.1
 FP64_TRAFFIC_PER_CELL_LAUNCH = {7: 452.0, 8: 392.8}    # 16 x 16 and 16 x 14, two CTAs per SM
-FP32_TRAFFIC_PER_CELL_LAUNCH = {9: 140.3}    # the column sweep (28 x 64 strips), four CTAs per SM
+FP32_TRAFFIC_PER_CELL_LAUNCH = {9: 140.4}    # the column sweep (28 x 64 strips), four CTAs per SM
 SWEEP_SHAPE = 9   # tile shape index of the column-sweep FP32 kernel (k_sweep)
 # the viscous FP64 kernel (same capture recipe, plume with nu_t = 0.5 m^2/s, 16 x 14 tile:
 # 1135.9 and 1377.4 flops)
