@@ -1,23 +1,28 @@
-// stage_sweep.cuh -- the plain FP32 stage of an axisymmetric plume as column sweeps.
+// stage_sweep.cuh -- the FP32 stage of an axisymmetric plume as column sweeps.
 //
 // The same SSP-RK2 stage as stage_tile (Sec. 3.2: MUSCL/van Leer, Roe fluxes, axisymmetric
 // source, phase-change source, RK combine, partials), organised for the instruction issue
-// of sm_103a instead of shared-memory staging.  A warp owns a strip of 28 cells in x (lanes
-// 2..29; lanes 0, 1, 30 and 31 carry the two-column halo) and sweeps R rows in r, one row
-// per iteration:
-//   - x direction inside the warp: neighbour values by shuffles, one x-face flux per lane;
-//   - r direction in registers: the row's primitive vector, the upper face state of the
-//     previous row's slope and the south-face flux stay in the thread from one row to the
-//     next, so every r face is reconstructed and fluxed once, with no shared memory and no
-//     barrier.
+// of sm_103a instead of shared-memory staging of faces.  A warp owns a strip of 28 cells in
+// x (lanes 2..29; lanes 0, 1, 30 and 31 carry the two-column halo) and sweeps R rows in r,
+// one row per iteration, with no CTA barrier:
+//   - x direction inside the warp: neighbour values from a three-row ring of primitive
+//     vectors in shared memory, the right face state and the west flux by shuffles, one
+//     x-face flux per lane;
+//   - r direction along the sweep: per lane, the upper face state of the row below and the
+//     flux of its south face wait in shared memory from one row to the next, so every r face
+//     is reconstructed and fluxed once;
+//   - a cell that the FP32 source screen keeps takes its phase-change source after the row's
+//     fluxes are stored (its divergence parked in the lane's slot), where the FP64 island
+//     finds few values live.
 // Every cell value is computed by the same expressions in the same order as in stage_tile,
 // so the state is bitwise that of the other tile shapes; only the summation order of the
-// FP64 totals differs (compensated FP32 sums per lane, FP64 from the warp on).  Rows whose
-// particle moments are +0 in all 32 columns (dry air: most of a plume outside its mixing
-// layer) skip the reconstruction of the three all-moment field pairs, whose face states are
-// then +0, and the Y_l, Y_s terms of the face thermodynamics, which drop out exactly; the
-// bits are those of the full formulas.  Variant: FP32, axisymmetric, without the diffusive
-// fluxes, one liquid set, plain source.
+// FP64 totals differs (compensated FP32 sums per lane, FP64 from the warp on).  Dry rows
+// (the particle moments +0 in all 32 columns; level 2: the soot too) skip the reconstruction
+// of the all-moment field pairs (and the soot pair), whose face states are then +0, and the
+// Y_l, Y_s terms of the face thermodynamics, which drop out exactly: the bits of the full
+// formulas.  Variant: FP32, axisymmetric, without the diffusive fluxes, one liquid set;
+// plain source, or (Q) FP32 + surrogate through a queue that k_sweep_queue works off.  Both
+// have a batched persistent form (k_batch_sweep, k_batch_queue).
 #pragma once
 #include "stage.cuh"
 
