@@ -46,6 +46,13 @@ def test_workspace_size_and_case_validation(P):
     assert P.ct_workspace_bytes(bad, P.CT_FP64) == 0
     assert "nx" in P.ct_last_error()
     assert P.ct_workspace_bytes(c, 7) == 0
+    # FP32 + surrogate on a case the column sweep steps: the surrogate queue (a cell index
+    # and 14 rates per cell, 4096 reduction records) on top of the FP32 workspace
+    n = c["nx"] * c["nr"]
+    extra = P.ct_workspace_bytes(c, P.CT_FP32_MLP) - P.ct_workspace_bytes(c, P.CT_FP32)
+    assert 60 * n + 4096 * 27 * 8 <= extra <= 60 * n + 4096 * 27 * 8 + 3 * 256
+    visc = dict(c, viscous=1, nu_t=0.1)          # the sweep does not step it: no queue
+    assert P.ct_workspace_bytes(visc, P.CT_FP32_MLP) == P.ct_workspace_bytes(visc, P.CT_FP32)
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu(P):
@@ -146,6 +153,8 @@ def test_batch_sizes_and_validation_without_a_gpu(P):
     assert P.ct_batch_state_elems(bc) == elems
     ws = P.ct_batch_workspace_bytes(bc)
     assert ws >= sum(P.ct_workspace_bytes(c, P.CT_FP32) for c in bc)
+    # every case the batched column sweep can step holds its surrogate queue
+    assert ws >= sum(P.ct_workspace_bytes(c, P.CT_FP32_MLP) for c in bc)
     noz = cases.nozzle_case()
     assert P.ct_batch_workspace_bytes(bc + [noz]) == 0
     assert "geom" in P.ct_last_error()
