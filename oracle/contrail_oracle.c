@@ -23,9 +23,12 @@
  * mechanism; reading P): droplets of homogeneous origin keep fields 5..8, droplets of
  * heterogeneous (soot-activated) origin get four more fields 14..17.
  *
- * Parity pins: see tests/test_oracle_*.py.  Parity unpinned (no independent reference
- * available): the Koop (2000) freezing polynomial coefficients, the alpha_crit reading of
- * the Kantrowitz factor, and everything that needs the paper's REFPROP/IAPWS-95 backend.
+ * Parity pins: see tests/test_oracle_*.py (golden values under tests/golden/).  Pinned
+ * under a reading, not against numbers the paper prints: alpha_crit of the Kantrowitz
+ * factor (Eq. 5), q_c = 1 and the soot gating of J_het.  Pinned against their own
+ * publications rather than the paper, which cites but does not print them: the Sonntag,
+ * IAPWS and Koop (2000) coefficient sets.  Parity unpinned: everything that needs the
+ * paper's REFPROP/IAPWS-95 backend.
  */
 #include <math.h>
 #include <stdint.h>
